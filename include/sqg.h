@@ -1,0 +1,239 @@
+/*
+ * sqg.h -- C ABI of the GB300 SymphonyQG query-phase library (libsqg.so).
+ *
+ * SymphonyQG (arXiv 2411.12229) answers an approximate k-nearest-neighbour
+ * query by a beam search over a graph in which every vertex owns one
+ * contiguous block: its raw fp32 vector, the RaBitQ 1-bit codes and
+ * correction factors of its out-neighbours (normalized about the vertex
+ * itself), and the neighbour ids (Sec. 3.1.3, "dedicated data layout").
+ * Expanding a vertex reads that block once: its exact distance updates the
+ * result set (implicit re-ranking, Sec. 3.1.2) and the neighbours' distances
+ * are estimated in one batch (Sec. 3.1.1, Eq. (5)-(6)); every unvisited
+ * neighbour enters the beam with its estimate, even when already there
+ * (multiple estimated distances, Sec. 3.1.2); Algorithm 1 gives the loop.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (SQG_OK) or a negative SQG_ERR_* code; nothing is thrown and
+ *     nothing is printed.  sqg_error_string() names a code.
+ *   - Pointers are DEVICE pointers unless the comment says host.  The caller
+ *     owns every buffer it passes; the library owns the index's device copy.
+ *   - Work is enqueued on the caller's stream and returns before it runs,
+ *     unless the comment says the call synchronizes.
+ *   - Floats are IEEE fp32; ids are uint32; SQG_NO_ID marks padding.
+ *   - Queries must be finite; d is the index's dimension.
+ *   - An index is read-only after loading: searches on different streams
+ *     may run concurrently.
+ */
+#ifndef SQG_H
+#define SQG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *sqg_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+/* ---- error codes (return values) ---- */
+#define SQG_OK 0
+#define SQG_ERR_INVALID_ARG (-1) /* null pointer, nq < 0, k < 1, ef < k, k > SQG_MAX_K, ... */
+#define SQG_ERR_IO (-2)          /* index file cannot be opened or read / written */
+#define SQG_ERR_FORMAT (-3)      /* bad magic, version, sizes or hash in the index file */
+#define SQG_ERR_OOM (-4)         /* host or device allocation failed */
+#define SQG_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+#define SQG_ERR_TIMEOUT (-6)     /* a bounded device wait expired (see SQG_STATUS_TIMEOUT) */
+#define SQG_ERR_CAPACITY (-7)    /* workspace or shared memory too small for the request */
+#define SQG_ERR_UNSUPPORTED (-8) /* shape the kernels are not built for (see sqg_index_load) */
+
+/* ---- per-query status bits (sqg_query_stats.status, device status word) ---- */
+#define SQG_STATUS_CAPACITY 1u     /* the hop cap ended the search (results still valid) */
+#define SQG_STATUS_LEARNED_STOP 2u /* the learned early stop ended the search */
+#define SQG_STATUS_BAD_PARAM 4u    /* this query's k or ef was invalid: output is padding */
+#define SQG_STATUS_TIMEOUT 8u      /* a bounded wait on a block copy expired: output is padding */
+
+#define SQG_MAX_K 256
+#define SQG_MAX_EF 2048
+#define SQG_NO_ID 0xFFFFFFFFu
+
+/* Learned early stop: a 16 -> 64 -> 64 -> 1 fp32 MLP (ReLU hidden units)
+ * over 16 search-state features; parameters flat in the order
+ * W1[64][16], b1[64], W2[64][64], b2[64], W3[64], b3. Not in the paper. */
+#define SQG_MLP_IN 16
+#define SQG_MLP_HIDDEN 64
+#define SQG_MLP_NPARAM 5313
+
+typedef struct sqg_index sqg_index; /* opaque; owns the device-resident blocks */
+
+typedef struct {
+    uint64_t n;            /* vertices */
+    uint32_t d;            /* dimension (a multiple of 32) */
+    uint32_t degree;       /* out-degree R of every vertex (a multiple of 32) */
+    uint32_t block_bytes;  /* bytes per vertex block, a multiple of 128 */
+    uint32_t entry;        /* entry point of Algorithm 1 */
+    uint32_t off_codes, off_factors, off_ids; /* byte offsets inside a block */
+    int32_t device;        /* CUDA device holding the index */
+    uint64_t device_bytes; /* device memory held by the index */
+} sqg_info;
+
+typedef struct {
+    float eps0;              /* admission key = estimate - eps0 * bound; 0 = Algorithm 1 */
+    int32_t multi_estimate;  /* 1: every unvisited neighbour enters the beam (Sec. 3.1.2);
+                                0: ablation "w/o ME", the first estimate only (Sec. 5.4) */
+    int32_t hop_cap;         /* expansions per query; 0 = 8*ef + 64 */
+    int32_t max_k, max_ef;   /* bounds of the batch's k[] and ef[]; 0 = read them from the
+                                device (sqg_search then synchronizes the stream once) */
+    const float *stop_mlp;   /* device, SQG_MLP_NPARAM floats, or NULL: learned stop off */
+    float stop_logit;        /* stop when the MLP's logit exceeds this */
+    int32_t stop_every;      /* evaluate the stop every this many expansions (>= 1) */
+    int32_t team;            /* lanes per query: 32 (default, 0) or 16 */
+    int32_t warps_per_block; /* 0 = library default */
+} sqg_search_params;
+
+typedef struct {
+    uint32_t hops;   /* vertices expanded */
+    uint32_t status; /* SQG_STATUS_* bits */
+} sqg_query_stats;
+
+/* Name of an error code (static string). */
+const char *sqg_error_string(int code);
+
+/* Load an index file (format below) from the HOST path `path` onto CUDA
+ * device `device` and return a handle in *out.  Validates magic, version,
+ * sizes and both FNV-1a hashes; SQG_ERR_FORMAT on any mismatch, SQG_ERR_IO
+ * if unreadable, SQG_ERR_UNSUPPORTED if d or degree is outside the built
+ * kernels (d in {32,...,2048} multiple of 32, degree in {32, 64}).
+ * Synchronous.  Layout of the file and of each vertex block: Sec. 3.1.3
+ * (raw vector, then the FastScan data, then the neighbour ids); space
+ * n(32D + 32R + DR) bits plus factors (Sec. 3.3).
+ *
+ * File v1, little-endian: 256-byte header
+ *   0 "SQG1" | 4 version=1 u32 | 8 n u64 | 16 d u32 | 20 R u32 |
+ *   24 block_bytes u32 | 28 entry u32 | 32 metric u32 (0 = squared L2) |
+ *   36 off_codes | 40 off_factors | 44 off_ids (u32) | 48 rot_offset u64 |
+ *   56 blocks_offset u64 | 64 file_bytes u64 | 72 seed_rotation u64 |
+ *   80 seed_graph u64 | 88 payload_hash u64 | 96 header_hash u64
+ * header_hash = FNV-1a-64 over u64 words of bytes [0,96); payload_hash over
+ * u64 words of [rot_offset, file_bytes).  At rot_offset: P^-1 as d*d fp32
+ * row-major.  At blocks_offset: n blocks; block of vertex v:
+ *   raw[d] fp32 | codes: u32 word w of neighbour j at index w*R + j, bit
+ *   (i mod 32) of word i/32 = code bit of dimension i | f_add[R],
+ *   f_rescale[R], f_err[R] fp32, popcount[R] u32 | ids[R] u32 | zero pad
+ *   to a multiple of 128 bytes. */
+int sqg_index_load(const char *path, int device, sqg_index **out);
+
+/* Free an index and its device memory (synchronizes the device). NULL is a no-op. */
+void sqg_index_free(sqg_index *ix);
+
+/* Shape of a loaded index into *out (host). */
+int sqg_index_info(const sqg_index *ix, sqg_info *out);
+
+/* Device workspace bytes sqg_search_ex needs for nq queries with the given
+ * bounds (host call, no device work). */
+size_t sqg_workspace_size(const sqg_index *ix, int nq, int max_k, int max_ef);
+
+/* Search nq queries (Algorithm 1 per query, with multiple estimated
+ * distances and implicit re-ranking, Sec. 3.1).
+ *   queries  nq x d fp32 row-major
+ *   k, ef    nq int32 each: results wanted and beam size n_b per query
+ *            (1 <= k <= SQG_MAX_K, k <= ef <= SQG_MAX_EF)
+ *   out_ids, out_dists: ragged, query i at offset sum_{j<i} k[j]; k[i]
+ *            (id, exact squared distance) pairs sorted by (dist, id),
+ *            padded with (SQG_NO_ID, +inf) when fewer vertices were reached.
+ *            A query with invalid k or ef contributes max(0, min(k,
+ *            SQG_MAX_K)) slots, all padding, and sets SQG_STATUS_BAD_PARAM.
+ * Scratch is taken from the stream-ordered allocator on `stream`.  The
+ * call synchronizes the stream once to read the batch's largest k and ef.
+ * SQG_ERR_INVALID_ARG for null pointers or nq < 0 (nq = 0 is a no-op). */
+int sqg_search(const sqg_index *ix, const float *queries, int nq, const int32_t *k, const int32_t *ef,
+               uint32_t *out_ids, float *out_dists, sqg_stream_t stream);
+
+/* sqg_search with explicit parameters (NULL = defaults), a caller-owned
+ * workspace (NULL = stream-ordered allocation) of ws_bytes >=
+ * sqg_workspace_size(), and optional per-query stats (nq entries, device).
+ * With params->max_k and max_ef given and a workspace, the call is
+ * asynchronous and allocates nothing.  SQG_ERR_CAPACITY when the workspace
+ * is too small or the bounds need more shared memory than a block has. */
+int sqg_search_ex(const sqg_index *ix, const float *queries, int nq, const int32_t *k, const int32_t *ef,
+                  uint32_t *out_ids, float *out_dists, const sqg_search_params *params, void *workspace,
+                  size_t ws_bytes, sqg_query_stats *stats, sqg_stream_t stream);
+
+/* Query preparation alone (the first kernels of sqg_search), for tests:
+ *   out_qrot   nq x d fp32: q' = P^-1 q (Eq. (4)), each coordinate an fmaf
+ *              chain over j = 0..d-1 starting from 0
+ *   out_planes nq x 4 x d/32 u32: bit (i mod 32) of word [b][i/32] = bit b
+ *              of the 4-bit code qbar_i
+ *   out_scal   nq x 4: (v_l, delta, Sq as float, 1/sqrt(d)) with
+ *              delta = (v_r - v_l)/15 and qbar_i = min(15,
+ *              trunc((q'_i - v_l) * 15/(v_r - v_l) + 0.5)) */
+int sqg_prepare_queries(const sqg_index *ix, const float *queries, int nq, float *out_qrot,
+                        uint32_t *out_planes, float *out_scal, sqg_stream_t stream);
+
+/* Estimates for all R neighbours of one vertex per query, for tests
+ * (Sec. 3.1.1): for query i and vertex v[i] writes, at [i*R + j],
+ *   S      = sum_d b_d qbar_d (int32, exact)
+ *   est    = f_add + dist_c + f_rescale * ip,
+ *            ip = fmaf(delta, 2S - Sq, v_l (2 popcount - d)) / sqrt(d)
+ *   key    = est - eps0 * f_err * sqrt(dist_c)
+ * and dist_c[i] = exact squared distance of query i to v[i]. */
+int sqg_estimate_block(const sqg_index *ix, const float *queries, int nq, const uint32_t *v, float eps0,
+                       int32_t *out_S, float *out_est, float *out_key, float *out_dist_c, sqg_stream_t stream);
+
+/* sqg_search_ex that also records the learned stop's training data (not in
+ * the paper).  At every stop_every-th expansion once the result holds k
+ * entries, query i appends the 16 search-state features (fp32) to
+ * trace_feat[(i*trace_cap + t)*16 ...] and, when gt is given (nq x gt_k
+ * ground-truth ids, gt_k >= every k[i]), the number of the first k[i] gt ids
+ * present in its current result to trace_hit[i*trace_cap + t]; trace_n[i]
+ * receives the number of rows written (at most trace_cap).  Scratch comes
+ * from the stream-ordered allocator. */
+int sqg_search_trace(const sqg_index *ix, const float *queries, int nq, const int32_t *k, const int32_t *ef,
+                     uint32_t *out_ids, float *out_dists, const sqg_search_params *params, sqg_query_stats *stats,
+                     const uint32_t *gt, int gt_k, float *trace_feat, int32_t *trace_hit, int32_t *trace_n,
+                     int trace_cap, sqg_stream_t stream);
+
+/* OR of the status bits every search on this index has raised since the
+ * last call, then cleared.  Synchronizes `stream`. */
+int sqg_get_status(const sqg_index *ix, sqg_stream_t stream, uint32_t *status);
+
+/* ---- host-side index construction (Algorithm 2, Sec. 3.2) ---- */
+
+/* Exact k nearest neighbours of every base vector among the base vectors
+ * (itself excluded), multithreaded on the host, fp32.  data n x d (host),
+ * out n x k (host) sorted by (dist, id).  For small n only (O(n^2 d)). */
+int sqg_knn_host(const float *data, uint64_t n, uint32_t d, uint32_t k, uint32_t *out, int threads);
+
+/* Build one graph of Algorithm 2 from candidate lists (host):
+ *   data n x d fp32; cand n x L uint32 candidates per vertex (any order,
+ *   SQG_NO_ID = none; the vertex itself and repeats are ignored);
+ *   out_adj n x R: for each vertex, NSG's pruning rule keeps at most R
+ *   candidates (Sec. 3.2.1), reverse edges are offered to their targets and
+ *   re-pruned, and the adaptive angle rule supplements pruned candidates
+ *   until exactly R edges remain (Sec. 3.2.2); random vertices fill any
+ *   remaining gap (Sec. 3.2.2, footnote).  Every vertex is then made
+ *   reachable from `entry` by replacing the farthest edge of a reachable
+ *   vertex.  out_stats (host, 4): [avg degree after NSG pruning x 1000,
+ *   vertices needing supplement, vertices randomly filled, repairs]. */
+int sqg_build_graph(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L, uint32_t R,
+                    uint32_t entry, uint64_t seed, uint32_t *out_adj, uint64_t *out_stats, int threads);
+
+/* Vertex nearest to the mean of the data (host), the entry point used by
+ * the builder. */
+uint32_t sqg_medoid(const float *data, uint64_t n, uint32_t d, int threads);
+
+/* Quantize every edge and write an index file (host; "prepare data for
+ * FastScan", Algorithm 2):  rot = P^-1 (d x d fp32, row-major, orthogonal);
+ * for the edge c -> o, v = P^-1 (o - c)/||o - c||, code bit b_i = [v_i >= 0],
+ * alpha = sum|v_i|/sqrt(d), xc = <x_bar, P^-1 c>,
+ * f_add = ||o-c||^2 + 2||o-c|| xc/alpha, f_rescale = -2||o-c||/alpha,
+ * f_err = 2||o-c|| sqrt((1-alpha^2)/alpha^2)/sqrt(d-1); o = c gives zero
+ * bits and factors.  Writes `path` (host) in the format of sqg_index_load. */
+int sqg_write_index(const char *path, const float *data, uint64_t n, uint32_t d, const uint32_t *adj,
+                    uint32_t R, const float *rot, uint32_t entry, uint64_t seed_rotation, uint64_t seed_graph,
+                    int threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SQG_H */

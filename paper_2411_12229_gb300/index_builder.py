@@ -1,0 +1,156 @@
+"""Index construction driver (Algorithm 2, Indexing, Sec. 3.2).
+
+The paper builds the graph by starting from a random R-regular graph and
+repeating, t times: prepare the FastScan data (quantize every edge), search
+the current graph for candidates of every vertex with its own query
+algorithm, prune the candidates with NSG's rule, adjust the graph; then
+supplement edges so that every vertex has exactly R, and prepare the final
+FastScan data.  Here:
+
+* the FastScan data and the file are written by ``sqg_write_index`` (host);
+* the candidate search of every vertex is the GPU search kernel itself
+  (``Index.search`` with the vertex's own vector as the query, k = L results
+  by exact distance), which is the paper's "leverage our search to
+  accelerate index construction";
+* pruning, reverse edges and the adaptive-angle supplement run in
+  ``sqg_build_graph`` (host, multithreaded), so every intermediate graph
+  already has exactly R edges and can be searched by the same kernel;
+* without a GPU (tests) the candidates come from a brute-force kNN.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import pathlib
+import time
+
+import numpy as np
+
+from . import _binding as B
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def random_rotation(d: int, seed: int) -> np.ndarray:
+    """P^-1 of a Haar-random orthogonal P (Sec. 2.2, the JLT of Eq. (3)):
+    QR of a seeded standard Gaussian matrix, column signs fixed by diag(R),
+    in fp64; returned as float32 row-major."""
+    g = np.random.Generator(np.random.PCG64(np.random.SeedSequence(entropy=seed, spawn_key=(11, d))))
+    a = g.standard_normal((d, d))
+    q, r = np.linalg.qr(a)
+    q = q * np.sign(np.diag(r))[None, :]
+    return np.ascontiguousarray(q.T, dtype=np.float32)
+
+
+def knn_host(data: np.ndarray, k: int, threads: int = 0) -> np.ndarray:
+    data = np.ascontiguousarray(data, dtype=np.float32)
+    out = np.empty((data.shape[0], k), dtype=np.uint32)
+    B.check(B.lib().sqg_knn_host(_p(data), data.shape[0], data.shape[1], k, _p(out), threads), "sqg_knn_host")
+    return out
+
+
+def medoid(data: np.ndarray, threads: int = 0) -> int:
+    data = np.ascontiguousarray(data, dtype=np.float32)
+    return int(B.lib().sqg_medoid(_p(data), data.shape[0], data.shape[1], threads))
+
+
+def build_graph(data: np.ndarray, cand: np.ndarray, R: int, entry: int, seed: int = 3,
+                threads: int = 0) -> tuple[np.ndarray, dict]:
+    data = np.ascontiguousarray(data, dtype=np.float32)
+    cand = np.ascontiguousarray(cand, dtype=np.uint32)
+    n = data.shape[0]
+    adj = np.empty((n, R), dtype=np.uint32)
+    st = np.zeros(4, dtype=np.uint64)
+    B.check(B.lib().sqg_build_graph(_p(data), n, data.shape[1], _p(cand), cand.shape[1], R, entry, seed,
+                                    _p(adj), _p(st), threads), "sqg_build_graph")
+    return adj, dict(avg_nsg_degree=st[0] / 1000.0, supplemented=int(st[1]), random_filled=int(st[2]),
+                     repairs=int(st[3]))
+
+
+def write_index(path, data: np.ndarray, adj: np.ndarray, rot: np.ndarray, entry: int, seed_rotation: int,
+                seed_graph: int, threads: int = 0) -> None:
+    data = np.ascontiguousarray(data, dtype=np.float32)
+    adj = np.ascontiguousarray(adj, dtype=np.uint32)
+    rot = np.ascontiguousarray(rot, dtype=np.float32)
+    B.check(B.lib().sqg_write_index(str(path).encode(), _p(data), data.shape[0], data.shape[1], _p(adj),
+                                    adj.shape[1], _p(rot), entry, seed_rotation, seed_graph, threads),
+            f"sqg_write_index({path})")
+
+
+def random_graph(n: int, R: int, seed: int) -> np.ndarray:
+    """R distinct random out-neighbours per vertex, none the vertex itself
+    (the random initial graph of Algorithm 2)."""
+    g = np.random.Generator(np.random.PCG64(np.random.SeedSequence(entropy=seed, spawn_key=(12,))))
+    if n - 1 < R:
+        raise ValueError("need n > R")
+    adj = g.integers(0, n - 1, size=(n, R), dtype=np.int64)
+    adj += adj >= np.arange(n)[:, None]  # skip the vertex itself
+    for _ in range(64):
+        s = np.sort(adj, axis=1)
+        bad = np.nonzero((s[:, 1:] == s[:, :-1]).any(axis=1))[0]
+        if bad.size == 0:
+            break
+        for u in bad:
+            row = g.choice(n - 1, size=R, replace=False)
+            row = row + (row >= u)
+            adj[u] = row
+    return adj.astype(np.uint32)
+
+
+def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None, ef_build: int = 128,
+                cand_k: int | None = None, rot_seed: int = 2, graph_seed: int = 3, device: int | None = None,
+                init: str = "auto", threads: int = 0, log=None) -> dict:
+    """Build an index file at `path` from base vectors `data` (n x d).
+
+    device=None: host-only build from an exact kNN (small n).
+    device given: Algorithm 2 with the GPU search providing the candidates;
+    init "random" (the paper) or "knn" (host brute force, small n)."""
+    t0 = time.time()
+    data = np.ascontiguousarray(data, dtype=np.float32)
+    n, d = data.shape
+    cand_k = cand_k or 2 * R
+    rot = random_rotation(d, rot_seed)
+    entry = medoid(data, threads)
+    info = dict(n=n, d=d, R=R, entry=entry, iterations=[])
+    tmp = pathlib.Path(str(path) + ".tmp")
+    if init == "auto":
+        init = "knn" if (device is None or n <= 50_000) else "random"
+    if init == "knn":
+        cand = knn_host(data, min(cand_k, n - 1), threads)
+        adj, st = build_graph(data, cand, R, entry, graph_seed, threads)
+        info["iterations"].append(dict(source="knn", **st))
+    else:
+        adj = random_graph(n, R, graph_seed)
+    if iterations is None:
+        iterations = 0 if device is None else (3 if init == "random" else 1)
+    write_index(tmp if iterations else path, data, adj, rot, entry, rot_seed, graph_seed, threads)
+    if iterations:
+        import torch
+
+        from .api import Index
+        dev = torch.device("cuda", device)
+        xd = torch.from_numpy(data).to(dev)
+        k_res = min(cand_k, n)
+        for it in range(iterations):
+            t1 = time.time()
+            ix = Index(tmp, device)
+            cand = np.empty((n, k_res), dtype=np.uint32)
+            step = 1 << 18
+            for a in range(0, n, step):
+                b = min(n, a + step)
+                ids, _ = ix.search(xd[a:b], k_res, max(ef_build, k_res))
+                cand[a:b] = ids.cpu().numpy().view(np.uint32)
+            ix.close()
+            adj, st = build_graph(data, cand, R, entry, graph_seed + it + 1, threads)
+            final = it == iterations - 1
+            write_index(path if final else tmp, data, adj, rot, entry, rot_seed, graph_seed, threads)
+            info["iterations"].append(dict(source="gpu-search", seconds=time.time() - t1, **st))
+            if log:
+                log(f"build iteration {it + 1}/{iterations}: {time.time() - t1:.1f}s {st}")
+        if tmp.exists():
+            os.remove(tmp)
+    info["seconds"] = time.time() - t0
+    return info

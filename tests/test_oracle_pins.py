@@ -1,0 +1,370 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, a brute-force enumeration, a statistical property the paper states
+(unbiasedness, Sec. 2.2; ~50% under-estimation, Sec. 3.1.2), an identity
+reached by another route, or the exact kNN.
+"""
+
+import itertools
+import pathlib
+
+import numpy as np
+import pytest
+
+GOLDEN = pathlib.Path(__file__).with_name("golden")
+
+
+def haar(d, rng):
+    a = rng.standard_normal((d, d))
+    q, r = np.linalg.qr(a)
+    return (q * np.sign(np.diag(r))[None, :]).astype(np.float32)
+
+
+# --------------------------------------------------------------- rotation / quantization
+
+def test_rotate_f32_close_to_f64(oracle_mod):
+    rng = np.random.default_rng(1)
+    for d in (32, 128, 960):
+        P = haar(d, rng)
+        q = rng.standard_normal(d).astype(np.float32) * 3
+        a = oracle_mod.rotate_f32(P, q)
+        b = oracle_mod.rotate_f64(P, q)
+        ref = P.astype(np.float64) @ q.astype(np.float64)
+        np.testing.assert_allclose(b, ref, rtol=0, atol=1e-12 * np.abs(ref).max() * d)
+        assert np.max(np.abs(a - b)) <= 1e-5 * np.abs(b).max()
+
+
+def test_query_quantizer_closed_form(oracle_mod):
+    """4-bit uniform quantizer: codes in [0,15], extremes at 0 and 15, and the
+    dequantized value v_l + delta*qbar within delta/2 of q' (reading R1)."""
+    rng = np.random.default_rng(2)
+    for d in (32, 128, 1536):
+        x = (rng.standard_normal(d) * rng.uniform(0.1, 10)).astype(np.float32)
+        r = oracle_mod.quantize_query(x)
+        qb = r["qbar"].astype(np.int64)
+        assert qb.min() == 0 and qb.max() == 15
+        assert qb[np.argmin(x)] == 0 and qb[np.argmax(x)] == 15
+        assert r["sq"] == qb.sum()
+        assert r["delta"] == pytest.approx((x.max() - x.min()) / 15, rel=1e-6)
+        err = np.abs(r["vl"] + r["delta"] * qb - x.astype(np.float64))
+        assert err.max() <= r["delta"] * 0.5 * (1 + 1e-5) + 1e-6
+    const = np.full(64, 2.5, np.float32)
+    r = oracle_mod.quantize_query(const)
+    assert r["delta"] == 0.0 and r["qbar"].max() == 0 and r["sq"] == 0
+
+
+def test_codeword_is_the_nearest_by_enumeration(oracle_mod):
+    """Eq. (3): o_bar is the codebook vector nearest to o, i.e. the x in
+    {+-1/sqrt(D)}^D maximizing <P x, o>; <o_bar, o> is alpha.  D = 8: all 256
+    codewords enumerated."""
+    rng = np.random.default_rng(3)
+    d = 8
+    signs = np.array(list(itertools.product([-1.0, 1.0], repeat=d))) / np.sqrt(d)
+    for _ in range(50):
+        Pinv = haar(d, rng)
+        P = Pinv.astype(np.float64).T
+        c = rng.standard_normal(d).astype(np.float32)
+        o = rng.standard_normal(d).astype(np.float32)
+        bits, f = oracle_mod.quantize_edge(Pinv, c, o)
+        u = o.astype(np.float64) - c
+        u /= np.linalg.norm(u)
+        scores = (signs @ P.T) @ u  # <P x, o> for every codeword x
+        best = np.argmax(scores)
+        assert f["alpha"] == pytest.approx(scores[best], rel=1e-9)
+        np.testing.assert_array_equal(bits, (signs[best] > 0).astype(np.uint8))
+
+
+def test_alpha_concentrates_near_sqrt_2_over_pi(oracle_mod):
+    """For a random direction, <o_bar,o> = sum|v_i|/sqrt(D) tends to
+    sqrt(2/pi) ~ 0.798 (mean |N(0,1/D)| * sqrt(D))."""
+    rng = np.random.default_rng(4)
+    d = 256
+    Pinv = haar(d, rng)
+    al = []
+    for _ in range(200):
+        c = rng.standard_normal(d).astype(np.float32)
+        o = rng.standard_normal(d).astype(np.float32)
+        al.append(oracle_mod.quantize_edge(Pinv, c, o)[1]["alpha"])
+    assert abs(np.mean(al) - np.sqrt(2 / np.pi)) < 0.01
+
+
+def test_alpha_one_makes_the_estimate_exact(oracle_mod):
+    """If P^-1 (o-c)/||o-c|| is exactly a codeword, <o_bar,o> = 1 and the
+    estimator returns <o,q>: the unquantized estimate equals the exact
+    squared distance (Eq. (2)-(4))."""
+    rng = np.random.default_rng(5)
+    for d in (32, 64, 128):
+        Pinv = haar(d, rng)
+        P = Pinv.astype(np.float64).T
+        x = np.where(rng.integers(0, 2, d) == 1, 1.0, -1.0) / np.sqrt(d)
+        c = rng.standard_normal(d)
+        o = (c + 2.5 * (P @ x)).astype(np.float32)
+        q = rng.standard_normal(d).astype(np.float32)
+        est, bound, exact = oracle_mod.estimate_unquantized(Pinv, c.astype(np.float32), o, q)
+        _, f = oracle_mod.quantize_edge(Pinv, c.astype(np.float32), o)
+        assert f["alpha"] == pytest.approx(1.0, abs=1e-6)
+        assert f["f_err"] == pytest.approx(0.0, abs=1e-2)
+        assert est == pytest.approx(exact, rel=1e-5)
+
+
+def test_decoupled_factors_equal_the_normalized_estimator(oracle_mod):
+    """Eq. (5)-(6) substituted into Eq. (2): the factor form f_add + dist_c +
+    f_rescale <x_bar, P^-1 q_r> (computed here from the oracle's bits and
+    factors) equals the estimator with the query normalized about c."""
+    rng = np.random.default_rng(6)
+    for d in (32, 128):
+        Pinv = haar(d, rng)
+        for _ in range(20):
+            c, o, q = (rng.standard_normal(d).astype(np.float32) * 3 for _ in range(3))
+            bits, f = oracle_mod.quantize_edge(Pinv, c, o)
+            xbar = (2.0 * bits - 1.0) / np.sqrt(d)
+            qprime = Pinv.astype(np.float64) @ q.astype(np.float64)
+            dist_c = float(np.sum((q.astype(np.float64) - c) ** 2))
+            via_factors = f["f_add"] + dist_c + f["f_rescale"] * float(xbar @ qprime)
+            est, _, _ = oracle_mod.estimate_unquantized(Pinv, c, o, q)
+            assert via_factors == pytest.approx(est, rel=1e-9, abs=1e-9)
+
+
+def _estimates_over_rotations(oracle_mod, d, M, seed):
+    rng = np.random.default_rng(seed)
+    c, o, q = (rng.standard_normal(d).astype(np.float32) for _ in range(3))
+    out = np.array([oracle_mod.estimate_unquantized(haar(d, rng), c, o, q) for _ in range(M)])
+    return out[:, 0], out[:, 1], out[0, 2]
+
+
+def test_estimator_is_unbiased_over_random_rotations(oracle_mod):
+    """Sec. 2.2: <o_bar,q>/<o_bar,o> estimates <o,q> without bias; averaged
+    over random rotations the distance estimate's mean error is 0 within
+    4 standard errors."""
+    est, _, exact = _estimates_over_rotations(oracle_mod, 64, 3000, 7)
+    err = est - exact
+    se = err.std(ddof=1) / np.sqrt(len(err))
+    assert abs(err.mean()) < 4 * se
+
+
+def test_half_of_the_estimates_underestimate(oracle_mod):
+    """Sec. 3.1.2, property (1): each estimate under-estimates with
+    probability ~50%."""
+    est, _, exact = _estimates_over_rotations(oracle_mod, 128, 3000, 8)
+    frac = np.mean(est < exact)
+    assert 0.45 < frac < 0.55
+
+
+def test_error_bound_coverage(oracle_mod):
+    """The error bound (RaBitQ's form, reading R7): the estimate's error
+    divided by f_err*||q_r-c|| is about N(0, 1-<o,q>^2) over rotations, so
+    eps0 standard deviations cover at least P(|Z| <= eps0): ~94% at 1.9,
+    >= 99% at 3 (Sec. 3.1.2, "error-bounded")."""
+    rng = np.random.default_rng(9)
+    z = []
+    for _ in range(40):
+        est, bound, exact = _estimates_over_rotations(oracle_mod, 128, 50, int(rng.integers(1 << 30)))
+        z.append(np.abs(est - exact) / bound)
+    z = np.concatenate(z)
+    assert np.mean(z <= 1.9) >= 0.92
+    assert np.mean(z <= 3.0) >= 0.99
+    assert np.mean(z <= 1.0) <= 0.80  # the bound is not loose by a constant factor
+
+
+def test_exact_distance_canonical_order(oracle_mod):
+    rng = np.random.default_rng(10)
+    for d in (32, 96, 128, 960, 1536):
+        a, b = rng.standard_normal(d).astype(np.float32), rng.standard_normal(d).astype(np.float32)
+        ref = float(np.sum((a.astype(np.float64) - b) ** 2))
+        assert oracle_mod.exact_dist_f32(a, b) == pytest.approx(ref, rel=1e-5)
+        assert oracle_mod.sqdist_f64(a, b) == pytest.approx(ref, rel=1e-12)
+
+
+def test_bruteforce_matches_numpy_with_id_ties(oracle_mod):
+    rng = np.random.default_rng(11)
+    x = rng.integers(-3, 4, size=(500, 32)).astype(np.float32)  # many exact ties
+    q = rng.integers(-3, 4, size=32).astype(np.float32)
+    ids, dd = oracle_mod.bruteforce(x, q, 25)
+    dist = np.sum((x.astype(np.float64) - q) ** 2, axis=1)
+    order = np.lexsort((np.arange(500), dist))[:25]
+    np.testing.assert_array_equal(ids, order)
+    np.testing.assert_allclose(dd, dist[order])
+
+
+# --------------------------------------------------------------- golden closed-form case
+
+def load_golden():
+    rows = [l.split() for l in (GOLDEN / "alpha_one_d32.txt").read_text().splitlines() if not l.startswith("#")]
+    c = np.array(rows[0][1:], dtype=np.float32)
+    s = np.array([r[1:] for r in rows if r[0] == "s"], dtype=np.float32)
+    q = [r for r in rows if r[0] == "q"][0]
+    return c, s, np.array(q[1:], dtype=np.float32)
+
+
+def golden_index(path):
+    """33 vertices: c and c + s_j; identity rotation; vertex 0 -> 1..32."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    c, s, q = load_golden()
+    x = np.vstack([c[None, :], c[None, :] + s]).astype(np.float32)
+    adj = np.array([[v for v in range(33) if v != u] for u in range(33)], dtype=np.uint32)
+    ib.write_index(path, x, adj, np.eye(32, dtype=np.float32), 0, 0, 0)
+    return x, q
+
+
+def test_golden_alpha_one_estimates_are_exact(oracle_mod, lib_built, tmp_path):
+    """tests/golden/alpha_one_d32.txt: every estimate from the index equals
+    the integer ||o_j - q||^2 (closed form), through the file the library
+    writes and the oracle's fp32 path (4-bit query exact: v_l=0, delta=1)."""
+    p = tmp_path / "golden.sqg"
+    x, q = golden_index(p)
+    O = oracle_mod.Index(p)
+    r = O.estimate_block(q, 0)
+    v = O.vertex(0)
+    exact = np.array([np.sum((x[j] - q).astype(np.int64) ** 2) for j in v["ids"]], dtype=np.float64)
+    np.testing.assert_allclose(r["est"], exact, rtol=2e-6)
+    # S = sum_i b_i qbar_i with qbar = q exactly
+    np.testing.assert_array_equal(r["S"], (v["bits"].astype(np.int64) @ q.astype(np.int64)))
+    assert r["dist_c"] == np.sum((x[0] - q).astype(np.int64) ** 2)
+
+
+# --------------------------------------------------------------- search (Algorithm 1)
+
+@pytest.fixture(scope="module")
+def small_graph(tmp_path_factory, lib_built, oracle_mod):
+    from paper_2411_12229_gb300 import index_builder as ib
+    from paper_2411_12229_gb300 import synth
+    w = synth.small(synth.TINY_10K_D128, 200, 20, n_components=4)
+    x = synth.base(w)
+    p = tmp_path_factory.mktemp("g") / "g200.sqg"
+    ib.build_index(p, x, 32)
+    return oracle_mod.Index(p), x, synth.queries(w)
+
+
+def test_full_beam_returns_exact_knn(small_graph, oracle_mod):
+    """With a beam that never truncates (ef >= n*(R+1) entries), Algorithm 1
+    expands every vertex reachable from the entry, so with implicit
+    re-ranking it returns the exact k nearest neighbours."""
+    O, x, qs = small_graph
+    ef = O.n * (O.R + 1)
+    for i in range(5):
+        ids, dists, hops, st = O.search(qs[i], 10, ef, hop_cap=10 * ef)
+        gt, gd = oracle_mod.bruteforce(x, qs[i], 10)
+        assert hops == O.n and st == 0
+        np.testing.assert_array_equal(ids, gt)
+        np.testing.assert_allclose(dists, gd, rtol=1e-5)
+
+
+def test_results_are_exact_distances_of_expanded_vertices(tiny_index, oracle_mod):
+    """Implicit re-ranking (Sec. 3.1.2): every returned distance is the exact
+    distance of a vertex the search expanded; results sorted by (dist, id)."""
+    p, x, qs = tiny_index
+    O = oracle_mod.Index(p)
+    for i in range(10):
+        ids, dists, hops, st, path = O.search(qs[i], 10, 64, path_cap=100000)
+        assert len(path) == hops and len(set(path.tolist())) == hops and path[0] == O.entry
+        assert set(ids.tolist()) <= set(path.tolist())
+        ex = np.array([np.sum((x[j].astype(np.float64) - qs[i]) ** 2) for j in ids])
+        np.testing.assert_allclose(dists, ex, rtol=1e-5)
+        order = np.lexsort((ids, dists))
+        np.testing.assert_array_equal(order, np.arange(10))
+        # the nearest expanded vertex is returned first
+        pd = np.array([np.sum((x[j].astype(np.float64) - qs[i]) ** 2) for j in path])
+        assert ids[0] == path[np.argmin(pd)]
+
+
+def test_hop_cap_one_returns_the_entry(tiny_index, oracle_mod):
+    p, x, qs = tiny_index
+    O = oracle_mod.Index(p)
+    ids, dists, hops, st = O.search(qs[0], 3, 8, hop_cap=1)
+    assert hops == 1 and st == oracle_mod.STATUS_CAPACITY
+    assert ids[0] == O.entry and ids[1] == oracle_mod.NO_ID and np.isinf(dists[1])
+
+
+def test_eps0_shifts_keys_by_the_bound(tiny_index, oracle_mod):
+    """key = est - eps0 * f_err * ||q_r - c|| (reading R7)."""
+    p, x, qs = tiny_index
+    O = oracle_mod.Index(p)
+    r0 = O.estimate_block(qs[1], 17, 0.0)
+    r1 = O.estimate_block(qs[1], 17, 1.5)
+    v = O.vertex(17)
+    np.testing.assert_array_equal(r0["key"], r0["est"])
+    np.testing.assert_array_equal(r0["est"], r1["est"])
+    bound = v["f_err"].astype(np.float64) * np.sqrt(r0["dist_c"])
+    np.testing.assert_allclose(r1["key"], r1["est"] - 1.5 * bound, rtol=1e-5, atol=1e-3)
+
+
+def test_without_multiple_estimates_is_a_valid_search(tiny_index, oracle_mod):
+    """Sec. 5.4 ablation 'w/o ME' (first estimate only): still returns exact
+    distances of expanded vertices, and never expands more vertices than
+    the full beam can hold distinct ids for."""
+    p, x, qs = tiny_index
+    O = oracle_mod.Index(p)
+    for i in range(10):
+        ids, dists, hops, st, path = O.search(qs[i], 10, 32, multi_estimate=False, path_cap=100000)
+        assert set(ids.tolist()) <= set(path.tolist()) and st == 0
+        ex = np.array([np.sum((x[j].astype(np.float64) - qs[i]) ** 2) for j in ids])
+        np.testing.assert_allclose(dists, ex, rtol=1e-5)
+
+
+def test_learned_stop_constant_networks(tiny_index, oracle_mod):
+    """A network whose logit is a constant +100 stops at the first
+    evaluation; -100 never stops and equals the plain search."""
+    p, x, qs = tiny_index
+    O = oracle_mod.Index(p)
+    mlp = np.zeros(oracle_mod.MLP_NPARAM, np.float32)
+    for i in range(5):
+        plain = O.search(qs[i], 10, 64)
+        mlp[-1] = -100.0
+        never = O.search(qs[i], 10, 64, mlp=mlp, stop_logit=0.0)
+        np.testing.assert_array_equal(plain[0], never[0])
+        assert never[2] == plain[2] and never[3] == 0
+        mlp[-1] = 100.0
+        stop = O.search(qs[i], 10, 64, mlp=mlp, stop_logit=0.0, stop_every=4)
+        assert stop[3] == oracle_mod.STATUS_LEARNED_STOP
+        assert stop[2] >= 10 and stop[2] % 4 == 0 and stop[2] <= plain[2]
+
+
+# --------------------------------------------------------------- MLP training math
+
+def test_mlp_gradient_matches_finite_differences(oracle_mod):
+    rng = np.random.default_rng(12)
+    P = rng.standard_normal(oracle_mod.MLP_NPARAM) * 0.2
+    x = rng.standard_normal((16, 16)).astype(np.float32)
+    y = (rng.uniform(size=16) > 0.5).astype(np.float32)
+    w = rng.uniform(0.5, 2, size=16).astype(np.float32)
+    loss, g = oracle_mod.mlp_loss_grad_f64(P, x, y, w)
+    idx = rng.choice(oracle_mod.MLP_NPARAM, 60, replace=False)
+    idx = np.concatenate([idx, [oracle_mod.MLP_NPARAM - 1, 0, 1100, 5200]])
+    h = 1e-6
+    for i in idx:
+        Pp, Pm = P.copy(), P.copy()
+        Pp[i] += h
+        Pm[i] -= h
+        fd = (oracle_mod.mlp_loss_grad_f64(Pp, x, y, w)[0] - oracle_mod.mlp_loss_grad_f64(Pm, x, y, w)[0]) / (2 * h)
+        assert g[i] == pytest.approx(fd, rel=1e-4, abs=1e-7)
+
+
+def test_mlp_f32_logit_matches_f64_forward(oracle_mod):
+    """The fp32 forward (device order) agrees with a plain fp64 forward."""
+    rng = np.random.default_rng(13)
+    P = (rng.standard_normal(oracle_mod.MLP_NPARAM) * 0.3).astype(np.float32)
+    W1 = P[:1024].reshape(64, 16).astype(np.float64)
+    b1 = P[1024:1088].astype(np.float64)
+    W2 = P[1088:5184].reshape(64, 64).astype(np.float64)
+    b2 = P[5184:5248].astype(np.float64)
+    W3 = P[5248:5312].astype(np.float64)
+    b3 = float(P[5312])
+    for _ in range(20):
+        x = rng.standard_normal(16).astype(np.float32)
+        h1 = np.maximum(W1 @ x + b1, 0)
+        h2 = np.maximum(W2 @ h1 + b2, 0)
+        z = W3 @ h2 + b3
+        assert oracle_mod.mlp_logit_f32(P, x) == pytest.approx(z, rel=1e-5, abs=1e-5)
+
+
+def test_adam_first_step_closed_form(oracle_mod):
+    """Adam's first step moves each parameter by lr*g/(|g| + eps)."""
+    rng = np.random.default_rng(14)
+    n = 100
+    p = rng.standard_normal(n)
+    p0 = p.copy()
+    m, v = np.zeros(n), np.zeros(n)
+    g = rng.standard_normal(n)
+    oracle_mod.adam_step_f64(p, m, v, g, 1, 0.01)
+    np.testing.assert_allclose(p, p0 - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
