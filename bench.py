@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Benchmark: queries/sec at recall@10 >= 0.95 on one GB300 (and N replicas).
+
+One step = one batched search (Algorithm 1 per query, all rows of the query
+path: rotation, quantization, beam search with implicit re-ranking) over the
+workload's full query batch, at the smallest beam size ef of the sweep that
+reaches recall@10 >= 0.95.  Inputs are resident in HBM before the timed
+region; L2 is flushed (a 512 MiB write) between timed steps, outside the
+timed events.  `e2e` repeats the step through host buffers (pinned H2D of
+the queries, D2H of ids and distances inside the timed region).
+
+Multi-GPU: queries are independent, so N ranks are N replicas, each with
+its own index copy and its own query batch (weak scaling, no collective on
+the data path); value = all ranks' queries / the slowest rank's time.
+
+--impl reference times the CPU oracle (oracle/, single-threaded C per query,
+run on all host cores) on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import pathlib
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = pathlib.Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+from paper_2411_12229_gb300 import synth  # noqa: E402
+
+METRIC = "queries/sec at recall@10>=0.95"
+UNIT = "queries/s"
+
+
+def log(*a):
+    print("[bench]", *a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched-1m-d128", choices=list(synth.WORKLOADS))
+    ap.add_argument("--n", type=int, default=0, help="override N (smaller runs)")
+    ap.add_argument("--nq", type=int, default=0, help="override the query count")
+    ap.add_argument("--cache", default=os.environ.get("SQG_CACHE", "/tmp/sqg_cache"))
+    ap.add_argument("--target", type=float, default=0.95)
+    ap.add_argument("--build-iters", type=int, default=3)
+    ap.add_argument("--ef-build", type=int, default=64)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--skip-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    w = synth.WORKLOADS[args.workload]
+    if args.n:
+        w = synth.small(w, args.n, w.n_queries)
+    if args.nq:
+        w = w.with_(n_queries=args.nq)
+    return w
+
+
+def cache_paths(args, w):
+    c = pathlib.Path(args.cache)
+    c.mkdir(parents=True, exist_ok=True)
+    tag = f"{w.name}-n{w.n}-R{w.degree}-it{args.build_iters}-ef{args.ef_build}"
+    return c / f"{tag}.sqg", c / f"{tag}-gt-q{w.n_queries}"
+
+
+def ensure_index(args, w, device, rank):
+    """Build the index once (Algorithm 2 on the GPU) and the exact ground
+    truth; cached on disk for the other ranks and later runs."""
+    from paper_2411_12229_gb300 import eval as E
+    from paper_2411_12229_gb300 import index_builder as ib
+    idx, gtp = cache_paths(args, w)
+    if rank == 0 and not idx.exists():
+        t = time.time()
+        base = synth.base(w)
+        log(f"building {idx.name}: n={w.n} d={w.d} R={w.degree}")
+        info = ib.build_index(str(idx) + ".part", base, w.degree, device=device, init="random",
+                              iterations=args.build_iters, ef_build=args.ef_build, cand_k=2 * w.degree, log=log)
+        os.replace(str(idx) + ".part", idx)
+        log(f"built in {time.time() - t:.1f}s {info['iterations'][-1]}")
+    return idx, gtp
+
+
+def ground_truth(args, w, gtp, queries, device, world):
+    from paper_2411_12229_gb300 import eval as E
+    f = pathlib.Path(f"{gtp}-w{world}.npz")
+    if f.exists():
+        z = np.load(f)
+        return z["ids"], z["dists"]
+    t = time.time()
+    ids, dd = E.ground_truth(synth.base(w), queries, 100 if w.mixed_k else 10, device=device)
+    np.savez(f, ids=ids, dists=dd)
+    log(f"ground truth in {time.time() - t:.1f}s")
+    return ids, dd
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={device}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in pathlib.Path(self.f.name).read_text().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_digest() -> str:
+    h = hashlib.sha256()
+    for p in sorted((ROOT / "paper_2411_12229_gb300" / "csrc").glob("search*")):
+        h.update(p.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        z = json.loads(p.read_text())
+        return float(z["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record(workload_name):
+    """DRAM bytes per launch of the search kernel from a committed ncu
+    summary, used only while the kernel source is unchanged since."""
+    p = ROOT / "profiles" / "search_kernel_traffic.json"
+    if not p.exists():
+        return None
+    z = json.loads(p.read_text())
+    if z.get("kernel_digest") != kernel_digest() or z.get("workload") != workload_name:
+        return None
+    return z
+
+
+def run_oracle(idx_path, queries, k, ef, seconds, threads, max_queries):
+    """The oracle as it stands, one query per task on `threads` host
+    threads (ctypes releases the GIL), for about `seconds`."""
+    from oracle import oracle
+    O = oracle.Index(idx_path)
+    done, ids = 0, {}
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        it = iter(range(min(max_queries, queries.shape[0])))
+        futs = {}
+        for _ in range(threads * 2):
+            i = next(it, None)
+            if i is not None:
+                futs[ex.submit(O.search, queries[i], k, ef)] = i
+        while futs:
+            fin, _ = cf.wait(futs, return_when=cf.FIRST_COMPLETED)
+            for f in fin:
+                ids[futs.pop(f)] = f.result()[0]
+                done += 1
+                if time.perf_counter() - t0 < seconds:
+                    i = next(it, None)
+                    if i is not None:
+                        futs[ex.submit(O.search, queries[i], k, ef)] = i
+    el = time.perf_counter() - t0
+    O.close()
+    return done, el, ids
+
+
+def bench_reference(args):
+    """CPU oracle arm: same metric and workload, bounded samples per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args)
+    import torch
+    dev = 0 if torch.cuda.is_available() else None
+    idx, gtp = ensure_index(args, w, dev, 0)
+    q = synth.queries(w)
+    gt_ids, _ = ground_truth(args, w, gtp, q, dev, 1)
+    threads = os.cpu_count() or 1
+    # the smallest ef whose recall on a 200-query sample reaches the target
+    ef_sel, sweep = None, []
+    for ef in w.ef:
+        done, el, ids = run_oracle(idx, q, 10, ef, 1e9, threads, 200)
+        r = float(np.mean([len(set(ids[i].tolist()) & set(gt_ids[i][:10].tolist())) / 10 for i in ids]))
+        sweep.append({"ef": ef, "recall": r, "qps": done / el})
+        if r >= args.target:
+            ef_sel = ef
+            break
+    ef_sel = ef_sel or w.ef[-1]
+    per_step = max(threads * 2, 64)
+    for _ in range(args.warmup):
+        run_oracle(idx, q, 10, ef_sel, 1e9, threads, threads)
+    tot_q, tot_t = 0, 0.0
+    for s in range(args.steps):
+        qs = q[(s * per_step) % q.shape[0]:][:per_step]
+        done, el, _ = run_oracle(idx, qs, 10, ef_sel, 1e9, threads, per_step)
+        tot_q += done
+        tot_t += el
+    v = tot_q / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "d": w.d, "degree": w.degree, "k": 10, "ef": ef_sel,
+                       "queries_per_step": per_step, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} queries per step of the {w.n_queries}-query batch at ef={ef_sel}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sweep": sweep}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return bench_reference(args)
+    import torch
+
+    from paper_2411_12229_gb300 import build as build_mod
+    build_mod.build()
+    from paper_2411_12229_gb300 import eval as E
+    from paper_2411_12229_gb300.api import Index
+
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload(args)
+    idx, gtp = ensure_index(args, w, local, rank)
+    if dist:
+        dist.barrier()
+    # each rank serves its own query batch (replicas, weak scaling)
+    allq = synth.queries(w, w.n_queries * world)
+    q = np.ascontiguousarray(allq[rank * w.n_queries:(rank + 1) * w.n_queries])
+    gt_ids, gt_d = ground_truth(args, w, f"{gtp}-r{rank}", q, local, world)
+    ix = Index(idx, local)
+    qd = torch.from_numpy(q).cuda()
+    k = 10
+    nq = q.shape[0]
+
+    # ---- sweep (untimed for the metric): recall, hops and QPS per ef
+    sweep = []
+    for ef in w.ef:
+        ids, dists, st = ix.search(qd, k, ef, stats=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            ix.search(qd, k, ef)
+        e1.record()
+        torch.cuda.synchronize()
+        rec = E.recall(ids.cpu().numpy(), gt_ids, k)
+        sweep.append({"ef": ef, "recall": round(rec, 4), "qps": round(3 * nq / (e0.elapsed_time(e1) / 1e3)),
+                      "hops": round(float(st[:, 0].float().mean()), 1)})
+        if rank == 0:
+            log(f"ef={ef} recall@10={rec:.4f} hops={sweep[-1]['hops']} qps~{sweep[-1]['qps']}")
+        if rec >= 0.995:
+            break
+    pick = lambda t: next((s["ef"] for s in sweep if s["recall"] >= t), None)  # noqa: E731
+    ef_sel = pick(args.target) or sweep[-1]["ef"]
+    if dist:
+        t = torch.tensor([ef_sel], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ef_sel = int(t.item())
+
+    # ---- timed steps
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = (torch.empty(nq * k, dtype=torch.int32, device="cuda"), torch.empty(nq * k, device="cuda"))
+    st = None
+    for _ in range(max(3, args.warmup)):
+        ix.search(qd, k, ef_sel, out=out)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in kev:  # create the underlying CUDA events
+        a.record()
+        b.record()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.zero_()
+        ev[s][0].record()
+        _, _, st = ix.search(qd, k, ef_sel, out=out, stats=True, timing_events=kev[s])
+        ev[s][1].record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    # ---- end to end through host buffers
+    qh = torch.from_numpy(q).pin_memory()
+    ih = torch.empty((nq, k), dtype=torch.int32).pin_memory()
+    dh = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for s in range(args.warmup + args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        qdev = qh.to("cuda", non_blocking=True)
+        ids2, d2 = ix.search(qdev, k, ef_sel)
+        ih.copy_(ids2, non_blocking=True)
+        dh.copy_(d2, non_blocking=True)
+        b.record()
+        b.synchronize()
+        if s >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    rec_sel = E.recall(out[0].view(nq, k).cpu().numpy(), gt_ids, k)
+    rec_e2e = E.recall(ih.numpy(), gt_ids, k)
+    hops = st[:, 0].double().cpu().numpy()
+
+    step_mean = float(np.mean(step_ms))
+    t_local = torch.tensor([step_mean, float(np.mean(e2e_ms))], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    step_max, e2e_max = float(t_local[0]), float(t_local[1])
+    value = world * nq / (step_max / 1e3)
+    e2e_value = world * nq / (e2e_max / 1e3)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the search kernel: algorithmic bytes / its event time
+    bb = ix.block_bytes
+    alg_bytes = float(hops.sum() * bb + nq * (4 * w.d + 8 * k))
+    kern_mean = float(np.mean(kern_ms))
+    achieved = alg_bytes / (kern_mean / 1e3) / 1e9
+    peak, peak_src = measured_peaks()
+    tr = traffic_record(w.name)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": round(kern_mean, 4),
+                "kernel": "sqg::search_kernel"}
+
+    cpu = None
+    if world == 1 and not args.skip_cpu:
+        threads = os.cpu_count() or 1
+        done, el, ids_o = run_oracle(idx, q, k, ef_sel, args.cpu_seconds, threads, nq)
+        cpu = {"value": round(done / el, 2), "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {done} of the {nq} queries at ef={ef_sel}, {el:.1f}s on {threads} threads"}
+        same = sum(np.array_equal(ids_o[i], out[0].view(nq, k)[i].cpu().numpy().view(np.uint32)) for i in ids_o)
+        cpu["ids_identical_to_gpu"] = f"{same}/{len(ids_o)}"
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_max, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "d": w.d, "degree": w.degree, "k": k, "ef": ef_sel,
+                   "queries_per_step": nq, "recall@10": round(rec_sel, 4), "parallelism": f"replicas{world}",
+                   "l2": "flushed (512 MiB write) between timed steps"},
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(nq * w.d * 4),
+                "d2h_bytes_per_step": int(nq * k * 8), "recall@10": round(rec_e2e, 4)},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+        "qps_at_recall": {str(t): next((s["qps"] for s in sweep if s["recall"] >= t), None)
+                          for t in (0.90, 0.95, 0.99)},
+        "ef_at_recall": {str(t): pick(t) for t in (0.90, 0.95, 0.99)},
+        "hops_mean": round(float(hops.mean()), 2),
+        "sweep": sweep,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -89,6 +89,8 @@ typedef struct {
     int32_t stop_every;      /* evaluate the stop every this many expansions (>= 1) */
     int32_t team;            /* lanes per query: 32 (default, 0) or 16 */
     int32_t warps_per_block; /* 0 = library default */
+    void *timing_events[2];  /* optional cudaEvent_t pair recorded on the stream right before
+                                and right after the search kernel; NULL = none */
 } sqg_search_params;
 
 typedef struct {

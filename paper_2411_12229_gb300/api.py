@@ -1,0 +1,201 @@
+"""Python face of libsqg: a thin wrapper over the C ABI (include/sqg.h).
+
+Device memory and streams come from PyTorch; every step of the search runs
+in the library's kernels.  Tensors are passed by ``data_ptr()`` and the
+current CUDA stream is used unless one is given.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import _binding as B
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _i32(x, nq: int, device) -> torch.Tensor:
+    if isinstance(x, torch.Tensor):
+        t = x.to(device=device, dtype=torch.int32).contiguous()
+    else:
+        t = torch.as_tensor(np.broadcast_to(np.asarray(x, dtype=np.int32), (nq,)).copy(), device=device)
+    if t.numel() != nq:
+        raise ValueError(f"expected {nq} values, got {t.numel()}")
+    return t
+
+
+class Index:
+    """A SymphonyQG index resident on one GPU (sqg_index_load)."""
+
+    def __init__(self, path: str | os.PathLike, device: int | None = None):
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        h = C.c_void_p()
+        B.check(B.lib().sqg_index_load(str(path).encode(), self.device, C.byref(h)), f"sqg_index_load({path})")
+        self._h = h
+        info = B.Info()
+        B.check(B.lib().sqg_index_info(h, C.byref(info)), "sqg_index_info")
+        self.n, self.d, self.degree = int(info.n), int(info.d), int(info.degree)
+        self.block_bytes, self.entry = int(info.block_bytes), int(info.entry)
+        self.device_bytes = int(info.device_bytes)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            B.lib().sqg_index_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> C.c_void_p:
+        return self._h
+
+    # ------------------------------------------------------------------ search
+    def params(self, *, eps0: float = 0.0, multi_estimate: bool = True, hop_cap: int = 0, max_k: int = 0,
+               max_ef: int = 0, stop_mlp: torch.Tensor | None = None, stop_logit: float = 0.0,
+               stop_every: int = 1, warps_per_block: int = 0, timing_events=None) -> B.SearchParams:
+        p = B.SearchParams()
+        p.eps0 = float(eps0)
+        p.multi_estimate = 1 if multi_estimate else 0
+        p.hop_cap = int(hop_cap)
+        p.max_k, p.max_ef = int(max_k), int(max_ef)
+        if stop_mlp is not None:
+            if stop_mlp.dtype != torch.float32 or not stop_mlp.is_cuda or stop_mlp.numel() != B.MLP_NPARAM:
+                raise ValueError("stop_mlp must be a CUDA float32 tensor of 5313 parameters")
+            p.stop_mlp = stop_mlp.data_ptr()
+        p.stop_logit = float(stop_logit)
+        p.stop_every = int(stop_every)
+        p.warps_per_block = int(warps_per_block)
+        if timing_events is not None:  # torch.cuda.Event pair, already recorded once
+            p.timing_events[0] = timing_events[0].cuda_event
+            p.timing_events[1] = timing_events[1].cuda_event
+        return p
+
+    def search(self, queries: torch.Tensor, k, ef, *, out: tuple | None = None, stats: bool = False,
+               workspace: torch.Tensor | None = None, stream=None, **kw):
+        """Search a batch (Algorithm 1 per query).
+
+        queries: (nq, d) float32 CUDA tensor.  k, ef: ints or (nq,) tensors.
+        Returns (ids int32, dists float32): shape (nq, k) when k is one int,
+        else flat ragged arrays (query i at offset sum_{j<i} k[j]).  Padding
+        is id -1 with distance +inf.  With stats=True also returns an
+        (nq, 2) int32 tensor of (hops, status bits)."""
+        if queries.dtype != torch.float32 or not queries.is_cuda or queries.dim() != 2 or queries.shape[1] != self.d:
+            raise ValueError(f"queries must be a CUDA float32 tensor of shape (nq, {self.d})")
+        queries = queries.contiguous()
+        nq, dev = queries.shape[0], queries.device
+        kt, et = _i32(k, nq, dev), _i32(ef, nq, dev)
+        uniform = not isinstance(k, torch.Tensor) and np.ndim(k) == 0
+        total = int(k) * nq if uniform else int(kt.clamp(0, B.MAX_K).sum().item())
+        if out is None:
+            ids = torch.empty(total, dtype=torch.int32, device=dev)
+            dists = torch.empty(total, dtype=torch.float32, device=dev)
+        else:
+            ids, dists = out
+        st = torch.empty((nq, 2), dtype=torch.int32, device=dev) if stats else None
+        p = self.params(**kw)
+        if uniform and p.max_k == 0:
+            p.max_k = int(k)
+        if not isinstance(ef, torch.Tensor) and np.ndim(ef) == 0 and p.max_ef == 0:
+            p.max_ef = int(ef)
+        ws_ptr, ws_bytes = (workspace.data_ptr(), workspace.numel() * workspace.element_size()) \
+            if workspace is not None else (None, 0)
+        rc = B.lib().sqg_search_ex(self._h, queries.data_ptr(), nq, kt.data_ptr(), et.data_ptr(), ids.data_ptr(),
+                                   dists.data_ptr(), C.byref(p), ws_ptr, ws_bytes,
+                                   st.data_ptr() if st is not None else None, _stream_ptr(stream))
+        B.check(rc, "sqg_search_ex")
+        if uniform:
+            ids, dists = ids.view(nq, int(k)), dists.view(nq, int(k))
+        return (ids, dists, st) if stats else (ids, dists)
+
+    def search_plain(self, queries: torch.Tensor, k: torch.Tensor, ef: torch.Tensor, out_ids: torch.Tensor,
+                     out_dists: torch.Tensor, stream=None) -> None:
+        """sqg_search exactly as the C ABI gives it (device k[], ef[])."""
+        rc = B.lib().sqg_search(self._h, queries.data_ptr(), queries.shape[0], k.data_ptr(), ef.data_ptr(),
+                                out_ids.data_ptr(), out_dists.data_ptr(), _stream_ptr(stream))
+        B.check(rc, "sqg_search")
+
+    def search_trace(self, queries: torch.Tensor, k: int, ef: int, gt: torch.Tensor | None, trace_cap: int,
+                     stream=None, **kw):
+        """Search that records the learned stop's features (and hits against
+        gt) at every evaluation point.  Returns ids, dists, stats, feats
+        (nq, cap, 16), hits (nq, cap), counts (nq,)."""
+        nq, dev = queries.shape[0], queries.device
+        kt, et = _i32(k, nq, dev), _i32(ef, nq, dev)
+        ids = torch.empty(nq * k, dtype=torch.int32, device=dev)
+        dists = torch.empty(nq * k, dtype=torch.float32, device=dev)
+        st = torch.empty((nq, 2), dtype=torch.int32, device=dev)
+        feats = torch.zeros((nq, trace_cap, B.MLP_IN), dtype=torch.float32, device=dev)
+        hits = torch.full((nq, trace_cap), -1, dtype=torch.int32, device=dev)
+        cnt = torch.zeros(nq, dtype=torch.int32, device=dev)
+        p = self.params(max_k=k, max_ef=ef, **kw)
+        gtp, gtk = (gt.data_ptr(), gt.shape[1]) if gt is not None else (None, 0)
+        rc = B.lib().sqg_search_trace(self._h, queries.contiguous().data_ptr(), nq, kt.data_ptr(), et.data_ptr(),
+                                      ids.data_ptr(), dists.data_ptr(), C.byref(p), st.data_ptr(), gtp, gtk,
+                                      feats.data_ptr(), hits.data_ptr(), cnt.data_ptr(), trace_cap,
+                                      _stream_ptr(stream))
+        B.check(rc, "sqg_search_trace")
+        return ids.view(nq, k), dists.view(nq, k), st, feats, hits, cnt
+
+    def workspace_size(self, nq: int, max_k: int, max_ef: int) -> int:
+        n = B.lib().sqg_workspace_size(self._h, nq, max_k, max_ef)
+        if n == 0:
+            raise B.SqgError(-1, "sqg_workspace_size")
+        return int(n)
+
+    def search_host(self, queries: np.ndarray, k: int, ef: int, *, pinned: tuple | None = None, **kw):
+        """End-to-end search from HOST arrays: copy the queries in, search,
+        copy (ids, dists) back; returns numpy arrays."""
+        nq = queries.shape[0]
+        dev = torch.device("cuda", self.device)
+        if pinned is None:
+            qh = torch.from_numpy(np.ascontiguousarray(queries, dtype=np.float32)).pin_memory()
+            ih = torch.empty((nq, k), dtype=torch.int32).pin_memory()
+            dh = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+        else:
+            qh, ih, dh = pinned
+        qd = qh.to(dev, non_blocking=True)
+        ids, dists = self.search(qd, k, ef, **kw)
+        ih.copy_(ids, non_blocking=True)
+        dh.copy_(dists, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return ih.numpy(), dh.numpy()
+
+    # ------------------------------------------------------------------ test hooks
+    def prepare_queries(self, queries: torch.Tensor, stream=None):
+        nq = queries.shape[0]
+        dev = queries.device
+        qrot = torch.empty((nq, self.d), dtype=torch.float32, device=dev)
+        planes = torch.empty((nq, 4, self.d // 32), dtype=torch.int32, device=dev)
+        scal = torch.empty((nq, 4), dtype=torch.float32, device=dev)
+        B.check(B.lib().sqg_prepare_queries(self._h, queries.contiguous().data_ptr(), nq, qrot.data_ptr(),
+                                            planes.data_ptr(), scal.data_ptr(), _stream_ptr(stream)),
+                "sqg_prepare_queries")
+        return qrot, planes, scal
+
+    def estimate_block(self, queries: torch.Tensor, v: torch.Tensor, eps0: float = 0.0, stream=None):
+        nq, dev, R = queries.shape[0], queries.device, self.degree
+        S = torch.empty((nq, R), dtype=torch.int32, device=dev)
+        est = torch.empty((nq, R), dtype=torch.float32, device=dev)
+        key = torch.empty((nq, R), dtype=torch.float32, device=dev)
+        dc = torch.empty(nq, dtype=torch.float32, device=dev)
+        vv = v.to(device=dev, dtype=torch.int32).contiguous()
+        B.check(B.lib().sqg_estimate_block(self._h, queries.contiguous().data_ptr(), nq, vv.data_ptr(), eps0,
+                                           S.data_ptr(), est.data_ptr(), key.data_ptr(), dc.data_ptr(),
+                                           _stream_ptr(stream)), "sqg_estimate_block")
+        return S, est, key, dc
+
+    def status(self, stream=None) -> int:
+        s = C.c_uint32()
+        B.check(B.lib().sqg_get_status(self._h, _stream_ptr(stream), C.byref(s)), "sqg_get_status")
+        return int(s.value)

@@ -1,0 +1,716 @@
+// search.cuh -- device code of the SymphonyQG query phase for sm_103a.
+//
+// One warp serves one query at a time and pulls the next query index from a
+// device work queue (persistent kernel).  Per query it runs Algorithm 1
+// (Querying, Sec. 3.1.3) with multiple estimated distances and implicit
+// re-ranking (Sec. 3.1.2):
+//
+//   select   the first unvisited beam entry (beam sorted by (key, id));
+//   fetch    the vertex's block -- raw vector, neighbour codes and factors,
+//            neighbour ids (Sec. 3.1.3) -- by one 1-D bulk copy
+//            (cp.async.bulk) into shared memory; the NEXT vertex's block is
+//            copied while the current one is merged (memory prefetching,
+//            Sec. 3.1.4), into the other of two buffers;
+//   exact    the squared distance from the raw vector updates the result
+//            set (implicit re-ranking);
+//   estimate every neighbour's distance: S = sum_i b_i qbar_i by AND +
+//            __popc against 4 bit-planes of the quantized rotated query,
+//            est = f_add + dist_c + f_rescale * ip (Eq. (2) with Eq. (5)-(6));
+//   admit    every unvisited neighbour enters the beam, duplicates of an id
+//            included, and the beam is cut to ef (Algorithm 1, line 6).
+//
+// Float decisions follow a fixed operation order (explicit __f*_rn
+// intrinsics; the file is built with -fmad=false), so that the CPU oracle
+// can take the same decisions bit for bit.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sqg.h"
+
+namespace sqg {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kVisited = 0x80000000u;
+constexpr uint32_t kIdMask = 0x7FFFFFFFu;
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s per bounded wait
+
+struct SearchArgs {
+    const unsigned char *blocks;
+    uint32_t block_bytes, n, d, R, entry;
+    uint32_t off_codes, off_factors, off_ids;
+    const float *queries;  // nq x d
+    const float *qrot;     // nq x d, P^-1 q
+    int nq;
+    const int32_t *k, *ef;
+    const long long *offsets;  // nq: output offset of each query
+    uint32_t *out_ids;
+    float *out_dists;
+    sqg_query_stats *stats;  // nq or null
+    uint32_t *status_word;   // OR of all status bits
+    unsigned int *queue_head;
+    int max_k, max_ef, hop_cap;
+    uint32_t hash_bits;
+    uint32_t *ghash;  // per-warp hash tables in global memory, or null (shared)
+    float eps0;
+    int multi_estimate;
+    const float *mlp;
+    float stop_logit;
+    int stop_every;
+    float *trace_feat;  // nq x trace_cap x 16, or null
+    int32_t *trace_hit; // nq x trace_cap
+    int32_t *trace_n;   // nq
+    int trace_cap;
+    const uint32_t *gt; // nq x gt_k ground-truth ids (trace mode)
+    int gt_k;
+    uint32_t warp_bytes, cta_bytes;
+    uint32_t o_buf0, o_buf1, o_bar, o_pkey, o_pid, o_hash, o_rkey, o_rid, o_planes;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Lane 0 only: arm the barrier for `bytes` and start the 1-D bulk copy.
+__device__ __forceinline__ void bulk_fetch(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for phase `parity` of `bar`; false on timeout (never hangs).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+// ---------------------------------------------------------------- ordering
+__device__ __forceinline__ bool kless(float ka, uint32_t ia, float kb, uint32_t ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+// ---------------------------------------------------------------- hash set
+__device__ __forceinline__ uint32_t hslot(uint32_t id, uint32_t bits) { return (id * 0x9E3779B1u) >> (32 - bits); }
+__device__ __forceinline__ void hash_insert(uint32_t *H, uint32_t bits, uint32_t id) {
+    const uint32_t mask = (1u << bits) - 1u;
+    uint32_t s = hslot(id, bits);
+    for (;;) {
+        uint32_t v = H[s];
+        if (v == id) return;
+        if (v == kEmpty) { H[s] = id; return; }
+        s = (s + 1) & mask;
+    }
+}
+__device__ __forceinline__ bool hash_contains(const uint32_t *H, uint32_t bits, uint32_t id) {
+    const uint32_t mask = (1u << bits) - 1u;
+    uint32_t s = hslot(id, bits);
+    for (;;) {
+        uint32_t v = H[s];
+        if (v == id) return true;
+        if (v == kEmpty) return false;
+        s = (s + 1) & mask;
+    }
+}
+
+// ---------------------------------------------------------------- query side
+// 4-bit uniform quantization of q' = P^-1 q over [v_l, v_r] (Sec. 3.1.1 with
+// the 4-bit reading): qbar_i = min(15, trunc((q'_i - v_l)*15/(v_r-v_l) + 0.5));
+// bit b of every qbar_i is packed into plane b by a warp ballot.
+struct QuerySide {
+    float vl, delta, inv_sqrt_d;
+    int sq;
+};
+__device__ __forceinline__ QuerySide quantize_warp(const float *qr, uint32_t d, uint32_t *planes, int lane) {
+    const uint32_t nw = d / 32;
+    float vl = qr[lane], vr = qr[lane];
+    for (uint32_t w = 1; w < nw; ++w) {
+        float x = qr[w * 32 + lane];
+        vl = x < vl ? x : vl;
+        vr = x > vr ? x : vr;
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        float a = __shfl_xor_sync(kFull, vl, o), b = __shfl_xor_sync(kFull, vr, o);
+        vl = a < vl ? a : vl;
+        vr = b > vr ? b : vr;
+    }
+    const float range = __fsub_rn(vr, vl);
+    QuerySide qs;
+    qs.vl = vl;
+    qs.delta = range > 0.0f ? __fdiv_rn(range, 15.0f) : 0.0f;
+    const float inv = range > 0.0f ? __fdiv_rn(15.0f, range) : 0.0f;
+    qs.inv_sqrt_d = __fdiv_rn(1.0f, __fsqrt_rn((float)d));
+    int sq = 0;
+    for (uint32_t w = 0; w < nw; ++w) {
+        int t = 0;
+        if (range > 0.0f) {
+            float x = __fsub_rn(qr[w * 32 + lane], vl);
+            x = __fmul_rn(x, inv);
+            x = __fadd_rn(x, 0.5f);
+            t = __float2int_rz(x);
+            t = t > 15 ? 15 : t;
+        }
+        sq += t;
+        uint32_t b0 = __ballot_sync(kFull, t & 1), b1 = __ballot_sync(kFull, t & 2);
+        uint32_t b2 = __ballot_sync(kFull, t & 4), b3 = __ballot_sync(kFull, t & 8);
+        if (lane == 0) {
+            planes[w] = b0;
+            planes[nw + w] = b1;
+            planes[2 * nw + w] = b2;
+            planes[3 * nw + w] = b3;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) sq += __shfl_xor_sync(kFull, sq, o);
+    qs.sq = sq;
+    return qs;
+}
+
+// Exact squared distance in the canonical order: lane l sums float4 chunks
+// l, l+32, ... (x, y, z, w; fmaf(d, d, acc) from 0), then an xor butterfly.
+template <int CH>
+__device__ __forceinline__ float exact_dist(const float4 (&qv)[CH], const float *raw, uint32_t nch, int lane) {
+    float acc = 0.0f;
+    const float4 *r4 = reinterpret_cast<const float4 *>(raw);
+#pragma unroll
+    for (int t = 0; t < CH; ++t) {
+        uint32_t c = lane + 32 * t;
+        if (c < nch) {
+            float4 x = r4[c];
+            float dx = __fsub_rn(qv[t].x, x.x), dy = __fsub_rn(qv[t].y, x.y);
+            float dz = __fsub_rn(qv[t].z, x.z), dw = __fsub_rn(qv[t].w, x.w);
+            acc = __fmaf_rn(dx, dx, acc);
+            acc = __fmaf_rn(dy, dy, acc);
+            acc = __fmaf_rn(dz, dz, acc);
+            acc = __fmaf_rn(dw, dw, acc);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(kFull, acc, o));
+    return acc;
+}
+
+// RaBitQ estimate of neighbour j from its block (Sec. 3.1.1):
+// S = sum_b 2^b popc(code & plane_b); ip = fmaf(delta, 2S-Sq, v_l(2pc-d))/sqrt(d);
+// est = fmaf(f_rescale, ip, f_add + dist_c); key = est - eps0 * f_err sqrt(dist_c).
+struct Est {
+    int S;
+    float est, key;
+};
+__device__ __forceinline__ Est estimate(const unsigned char *blk, const SearchArgs &a, const uint32_t *planes,
+                                        const QuerySide &qs, uint32_t j, float dist_c) {
+    const uint32_t nw = a.d / 32, R = a.R;
+    const uint32_t *codes = reinterpret_cast<const uint32_t *>(blk + a.off_codes) + j;
+    int s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll 4
+    for (uint32_t w = 0; w < nw; ++w) {
+        uint32_t c = codes[w * R];
+        s0 += __popc(c & planes[w]);
+        s1 += __popc(c & planes[nw + w]);
+        s2 += __popc(c & planes[2 * nw + w]);
+        s3 += __popc(c & planes[3 * nw + w]);
+    }
+    const int S = s0 + 2 * s1 + 4 * s2 + 8 * s3;
+    const float *fac = reinterpret_cast<const float *>(blk + a.off_factors);
+    const float f_add = fac[j], f_rescale = fac[R + j], f_err = fac[2 * R + j];
+    const int pc = (int)reinterpret_cast<const uint32_t *>(fac)[3 * R + j];
+    const float A = (float)(2 * S - qs.sq);
+    const float B = __fmul_rn(qs.vl, (float)(2 * pc - (int)a.d));
+    const float ip = __fmul_rn(__fmaf_rn(qs.delta, A, B), qs.inv_sqrt_d);
+    Est e;
+    e.S = S;
+    e.est = __fmaf_rn(f_rescale, ip, __fadd_rn(f_add, dist_c));
+    const float bound = __fmul_rn(f_err, __fsqrt_rn(dist_c));
+    e.key = __fsub_rn(e.est, __fmul_rn(a.eps0, bound));
+    return e;
+}
+
+// ---------------------------------------------------------------- learned stop
+// Features of the search state (all IEEE +,-,*,/ so both sides agree).
+struct StopState {
+    int hops, last_improve, inserted_last;
+    float ema_improve, ema_insert, dist_c;
+};
+__device__ __forceinline__ float clamp8(float x) { return x < -8.0f ? -8.0f : (x > 8.0f ? 8.0f : x); }
+
+// MLP 16 -> 64 -> 64 -> 1 on one warp; weights in shared memory, layer
+// matrices stored transposed ([in][out]) for conflict-free reads.  Hidden
+// neuron o is an fmaf chain over its inputs in order starting from its bias;
+// the output adds p_l = fmaf(W3[l+32], h[l+32], W3[l] h[l]) by xor butterfly,
+// then b3.
+__device__ __forceinline__ float mlp_logit_warp(const float *w, const float (&f)[SQG_MLP_IN], int lane) {
+    const float *W1t = w;                         // [16][64]
+    const float *b1 = W1t + SQG_MLP_IN * 64;      // [64]
+    const float *W2t = b1 + 64;                   // [64][64]
+    const float *b2 = W2t + 64 * 64;              // [64]
+    const float *W3 = b2 + 64;                    // [64]
+    const float *b3 = W3 + 64;                    // [1]
+    float ha = b1[lane], hb = b1[lane + 32];
+#pragma unroll
+    for (int i = 0; i < SQG_MLP_IN; ++i) {
+        ha = __fmaf_rn(W1t[i * 64 + lane], f[i], ha);
+        hb = __fmaf_rn(W1t[i * 64 + lane + 32], f[i], hb);
+    }
+    ha = ha > 0.0f ? ha : 0.0f;
+    hb = hb > 0.0f ? hb : 0.0f;
+    float ga = b2[lane], gb = b2[lane + 32];
+#pragma unroll 8
+    for (int i = 0; i < 64; ++i) {
+        float hi = __shfl_sync(kFull, i < 32 ? ha : hb, i & 31);
+        ga = __fmaf_rn(W2t[i * 64 + lane], hi, ga);
+        gb = __fmaf_rn(W2t[i * 64 + lane + 32], hi, gb);
+    }
+    ga = ga > 0.0f ? ga : 0.0f;
+    gb = gb > 0.0f ? gb : 0.0f;
+    float p = __fmaf_rn(W3[lane + 32], gb, __fmul_rn(W3[lane], ga));
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) p = __fadd_rn(p, __shfl_xor_sync(kFull, p, o));
+    return __fadd_rn(p, b3[0]);
+}
+
+// ---------------------------------------------------------------- the kernel
+template <int CH, int NB>
+__global__ void __launch_bounds__(128, 1) search_kernel(const SearchArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t R = a.R, d = a.d, nch = d / 4, nw = d / 32;
+
+    float *wts = reinterpret_cast<float *>(smem);
+    if (a.mlp) {  // transpose W1, W2 into [in][out]
+        const float *W1 = a.mlp, *b1 = W1 + 64 * SQG_MLP_IN, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64;
+        for (int i = threadIdx.x; i < 64 * SQG_MLP_IN; i += blockDim.x) {
+            int o = i / SQG_MLP_IN, c = i % SQG_MLP_IN;
+            wts[c * 64 + o] = W1[i];
+        }
+        float *q = wts + 64 * SQG_MLP_IN;
+        for (int i = threadIdx.x; i < 64; i += blockDim.x) q[i] = b1[i];
+        q += 64;
+        for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+            int o = i / 64, c = i % 64;
+            q[c * 64 + o] = W2[i];
+        }
+        q += 64 * 64;
+        for (int i = threadIdx.x; i < 64; i += blockDim.x) q[i] = b2[i];
+        q += 64;
+        for (int i = threadIdx.x; i < 65; i += blockDim.x) q[i] = W3[i];  // W3 and b3
+    }
+    __syncthreads();
+
+    unsigned char *ws = smem + a.cta_bytes + (size_t)warp * a.warp_bytes;
+    unsigned char *buf[2] = {ws + a.o_buf0, ws + a.o_buf1};
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ws + a.o_bar);
+    float *pkey = reinterpret_cast<float *>(ws + a.o_pkey);
+    uint32_t *pid = reinterpret_cast<uint32_t *>(ws + a.o_pid);
+    float *rkey = reinterpret_cast<float *>(ws + a.o_rkey);
+    uint32_t *rid = reinterpret_cast<uint32_t *>(ws + a.o_rid);
+    uint32_t *planes = reinterpret_cast<uint32_t *>(ws + a.o_planes);
+    const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
+    uint32_t *H = a.ghash ? a.ghash + ((size_t)gwarp << a.hash_bits) : reinterpret_cast<uint32_t *>(ws + a.o_hash);
+    const uint32_t hsize = 1u << a.hash_bits;
+
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    fence_mbar_init();
+    __syncwarp();
+    uint32_t phase = 0;     // bit b: parity of the next completion of bar[b]
+    bool healthy = true;    // false after an unrecovered copy timeout
+
+    while (healthy) {
+        int qi = 0;
+        if (lane == 0) qi = (int)atomicAdd(a.queue_head, 1u);
+        qi = __shfl_sync(kFull, qi, 0);
+        if (qi >= a.nq) break;
+
+        const int k = a.k[qi], ef = a.ef[qi];
+        const long long off = a.offsets[qi];
+        uint32_t status = 0;
+        if (!(k >= 1 && k <= a.max_k && ef >= k && ef <= a.max_ef)) {
+            const int kk = k < 0 ? 0 : (k > SQG_MAX_K ? SQG_MAX_K : k);
+            for (int t = lane; t < kk; t += 32) {
+                a.out_ids[off + t] = SQG_NO_ID;
+                a.out_dists[off + t] = __int_as_float(0x7f800000);
+            }
+            if (lane == 0) {
+                if (a.stats) a.stats[qi] = sqg_query_stats{0u, SQG_STATUS_BAD_PARAM};
+                atomicOr(a.status_word, SQG_STATUS_BAD_PARAM);
+                if (a.trace_n) a.trace_n[qi] = 0;
+            }
+            continue;
+        }
+        const int hop_cap = a.hop_cap > 0 ? a.hop_cap : 8 * ef + 64;
+
+        // ---- query setup: raw query in registers, quantized rotated query planes
+        float4 qv[CH];
+        const float *q = a.queries + (size_t)qi * d;
+#pragma unroll
+        for (int t = 0; t < CH; ++t) {
+            uint32_t c = lane + 32 * t;
+            qv[t] = c < nch ? reinterpret_cast<const float4 *>(q)[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const QuerySide qs = quantize_warp(a.qrot + (size_t)qi * d, d, planes, lane);
+        for (uint32_t i = lane; i < hsize; i += 32) H[i] = kEmpty;
+
+        // ---- Algorithm 1, line 1: the beam and the result start from the entry
+        int m = 1, cur = 0, rc = 0;
+        if (lane == 0) {
+            pid[0] = a.entry;
+            pkey[0] = 0.0f;  // replaced by the entry's exact distance at its expansion
+        }
+        int cb = 0;                          // buffer holding the block to expand next
+        uint32_t pend = a.entry;             // id whose block is in flight into buf[cb]
+        bool inflight = true;
+        __syncwarp();
+        if (lane == 0) {
+            fence_proxy_async();
+            bulk_fetch(buf[0], a.blocks + (size_t)a.entry * a.block_bytes, a.block_bytes, &bar[0]);
+        }
+        StopState st{0, 0, 0, 0.0f, 0.0f, 0.0f};
+        int tn = 0;
+        int hops = 0;
+
+        while (cur < m) {
+            if (hops >= hop_cap) { status |= SQG_STATUS_CAPACITY; break; }
+            const uint32_t p = pid[cur] & kIdMask;
+            for (int i = cur + lane; i < m; i += 32)
+                if ((pid[i] & kIdMask) == p) pid[i] = p | kVisited;
+            if (lane == 0) hash_insert(H, a.hash_bits, p);
+            __syncwarp();
+            ++hops;
+            // next unvisited beam entry after cur
+            int nxt = m;
+            for (int base = cur + 1; base < m; base += 32) {
+                int i = base + lane;
+                uint32_t b = __ballot_sync(kFull, i < m && !(pid[i] & kVisited));
+                if (b) { nxt = base + __ffs(b) - 1; break; }
+            }
+            if (!inflight || pend != p) {  // the prefetch always targets p; kept as a safeguard
+                if (inflight) {
+                    if (!mbar_wait_bounded(&bar[cb], (phase >> cb) & 1u)) { status |= SQG_STATUS_TIMEOUT; healthy = false; break; }
+                    phase ^= 1u << cb;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    fence_proxy_async();
+                    bulk_fetch(buf[cb], a.blocks + (size_t)p * a.block_bytes, a.block_bytes, &bar[cb]);
+                }
+                pend = p;
+                inflight = true;
+            }
+            if (!mbar_wait_bounded(&bar[cb], (phase >> cb) & 1u)) {
+                status |= SQG_STATUS_TIMEOUT;
+                healthy = false;
+                break;
+            }
+            phase ^= 1u << cb;
+            inflight = false;
+            const unsigned char *blk = buf[cb];
+
+            // ---- line 4: exact distance, implicit re-ranking
+            const float dist_c = exact_dist<CH>(qv, reinterpret_cast<const float *>(blk), nch, lane);
+            if (hops == 1 && lane == 0) pkey[0] = dist_c;
+            bool improved = false;
+            {
+                const bool full = rc == k;
+                if (!full || kless(dist_c, p, rkey[k - 1], rid[k - 1])) {
+                    improved = true;
+                    int pos = 0;
+                    for (int base = 0; base < rc; base += 32) {
+                        int i = base + lane;
+                        pos += __popc(__ballot_sync(kFull, i < rc && kless(rkey[i], rid[i], dist_c, p)));
+                    }
+                    const int top = full ? k - 1 : rc;  // entries [pos, top) move up one
+                    for (int base = ((top - 1) & ~31); base >= (pos & ~31) && top > pos; base -= 32) {
+                        int i = base + lane;
+                        bool mv = i >= pos && i < top;
+                        float kk = mv ? rkey[i] : 0.0f;
+                        uint32_t ii = mv ? rid[i] : 0u;
+                        __syncwarp();
+                        if (mv) { rkey[i + 1] = kk; rid[i + 1] = ii; }
+                        __syncwarp();
+                    }
+                    if (lane == 0) { rkey[pos] = dist_c; rid[pos] = p; }
+                    rc = full ? k : rc + 1;
+                }
+            }
+
+            // ---- line 5: estimates for all R neighbours from the same block
+            const uint32_t *ids = reinterpret_cast<const uint32_t *>(blk + a.off_ids);
+            const bool full = m == ef;
+            const float wk = pkey[ef - 1 < m ? ef - 1 : 0];
+            const uint32_t wi = pid[ef - 1 < m ? ef - 1 : 0] & kIdMask;
+            float ck[NB];
+            uint32_t cid[NB];
+            int cpos[NB];
+            bool adm[NB];
+#pragma unroll
+            for (int t = 0; t < NB; ++t) {
+                const uint32_t j = lane + 32 * t;
+                cid[t] = ids[j];
+                const Est e = estimate(blk, a, planes, qs, j, dist_c);
+                ck[t] = e.key;
+                // line 6: only unvisited neighbours enter; an entry that the cut
+                // to ef would drop at once is skipped early
+                adm[t] = !full || kless(ck[t], cid[t], wk, wi);
+                if (adm[t]) adm[t] = !hash_contains(H, a.hash_bits, cid[t]);
+            }
+            if (!a.multi_estimate) {  // ablation w/o ME: skip ids already in the beam
+#pragma unroll
+                for (int t = 0; t < NB; ++t) {
+                    bool in = false;
+                    for (int i = 0; i < m && adm[t]; ++i) in |= (pid[i] & kIdMask) == cid[t];
+                    adm[t] = adm[t] && !in;
+                }
+            }
+            // position in the beam; an identical (key, id) already there is dropped
+#pragma unroll
+            for (int t = 0; t < NB; ++t) {
+                cpos[t] = 0;
+                if (adm[t]) {
+                    int lo = 0, hi = m;
+                    while (lo < hi) {
+                        int mid = (lo + hi) >> 1;
+                        if (kless(pkey[mid], pid[mid] & kIdMask, ck[t], cid[t])) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    cpos[t] = lo;
+                    if (lo < m && pkey[lo] == ck[t] && (pid[lo] & kIdMask) == cid[t]) adm[t] = false;
+                }
+            }
+            uint32_t am[NB];
+            int nadm = 0;
+#pragma unroll
+            for (int t = 0; t < NB; ++t) {
+                am[t] = __ballot_sync(kFull, adm[t]);
+                nadm += __popc(am[t]);
+            }
+            // rank among the admitted candidates (ids in a block are distinct)
+            int rank[NB];
+#pragma unroll
+            for (int t = 0; t < NB; ++t) rank[t] = 0;
+            float bk = __int_as_float(0x7f800000);
+            uint32_t bi = kEmpty;
+#pragma unroll
+            for (int t2 = 0; t2 < NB; ++t2) {
+                uint32_t mm = am[t2];
+                while (mm) {
+                    const int src = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const float ok = __shfl_sync(kFull, ck[t2], src);
+                    const uint32_t oi = __shfl_sync(kFull, cid[t2], src);
+#pragma unroll
+                    for (int t = 0; t < NB; ++t) rank[t] += kless(ok, oi, ck[t], cid[t]) ? 1 : 0;
+                    if (kless(ok, oi, bk, bi)) { bk = ok; bi = oi; }
+                }
+            }
+            // ---- memory prefetching (Sec. 3.1.4): the next vertex is the smaller
+            // of the first unvisited beam entry and the best admitted candidate
+            uint32_t next_id = kEmpty;
+            if (nxt < m) {
+                const float nk = pkey[nxt];
+                const uint32_t ni = pid[nxt] & kIdMask;
+                next_id = (nadm > 0 && kless(bk, bi, nk, ni)) ? bi : ni;
+            } else if (nadm > 0) {
+                next_id = bi;
+            }
+            __syncwarp();
+            if (next_id != kEmpty) {
+                const int nb = cb ^ 1;
+                if (lane == 0) {
+                    fence_proxy_async();
+                    bulk_fetch(buf[nb], a.blocks + (size_t)next_id * a.block_bytes, a.block_bytes, &bar[nb]);
+                }
+                cb = nb;
+                pend = next_id;
+                inflight = true;
+            }
+
+            // ---- line 6: merge the admitted candidates and cut the beam to ef
+            int inserted = 0;
+            if (nadm > 0) {
+                int minpos = m;
+#pragma unroll
+                for (int t = 0; t < NB; ++t)
+                    if (adm[t]) minpos = min(minpos, cpos[t]);
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) minpos = min(minpos, __shfl_xor_sync(kFull, minpos, o));
+                int nxt_shift = 0;
+                for (int base = ((m - 1) & ~31); base >= (minpos & ~31); base -= 32) {
+                    const int i = base + lane;
+                    const bool valid = i >= minpos && i < m;
+                    int cnt = 0;
+#pragma unroll
+                    for (int t2 = 0; t2 < NB; ++t2) {
+                        uint32_t mm = am[t2];
+                        while (mm) {
+                            const int src = __ffs(mm) - 1;
+                            mm &= mm - 1;
+                            cnt += __shfl_sync(kFull, cpos[t2], src) <= i ? 1 : 0;
+                        }
+                    }
+                    if (i == nxt) nxt_shift = cnt;
+                    const float kk = valid ? pkey[i] : 0.0f;
+                    const uint32_t ii = valid ? pid[i] : 0u;
+                    __syncwarp();
+                    if (valid && cnt > 0 && i + cnt < ef) { pkey[i + cnt] = kk; pid[i + cnt] = ii; }
+                    __syncwarp();
+                }
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) nxt_shift += __shfl_xor_sync(kFull, nxt_shift, o);
+                int newcur = m + nadm;  // "none"
+#pragma unroll
+                for (int t = 0; t < NB; ++t) {
+                    const int fp = cpos[t] + rank[t];
+                    const bool keep = adm[t] && fp < ef;
+                    if (keep) {
+                        pkey[fp] = ck[t];
+                        pid[fp] = cid[t];
+                        newcur = min(newcur, fp);
+                    }
+                    inserted += __popc(__ballot_sync(kFull, keep));
+                }
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) newcur = min(newcur, __shfl_xor_sync(kFull, newcur, o));
+                if (nxt < m && nxt >= minpos) {
+                    if (nxt + nxt_shift < ef) newcur = min(newcur, nxt + nxt_shift);
+                } else if (nxt < m) {
+                    newcur = min(newcur, nxt);
+                }
+                m = min(ef, m + nadm);
+                cur = newcur < m ? newcur : m;
+            } else {
+                cur = nxt;
+            }
+            __syncwarp();
+
+            // ---- learned early stop (not in the paper) / trace
+            st.hops = hops;
+            st.inserted_last = inserted;
+            st.dist_c = dist_c;
+            if (improved) st.last_improve = hops;
+            st.ema_improve = __fadd_rn(__fmul_rn(0.75f, st.ema_improve), __fmul_rn(0.25f, improved ? 1.0f : 0.0f));
+            st.ema_insert = __fadd_rn(__fmul_rn(0.75f, st.ema_insert),
+                                      __fmul_rn(0.25f, __fdiv_rn((float)inserted, (float)R)));
+            if ((a.mlp || a.trace_feat) && a.stop_every > 0 && hops % a.stop_every == 0 && rc == k) {
+                int u = 0;
+                for (int base = 0; base < m; base += 32) {
+                    int i = base + lane;
+                    u += __popc(__ballot_sync(kFull, i < m && !(pid[i] & kVisited)));
+                }
+                const float rk = rkey[k - 1];
+                const float den = rk > 1e-20f ? rk : 1e-20f;
+                const float fef = (float)ef;
+                const float since = (float)(hops - st.last_improve);
+                float f[SQG_MLP_IN];
+                f[0] = __fdiv_rn((float)hops, fef);
+                f[1] = __fdiv_rn(since, fef);
+                f[2] = __fdiv_rn((float)u, fef);
+                f[3] = __fdiv_rn((float)m, fef);
+                f[4] = __fdiv_rn(rkey[0], den);
+                f[5] = u > 0 ? __fdiv_rn(pkey[cur], den) : 0.0f;
+                f[6] = __fdiv_rn(dist_c, den);
+                f[7] = __fdiv_rn((float)inserted, (float)R);
+                f[8] = __fdiv_rn((float)k, fef);
+                f[9] = st.ema_improve;
+                f[10] = st.ema_insert;
+                f[11] = __fdiv_rn(pkey[0], den);
+                f[12] = __fdiv_rn(pkey[m - 1], den);
+                f[13] = __fdiv_rn(since, __fadd_rn((float)hops, 1.0f));
+                f[14] = dist_c <= rk ? 1.0f : 0.0f;
+                f[15] = __fdiv_rn((float)k, 100.0f);
+#pragma unroll
+                for (int i = 0; i < SQG_MLP_IN; ++i) f[i] = clamp8(f[i]);
+                if (a.trace_feat && tn < a.trace_cap) {
+                    float *dst = a.trace_feat + ((size_t)qi * a.trace_cap + tn) * SQG_MLP_IN;
+                    if (lane < SQG_MLP_IN) {
+                        float v = f[0];
+#pragma unroll
+                        for (int i = 1; i < SQG_MLP_IN; ++i) v = lane == i ? f[i] : v;
+                        dst[lane] = v;
+                    }
+                    if (a.gt) {
+                        int hit = 0;
+                        const uint32_t *g = a.gt + (size_t)qi * a.gt_k;
+                        for (int i = lane; i < rc; i += 32) {
+                            const uint32_t x = rid[i];
+                            for (int b = 0; b < k; ++b) hit += g[b] == x ? 1 : 0;
+                        }
+#pragma unroll
+                        for (int o = 16; o >= 1; o >>= 1) hit += __shfl_xor_sync(kFull, hit, o);
+                        if (lane == 0) a.trace_hit[(size_t)qi * a.trace_cap + tn] = hit;
+                    }
+                    ++tn;
+                }
+                if (a.mlp && mlp_logit_warp(wts, f, lane) > a.stop_logit) {
+                    status |= SQG_STATUS_LEARNED_STOP;
+                    break;
+                }
+            }
+        }
+        // drain a prefetch that will not be used
+        if (inflight) {
+            if (mbar_wait_bounded(&bar[cb], (phase >> cb) & 1u)) {
+                phase ^= 1u << cb;
+            } else {
+                status |= SQG_STATUS_TIMEOUT;
+                healthy = false;
+            }
+        }
+        __syncwarp();
+        // ---- line 8: the k nearest expanded vertices by exact distance
+        const bool ok = !(status & SQG_STATUS_TIMEOUT);
+        for (int t = lane; t < k; t += 32) {
+            const bool have = ok && t < rc;
+            a.out_ids[off + t] = have ? rid[t] : SQG_NO_ID;
+            a.out_dists[off + t] = have ? rkey[t] : __int_as_float(0x7f800000);
+        }
+        if (lane == 0) {
+            if (a.stats) a.stats[qi] = sqg_query_stats{(uint32_t)hops, status};
+            if (status) atomicOr(a.status_word, status);
+            if (a.trace_n) a.trace_n[qi] = tn;
+        }
+        __syncwarp();
+    }
+}
+
+// Host-side launch helpers, defined in the instantiation units.
+cudaError_t launch_search_nb1(int ch, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const SearchArgs &a);
+cudaError_t launch_search_nb2(int ch, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const SearchArgs &a);
+cudaError_t search_occupancy_nb1(int ch, int block, size_t smem, int *blocks_per_sm);
+cudaError_t search_occupancy_nb2(int ch, int block, size_t smem, int *blocks_per_sm);
+
+}  // namespace sqg

@@ -1,0 +1,648 @@
+// sqg_api.cu -- the C ABI of libsqg: index loading, launch planning and the
+// query-preparation kernels (rotation q' = P^-1 q, Eq. (4); 4-bit
+// quantization; per-query output offsets).  The search kernel itself is in
+// search.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/sqg.h"
+#include "index_format.h"
+#include "search.cuh"
+
+using namespace sqg;
+
+struct sqg_index {
+    int device;
+    sqg_fmt::Layout lay;
+    uint32_t entry;
+    unsigned char *d_blocks;
+    float *d_rot;
+    uint32_t *d_status;
+    int num_sms;
+    size_t smem_optin;
+};
+
+namespace {
+
+constexpr int kPlanThreads = 1024;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- kernels
+
+// Output offsets (exclusive prefix sum of each query's slot count) and the
+// largest valid k / ef of the batch.  One block; nq is looped in tiles.
+__global__ void plan_kernel(const int32_t *k, const int32_t *ef, int nq, long long *offsets, int *maxes) {
+    __shared__ long long warp_sums[kPlanThreads / 32];
+    __shared__ long long carry;
+    __shared__ int smax_k, smax_ef;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) { carry = 0; smax_k = 0; smax_ef = 0; }
+    __syncthreads();
+    int mk = 0, me = 0;
+    for (int base = 0; base < nq; base += kPlanThreads) {
+        const int i = base + tid;
+        long long c = 0;
+        if (i < nq) {
+            const int kk = k[i], ee = ef[i];
+            c = kk < 0 ? 0 : (kk > SQG_MAX_K ? SQG_MAX_K : kk);
+            if (kk >= 1 && kk <= SQG_MAX_K && ee >= kk && ee <= SQG_MAX_EF) {
+                mk = max(mk, kk);
+                me = max(me, ee);
+            }
+        }
+        long long x = c;  // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            long long s = lane < kPlanThreads / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                long long y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+                if (lane >= o) s += y;
+            }
+            warp_sums[lane] = s;  // inclusive over warps
+        }
+        __syncthreads();
+        const long long before = carry + (w > 0 ? warp_sums[w - 1] : 0) + x - c;
+        if (i < nq) offsets[i] = before;
+        __syncthreads();
+        if (tid == kPlanThreads - 1) carry = before + c;
+        __syncthreads();
+    }
+    atomicMax(&smax_k, mk);
+    atomicMax(&smax_ef, me);
+    __syncthreads();
+    if (tid == 0) {
+        maxes[0] = smax_k;
+        maxes[1] = smax_ef;
+    }
+}
+
+// q' = P^-1 q for a batch: out[r][i] = fmaf-chain over j = 0..d-1 of
+// rot[i][j] * q[r][j], starting from 0 (Eq. (4)).  64 x 64 output tiles,
+// 256 threads with 4 x 4 outputs each; every output keeps one accumulator
+// and walks j in order, so the tiling does not change a single bit.
+constexpr int kRotT = 64, kRotK = 16;
+__global__ void __launch_bounds__(256) rotate_kernel(const float *__restrict__ q, const float *__restrict__ rot,
+                                                     float *__restrict__ out, int nq, int d) {
+    __shared__ float As[kRotK][kRotT + 4];  // [j][row]
+    __shared__ float Bs[kRotK][kRotT + 4];  // [j][col]
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int r0 = blockIdx.y * kRotT, c0 = blockIdx.x * kRotT;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+    for (int j0 = 0; j0 < d; j0 += kRotK) {
+        for (int e = threadIdx.x; e < kRotT * kRotK; e += 256) {
+            const int rr = e / kRotK, jj = e % kRotK;
+            const int gr = r0 + rr, gc = c0 + rr;
+            As[jj][rr] = gr < nq ? q[(size_t)gr * d + j0 + jj] : 0.0f;
+            Bs[jj][rr] = gc < d ? rot[(size_t)gc * d + j0 + jj] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int jj = 0; jj < kRotK; ++jj) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[jj][ty * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[jj][tx * 4 + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = __fmaf_rn(bv[b], av[a], acc[a][b]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int gr = r0 + ty * 4 + a;
+        if (gr >= nq) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int gc = c0 + tx * 4 + b;
+            if (gc < d) out[(size_t)gr * d + gc] = acc[a][b];
+        }
+    }
+}
+
+// Quantized query export (test entry point): one warp per query.
+__global__ void quantize_kernel(const float *qrot, int nq, int d, uint32_t *planes, float *scal) {
+    const int lane = threadIdx.x & 31;
+    const int qi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (qi >= nq) return;
+    extern __shared__ uint32_t pl_smem[];
+    uint32_t *pl = pl_smem + (threadIdx.x >> 5) * (4 * (d / 32));
+    const QuerySide qs = quantize_warp(qrot + (size_t)qi * d, (uint32_t)d, pl, lane);
+    __syncwarp();
+    for (int i = lane; i < 4 * (d / 32); i += 32) planes[(size_t)qi * 4 * (d / 32) + i] = pl[i];
+    if (lane == 0) {
+        scal[qi * 4 + 0] = qs.vl;
+        scal[qi * 4 + 1] = qs.delta;
+        scal[qi * 4 + 2] = (float)qs.sq;
+        scal[qi * 4 + 3] = qs.inv_sqrt_d;
+    }
+}
+
+// Estimates of one block per query with the search kernel's own device
+// functions (test entry point).  One warp per query; the block is staged in
+// shared memory with plain 16-byte loads.
+__global__ void estimate_block_kernel(SearchArgs a, const uint32_t *v, int32_t *out_S, float *out_est,
+                                      float *out_key, float *out_dist_c) {
+    extern __shared__ __align__(16) unsigned char eb_smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int qi = blockIdx.x * (blockDim.x >> 5) + w;
+    if (qi >= a.nq) return;
+    const uint32_t d = a.d, R = a.R;
+    unsigned char *blk = eb_smem + (size_t)w * a.warp_bytes;
+    uint32_t *planes = reinterpret_cast<uint32_t *>(blk + a.block_bytes);
+    const uint32_t vv = v[qi];
+    if (vv >= a.n) {  // out-of-range vertex: NaN outputs, no access
+        for (uint32_t j = lane; j < R; j += 32) {
+            out_S[(size_t)qi * R + j] = 0;
+            out_est[(size_t)qi * R + j] = __int_as_float(0x7fc00000);
+            out_key[(size_t)qi * R + j] = __int_as_float(0x7fc00000);
+        }
+        if (lane == 0) out_dist_c[qi] = __int_as_float(0x7fc00000);
+        return;
+    }
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.blocks + (size_t)vv * a.block_bytes);
+    for (uint32_t i = lane; i < a.block_bytes / 16; i += 32) reinterpret_cast<uint4 *>(blk)[i] = src[i];
+    float4 qv[16];
+    const float *q = a.queries + (size_t)qi * d;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        uint32_t c = lane + 32 * t;
+        qv[t] = c < d / 4 ? reinterpret_cast<const float4 *>(q)[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const QuerySide qs = quantize_warp(a.qrot + (size_t)qi * d, d, planes, lane);
+    __syncwarp();
+    const float dist_c = exact_dist<16>(qv, reinterpret_cast<const float *>(blk), d / 4, lane);
+    for (uint32_t j = lane; j < R; j += 32) {
+        const Est e = estimate(blk, a, planes, qs, j, dist_c);
+        out_S[(size_t)qi * R + j] = e.S;
+        out_est[(size_t)qi * R + j] = e.est;
+        out_key[(size_t)qi * R + j] = e.key;
+    }
+    if (lane == 0) out_dist_c[qi] = dist_c;
+}
+
+// ---------------------------------------------------------------- planning
+
+int pick_ch(uint32_t d) {
+    const uint32_t need = (d / 4 + 31) / 32;
+    for (int c : {1, 2, 4, 8, 12, 16})
+        if ((uint32_t)c >= need) return c;
+    return -1;
+}
+
+struct LaunchPlan {
+    int ch, nb, warps, grid;
+    size_t smem;
+    SearchArgs a;  // layout fields filled in
+    bool ghash;
+    // workspace layout
+    size_t ws_offsets, ws_qrot, ws_queue, ws_maxes, ws_stats, ws_ghash, ws_total;
+};
+
+int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_search_params &p, LaunchPlan &pl) {
+    const uint32_t d = ix->lay.d, R = ix->lay.R, bb = ix->lay.block_bytes;
+    pl.ch = pick_ch(d);
+    pl.nb = (int)(R / 32);
+    if (pl.ch < 0 || (pl.nb != 1 && pl.nb != 2)) return SQG_ERR_UNSUPPORTED;
+    const long long cap = p.hop_cap > 0 ? p.hop_cap : 8LL * max_ef + 64;
+    uint32_t bits = 5;
+    while ((1ull << bits) < 2ull * (unsigned long long)cap + 1) ++bits;
+    if (bits > 26) return SQG_ERR_CAPACITY;
+    SearchArgs &a = pl.a;
+    std::memset(&a, 0, sizeof(a));
+    a.hash_bits = bits;
+    const size_t hash_bytes = (size_t)4 << bits;
+    size_t o = 0;
+    a.o_buf0 = (uint32_t)o; o += bb;
+    a.o_buf1 = (uint32_t)o; o += bb;
+    a.o_bar = (uint32_t)o; o += 16;
+    a.o_planes = (uint32_t)o; o = align_up(o + 16 * (d / 32), 16);
+    a.o_pkey = (uint32_t)o; o = align_up(o + 4 * (size_t)max_ef, 16);
+    a.o_pid = (uint32_t)o; o = align_up(o + 4 * (size_t)max_ef, 16);
+    a.o_rkey = (uint32_t)o; o = align_up(o + 4 * (size_t)max_k, 16);
+    a.o_rid = (uint32_t)o; o = align_up(o + 4 * (size_t)max_k, 16);
+    const size_t base = o;
+    pl.ghash = hash_bytes > 16384;
+    a.o_hash = (uint32_t)o;
+    size_t warp_bytes = align_up(base + (pl.ghash ? 0 : hash_bytes), 128);
+    const size_t cta = p.stop_mlp ? align_up(sizeof(float) * SQG_MLP_NPARAM, 128) : 0;
+    int warps = p.warps_per_block > 0 ? p.warps_per_block : 4;
+    warps = std::min(warps, 4);
+    while (warps > 1 && cta + warps * warp_bytes > ix->smem_optin) --warps;
+    if (cta + warps * warp_bytes > ix->smem_optin && !pl.ghash) {
+        pl.ghash = true;
+        warp_bytes = align_up(base, 128);
+    }
+    if (cta + warps * warp_bytes > ix->smem_optin) return SQG_ERR_CAPACITY;
+    a.warp_bytes = (uint32_t)warp_bytes;
+    a.cta_bytes = (uint32_t)cta;
+    pl.warps = warps;
+    pl.smem = cta + warps * warp_bytes;
+    int per_sm = 0;
+    cudaError_t e = pl.nb == 1 ? search_occupancy_nb1(pl.ch, warps * 32, pl.smem, &per_sm)
+                               : search_occupancy_nb2(pl.ch, warps * 32, pl.smem, &per_sm);
+    if (e != cudaSuccess) return SQG_ERR_CUDA;
+    if (per_sm < 1) return SQG_ERR_CAPACITY;
+    const long long want = ((long long)nq + warps - 1) / warps;
+    pl.grid = (int)std::max(1LL, std::min<long long>((long long)per_sm * ix->num_sms, want));
+    // workspace
+    size_t w = 0;
+    pl.ws_offsets = w; w = align_up(w + 8 * (size_t)std::max(nq, 1), 256);
+    pl.ws_qrot = w; w = align_up(w + 4 * (size_t)std::max(nq, 1) * d, 256);
+    pl.ws_queue = w; w = align_up(w + 4, 256);
+    pl.ws_maxes = w; w = align_up(w + 8, 256);
+    pl.ws_stats = w; w = align_up(w + sizeof(sqg_query_stats) * (size_t)std::max(nq, 1), 256);
+    pl.ws_ghash = w;
+    if (pl.ghash) w = align_up(w + hash_bytes * (size_t)pl.grid * warps, 256);
+    pl.ws_total = w;
+    return SQG_OK;
+}
+
+sqg_search_params default_params() {
+    sqg_search_params p;
+    std::memset(&p, 0, sizeof(p));
+    p.multi_estimate = 1;
+    p.stop_every = 1;
+    return p;
+}
+
+int check_params(const sqg_search_params &p) {
+    if (p.hop_cap < 0 || p.max_k < 0 || p.max_ef < 0 || p.max_k > SQG_MAX_K || p.max_ef > SQG_MAX_EF ||
+        (p.max_k > 0 && p.max_ef > 0 && p.max_ef < p.max_k) || p.stop_every < 0 ||
+        (p.team != 0 && p.team != 32) || p.warps_per_block < 0 || !std::isfinite(p.eps0) ||
+        (p.stop_mlp && p.stop_every < 1))
+        return SQG_ERR_INVALID_ARG;
+    return SQG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" const char *sqg_error_string(int code) {
+    switch (code) {
+        case SQG_OK: return "ok";
+        case SQG_ERR_INVALID_ARG: return "invalid argument";
+        case SQG_ERR_IO: return "i/o error";
+        case SQG_ERR_FORMAT: return "bad index file format";
+        case SQG_ERR_OOM: return "out of memory";
+        case SQG_ERR_CUDA: return "CUDA error";
+        case SQG_ERR_TIMEOUT: return "bounded device wait expired";
+        case SQG_ERR_CAPACITY: return "capacity exceeded";
+        case SQG_ERR_UNSUPPORTED: return "unsupported index shape";
+        default: return "unknown error";
+    }
+}
+
+extern "C" int sqg_index_load(const char *path, int device, sqg_index **out) {
+    if (!path || !out || device < 0) return SQG_ERR_INVALID_ARG;
+    *out = nullptr;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return SQG_ERR_IO;
+    std::fseek(f, 0, SEEK_END);
+    const long long fsize = std::ftell(f);
+    std::fseek(f, 0, SEEK_SET);
+    unsigned char hdr[sqg_fmt::kHeaderBytes];
+    if (fsize < (long long)sizeof(hdr) || std::fread(hdr, 1, sizeof(hdr), f) != sizeof(hdr)) {
+        std::fclose(f);
+        return fsize < (long long)sizeof(hdr) ? SQG_ERR_FORMAT : SQG_ERR_IO;
+    }
+    sqg_fmt::Header h;
+    if (!sqg_fmt::parse_header(hdr, (uint64_t)fsize, h)) {
+        std::fclose(f);
+        return SQG_ERR_FORMAT;
+    }
+    const sqg_fmt::Layout &L = h.l;
+    if (L.n > 0x7FFFFFFFull) { std::fclose(f); return SQG_ERR_UNSUPPORTED; }
+    if (pick_ch(L.d) < 0 || (L.R != 32 && L.R != 64)) { std::fclose(f); return SQG_ERR_UNSUPPORTED; }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device >= ndev) {
+        cudaGetLastError();
+        std::fclose(f);
+        return SQG_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(device);
+    sqg_index *ix = new (std::nothrow) sqg_index();
+    if (!ix) { std::fclose(f); return SQG_ERR_OOM; }
+    ix->device = device;
+    ix->lay = L;
+    ix->entry = h.entry;
+    cudaDeviceGetAttribute(&ix->num_sms, cudaDevAttrMultiProcessorCount, device);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    ix->smem_optin = (size_t)optin;
+    const size_t block_bytes_total = (size_t)L.n * L.block_bytes;
+    if (cudaMalloc(&ix->d_blocks, block_bytes_total) != cudaSuccess ||
+        cudaMalloc(&ix->d_rot, sizeof(float) * (size_t)L.d * L.d) != cudaSuccess ||
+        cudaMalloc(&ix->d_status, sizeof(uint32_t)) != cudaSuccess) {
+        std::fclose(f);
+        sqg_index_free(ix);
+        cudaGetLastError();
+        return SQG_ERR_OOM;
+    }
+    cudaMemset(ix->d_status, 0, sizeof(uint32_t));
+    // stream the payload through a pinned buffer, hashing and checking ids
+    const size_t chunk = (size_t)64 << 20;
+    unsigned char *stage = nullptr;
+    if (cudaMallocHost(&stage, chunk) != cudaSuccess) {
+        std::fclose(f);
+        sqg_index_free(ix);
+        return SQG_ERR_OOM;
+    }
+    uint64_t hash = sqg_fmt::kFnvBasis;
+    int rc = SQG_OK;
+    // rotation + padding
+    {
+        const size_t nbytes = L.blocks_offset - L.rot_offset;
+        std::vector<unsigned char> buf(nbytes);
+        if (std::fread(buf.data(), 1, nbytes, f) != nbytes) rc = SQG_ERR_IO;
+        else {
+            hash = sqg_fmt::fnv_words(hash, buf.data(), nbytes);
+            if (cudaMemcpy(ix->d_rot, buf.data(), sizeof(float) * (size_t)L.d * L.d, cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+                rc = SQG_ERR_CUDA;
+        }
+    }
+    const size_t per_chunk = std::max<size_t>(1, chunk / L.block_bytes);
+    std::vector<uint32_t> ids(L.R);
+    for (uint64_t v0 = 0; rc == SQG_OK && v0 < L.n; v0 += per_chunk) {
+        const uint64_t nv = std::min<uint64_t>(per_chunk, L.n - v0);
+        const size_t nbytes = nv * L.block_bytes;
+        if (std::fread(stage, 1, nbytes, f) != nbytes) { rc = SQG_ERR_IO; break; }
+        hash = sqg_fmt::fnv_words(hash, stage, nbytes);
+        for (uint64_t t = 0; t < nv && rc == SQG_OK; ++t) {
+            const unsigned char *b = stage + t * L.block_bytes + L.off_ids;
+            for (uint32_t j = 0; j < L.R; ++j) ids[j] = sqg_fmt::load_u32(b + 4 * j);
+            std::sort(ids.begin(), ids.end());
+            for (uint32_t j = 0; j < L.R; ++j)
+                if (ids[j] >= L.n || ids[j] == v0 + t || (j > 0 && ids[j] == ids[j - 1])) rc = SQG_ERR_FORMAT;
+        }
+        if (rc == SQG_OK && cudaMemcpy(ix->d_blocks + v0 * L.block_bytes, stage, nbytes, cudaMemcpyHostToDevice) !=
+                                cudaSuccess)
+            rc = SQG_ERR_CUDA;
+    }
+    cudaFreeHost(stage);
+    std::fclose(f);
+    if (rc == SQG_OK && hash != h.payload_hash) rc = SQG_ERR_FORMAT;
+    if (rc != SQG_OK) {
+        sqg_index_free(ix);
+        return rc;
+    }
+    *out = ix;
+    return SQG_OK;
+}
+
+extern "C" void sqg_index_free(sqg_index *ix) {
+    if (!ix) return;
+    DeviceGuard g(ix->device);
+    cudaDeviceSynchronize();
+    if (ix->d_blocks) cudaFree(ix->d_blocks);
+    if (ix->d_rot) cudaFree(ix->d_rot);
+    if (ix->d_status) cudaFree(ix->d_status);
+    delete ix;
+}
+
+extern "C" int sqg_index_info(const sqg_index *ix, sqg_info *out) {
+    if (!ix || !out) return SQG_ERR_INVALID_ARG;
+    out->n = ix->lay.n;
+    out->d = ix->lay.d;
+    out->degree = ix->lay.R;
+    out->block_bytes = ix->lay.block_bytes;
+    out->entry = ix->entry;
+    out->off_codes = ix->lay.off_codes;
+    out->off_factors = ix->lay.off_factors;
+    out->off_ids = ix->lay.off_ids;
+    out->device = ix->device;
+    out->device_bytes = (uint64_t)ix->lay.n * ix->lay.block_bytes + 4ull * ix->lay.d * ix->lay.d + 4;
+    return SQG_OK;
+}
+
+extern "C" size_t sqg_workspace_size(const sqg_index *ix, int nq, int max_k, int max_ef) {
+    if (!ix || nq < 0 || max_k < 1 || max_k > SQG_MAX_K || max_ef < max_k || max_ef > SQG_MAX_EF) return 0;
+    DeviceGuard g(ix->device);
+    // the larger of the plans without and with the learned stop's weights
+    LaunchPlan pl;
+    sqg_search_params p = default_params();
+    if (make_plan(ix, nq, max_k, max_ef, p, pl) != SQG_OK) return 0;
+    size_t need = pl.ws_total;
+    p.stop_mlp = reinterpret_cast<const float *>(16);  // any non-null: only the layout is planned
+    if (make_plan(ix, nq, max_k, max_ef, p, pl) == SQG_OK) need = std::max(need, pl.ws_total);
+    return need;
+}
+
+static int search_impl(const sqg_index *ix, const float *queries, int nq, const int32_t *k, const int32_t *ef,
+                       uint32_t *out_ids, float *out_dists, const sqg_search_params *params, void *workspace,
+                       size_t ws_bytes, sqg_query_stats *stats, cudaStream_t stream, float *trace_feat,
+                       int32_t *trace_hit, int32_t *trace_n, int trace_cap, const uint32_t *gt, int gt_k) {
+    if (!ix || nq < 0) return SQG_ERR_INVALID_ARG;
+    if (nq == 0) return SQG_OK;
+    if (!queries || !k || !ef || !out_ids || !out_dists) return SQG_ERR_INVALID_ARG;
+    sqg_search_params p = params ? *params : default_params();
+    if (params && p.stop_every == 0) p.stop_every = 1;
+    if (check_params(p) != SQG_OK) return SQG_ERR_INVALID_ARG;
+    DeviceGuard g(ix->device);
+    cudaError_t e;
+    int max_k = p.max_k, max_ef = p.max_ef;
+    if (max_k == 0 || max_ef == 0) {  // read the batch's bounds (one stream sync)
+        void *tmp = nullptr;
+        if (cudaMallocAsync(&tmp, 8 * (size_t)nq + 256, stream) != cudaSuccess) return SQG_ERR_OOM;
+        int *maxes = reinterpret_cast<int *>(reinterpret_cast<char *>(tmp) + align_up(8 * (size_t)nq, 256));
+        plan_kernel<<<1, kPlanThreads, 0, stream>>>(k, ef, nq, reinterpret_cast<long long *>(tmp), maxes);
+        int hm[2] = {0, 0};
+        e = cudaMemcpyAsync(hm, maxes, sizeof(hm), cudaMemcpyDeviceToHost, stream);
+        cudaError_t e2 = cudaStreamSynchronize(stream);
+        cudaFreeAsync(tmp, stream);
+        if (e != cudaSuccess || e2 != cudaSuccess) return SQG_ERR_CUDA;
+        if (max_k == 0) max_k = std::max(1, hm[0]);
+        if (max_ef == 0) max_ef = std::max(max_k, hm[1]);
+    }
+    LaunchPlan pl;
+    int rc = make_plan(ix, nq, max_k, max_ef, p, pl);
+    if (rc != SQG_OK) return rc;
+    bool own_ws = false;
+    if (!workspace) {
+        if (cudaMallocAsync(&workspace, pl.ws_total, stream) != cudaSuccess) return SQG_ERR_OOM;
+        own_ws = true;
+    } else if (ws_bytes < pl.ws_total) {
+        return SQG_ERR_CAPACITY;
+    }
+    char *ws = reinterpret_cast<char *>(workspace);
+    SearchArgs &a = pl.a;
+    a.blocks = ix->d_blocks;
+    a.block_bytes = ix->lay.block_bytes;
+    a.n = (uint32_t)ix->lay.n;
+    a.d = ix->lay.d;
+    a.R = ix->lay.R;
+    a.entry = ix->entry;
+    a.off_codes = ix->lay.off_codes;
+    a.off_factors = ix->lay.off_factors;
+    a.off_ids = ix->lay.off_ids;
+    a.queries = queries;
+    a.qrot = reinterpret_cast<float *>(ws + pl.ws_qrot);
+    a.nq = nq;
+    a.k = k;
+    a.ef = ef;
+    a.offsets = reinterpret_cast<long long *>(ws + pl.ws_offsets);
+    a.out_ids = out_ids;
+    a.out_dists = out_dists;
+    a.stats = stats ? stats : reinterpret_cast<sqg_query_stats *>(ws + pl.ws_stats);
+    a.status_word = ix->d_status;
+    a.queue_head = reinterpret_cast<unsigned int *>(ws + pl.ws_queue);
+    a.max_k = max_k;
+    a.max_ef = max_ef;
+    a.hop_cap = p.hop_cap;
+    a.ghash = pl.ghash ? reinterpret_cast<uint32_t *>(ws + pl.ws_ghash) : nullptr;
+    a.eps0 = p.eps0;
+    a.multi_estimate = p.multi_estimate;
+    a.mlp = p.stop_mlp;
+    a.stop_logit = p.stop_logit;
+    a.stop_every = p.stop_every;
+    a.trace_feat = trace_feat;
+    a.trace_hit = trace_hit;
+    a.trace_n = trace_n;
+    a.trace_cap = trace_cap;
+    a.gt = gt;
+    a.gt_k = gt_k;
+
+    plan_kernel<<<1, kPlanThreads, 0, stream>>>(k, ef, nq, const_cast<long long *>(a.offsets),
+                                                reinterpret_cast<int *>(ws + pl.ws_maxes));
+    dim3 rg((ix->lay.d + kRotT - 1) / kRotT, (nq + kRotT - 1) / kRotT);
+    rotate_kernel<<<rg, 256, 0, stream>>>(queries, ix->d_rot, const_cast<float *>(a.qrot), nq, (int)ix->lay.d);
+    e = cudaMemsetAsync(a.queue_head, 0, sizeof(unsigned int), stream);
+    if (e == cudaSuccess && p.timing_events[0])
+        e = cudaEventRecord(reinterpret_cast<cudaEvent_t>(p.timing_events[0]), stream);
+    if (e == cudaSuccess) {
+        e = pl.nb == 1 ? launch_search_nb1(pl.ch, dim3(pl.grid), dim3(pl.warps * 32), pl.smem, stream, a)
+                       : launch_search_nb2(pl.ch, dim3(pl.grid), dim3(pl.warps * 32), pl.smem, stream, a);
+    }
+    if (e == cudaSuccess && p.timing_events[1])
+        e = cudaEventRecord(reinterpret_cast<cudaEvent_t>(p.timing_events[1]), stream);
+    if (own_ws) cudaFreeAsync(workspace, stream);
+    if (e != cudaSuccess) return SQG_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? SQG_OK : SQG_ERR_CUDA;
+}
+
+extern "C" int sqg_search(const sqg_index *ix, const float *queries, int nq, const int32_t *k, const int32_t *ef,
+                          uint32_t *out_ids, float *out_dists, sqg_stream_t stream) {
+    return search_impl(ix, queries, nq, k, ef, out_ids, out_dists, nullptr, nullptr, 0, nullptr,
+                       reinterpret_cast<cudaStream_t>(stream), nullptr, nullptr, nullptr, 0, nullptr, 0);
+}
+
+extern "C" int sqg_search_ex(const sqg_index *ix, const float *queries, int nq, const int32_t *k,
+                             const int32_t *ef, uint32_t *out_ids, float *out_dists,
+                             const sqg_search_params *params, void *workspace, size_t ws_bytes,
+                             sqg_query_stats *stats, sqg_stream_t stream) {
+    return search_impl(ix, queries, nq, k, ef, out_ids, out_dists, params, workspace, ws_bytes, stats,
+                       reinterpret_cast<cudaStream_t>(stream), nullptr, nullptr, nullptr, 0, nullptr, 0);
+}
+
+extern "C" int sqg_search_trace(const sqg_index *ix, const float *queries, int nq, const int32_t *k,
+                                const int32_t *ef, uint32_t *out_ids, float *out_dists,
+                                const sqg_search_params *params, sqg_query_stats *stats, const uint32_t *gt,
+                                int gt_k, float *trace_feat, int32_t *trace_hit, int32_t *trace_n, int trace_cap,
+                                sqg_stream_t stream) {
+    if (!trace_feat || !trace_n || trace_cap < 1 || (gt && (!trace_hit || gt_k < 1))) return SQG_ERR_INVALID_ARG;
+    return search_impl(ix, queries, nq, k, ef, out_ids, out_dists, params, nullptr, 0, stats,
+                       reinterpret_cast<cudaStream_t>(stream), trace_feat, trace_hit, trace_n, trace_cap, gt, gt_k);
+}
+
+extern "C" int sqg_prepare_queries(const sqg_index *ix, const float *queries, int nq, float *out_qrot,
+                                   uint32_t *out_planes, float *out_scal, sqg_stream_t stream_) {
+    if (!ix || nq < 0) return SQG_ERR_INVALID_ARG;
+    if (nq == 0) return SQG_OK;
+    if (!queries || !out_qrot || !out_planes || !out_scal) return SQG_ERR_INVALID_ARG;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    DeviceGuard g(ix->device);
+    const int d = (int)ix->lay.d;
+    dim3 rg((d + kRotT - 1) / kRotT, (nq + kRotT - 1) / kRotT);
+    rotate_kernel<<<rg, 256, 0, stream>>>(queries, ix->d_rot, out_qrot, nq, d);
+    const int wpb = 4;
+    quantize_kernel<<<(nq + wpb - 1) / wpb, wpb * 32, sizeof(uint32_t) * wpb * 4 * (d / 32), stream>>>(
+        out_qrot, nq, d, out_planes, out_scal);
+    return cudaGetLastError() == cudaSuccess ? SQG_OK : SQG_ERR_CUDA;
+}
+
+extern "C" int sqg_estimate_block(const sqg_index *ix, const float *queries, int nq, const uint32_t *v,
+                                  float eps0, int32_t *out_S, float *out_est, float *out_key, float *out_dist_c,
+                                  sqg_stream_t stream_) {
+    if (!ix || nq < 0 || !std::isfinite(eps0)) return SQG_ERR_INVALID_ARG;
+    if (nq == 0) return SQG_OK;
+    if (!queries || !v || !out_S || !out_est || !out_key || !out_dist_c) return SQG_ERR_INVALID_ARG;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    DeviceGuard g(ix->device);
+    const int d = (int)ix->lay.d;
+    float *qrot = nullptr;
+    if (cudaMallocAsync(&qrot, sizeof(float) * (size_t)nq * d, stream) != cudaSuccess) return SQG_ERR_OOM;
+    dim3 rg((d + kRotT - 1) / kRotT, (nq + kRotT - 1) / kRotT);
+    rotate_kernel<<<rg, 256, 0, stream>>>(queries, ix->d_rot, qrot, nq, d);
+    SearchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.blocks = ix->d_blocks;
+    a.block_bytes = ix->lay.block_bytes;
+    a.n = (uint32_t)ix->lay.n;
+    a.d = ix->lay.d;
+    a.R = ix->lay.R;
+    a.off_codes = ix->lay.off_codes;
+    a.off_factors = ix->lay.off_factors;
+    a.off_ids = ix->lay.off_ids;
+    a.queries = queries;
+    a.qrot = qrot;
+    a.nq = nq;
+    a.eps0 = eps0;
+    a.warp_bytes = (uint32_t)align_up(ix->lay.block_bytes + 16 * (d / 32), 16);
+    const int wpb = 2;
+    const size_t smem = (size_t)wpb * a.warp_bytes;
+    cudaError_t e = cudaFuncSetAttribute(estimate_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        estimate_block_kernel<<<(nq + wpb - 1) / wpb, wpb * 32, smem, stream>>>(a, v, out_S, out_est, out_key,
+                                                                               out_dist_c);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(qrot, stream);
+    return e == cudaSuccess ? SQG_OK : SQG_ERR_CUDA;
+}
+
+extern "C" int sqg_get_status(const sqg_index *ix, sqg_stream_t stream_, uint32_t *status) {
+    if (!ix || !status) return SQG_ERR_INVALID_ARG;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    DeviceGuard g(ix->device);
+    uint32_t h = 0;
+    if (cudaMemcpyAsync(&h, ix->d_status, sizeof(h), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaMemsetAsync(ix->d_status, 0, sizeof(uint32_t), stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return SQG_ERR_CUDA;
+    *status = h;
+    return SQG_OK;
+}

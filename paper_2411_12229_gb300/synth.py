@@ -115,8 +115,9 @@ def _draw(w: Workload, stream: int, lo: int, hi: int, C: np.ndarray,
         r0, r1 = c * _CHUNK, (c + 1) * _CHUNK
         g = _rng(w, stream, c)
         comp = g.integers(0, w.n_components, size=_CHUNK)
-        x = g.standard_normal((_CHUNK, w.d), dtype=np.float32)
         a, b = max(lo, r0), min(hi, r1)
+        # the stream is sequential: rows past b are never needed
+        x = g.standard_normal((b - r0, w.d), dtype=np.float32)
         sel = slice(a - r0, b - r0)
         xs = x[sel]
         xs *= np.float32(w.noise_std)

@@ -1,0 +1,288 @@
+"""GPU parity: every kernel step through the C ABI against the CPU oracle.
+
+Bars: integer sums and ids bit-exact; fp32 estimates, keys and exact
+distances bit-exact too (both sides take their float decisions in the same
+precision and order), which is stricter than the 1e-5 relative tolerance
+the float values would need on their own.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gpu_tiny(tiny_index):
+    from paper_2411_12229_gb300.api import Index
+    p, x, q = tiny_index
+    return Index(p, 0), p, x, q
+
+
+@pytest.fixture(scope="module")
+def gpu_tiny64(tiny_index_r64):
+    from paper_2411_12229_gb300.api import Index
+    p, x, q = tiny_index_r64
+    return Index(p, 0), p, x, q
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.mark.parametrize("which", ["gpu_tiny", "gpu_tiny64"])
+def test_prepare_queries_bit_exact(which, request, oracle_mod):
+    """q' = P^-1 q (Eq. (4)) and its 4-bit planes, identical to the oracle."""
+    ix, p, x, q = request.getfixturevalue(which)
+    O = oracle_mod.Index(p)
+    qd = torch.from_numpy(q).cuda()
+    qrot, planes, scal = ix.prepare_queries(qd)
+    qrot, planes, scal = _np(qrot), _np(planes).view(np.uint32), _np(scal)
+    for i in range(q.shape[0]):
+        r = O.prepare_query(q[i])
+        np.testing.assert_array_equal(qrot[i], r["qrot"])
+        assert scal[i, 0] == r["vl"] and scal[i, 1] == r["delta"] and scal[i, 2] == r["sq"]
+        qb = r["qbar"].astype(np.uint32)
+        for b in range(4):
+            bits = (qb >> b) & 1
+            words = np.array([int("".join(str(v) for v in bits[w * 32:(w + 1) * 32][::-1]), 2)
+                              for w in range(ix.d // 32)], dtype=np.uint32)
+            np.testing.assert_array_equal(planes[i, b], words)
+
+
+@pytest.mark.parametrize("which", ["gpu_tiny", "gpu_tiny64"])
+@pytest.mark.parametrize("eps0", [0.0, 1.9])
+def test_estimates_bit_exact(which, eps0, request, oracle_mod):
+    """S (AND + popc over bit-planes) = sum_i b_i qbar_i exactly; est, key
+    and dist_c bit-identical to the oracle (Sec. 3.1.1)."""
+    ix, p, x, q = request.getfixturevalue(which)
+    O = oracle_mod.Index(p)
+    rng = np.random.default_rng(0)
+    v = rng.integers(0, ix.n, size=q.shape[0]).astype(np.int32)
+    S, est, key, dc = (_np(t) for t in ix.estimate_block(torch.from_numpy(q).cuda(), torch.from_numpy(v), eps0))
+    for i in range(q.shape[0]):
+        r = O.estimate_block(q[i], int(v[i]), eps0)
+        np.testing.assert_array_equal(S[i], r["S"])
+        np.testing.assert_array_equal(est[i], r["est"])
+        np.testing.assert_array_equal(key[i], r["key"])
+        assert dc[i] == r["dist_c"]
+
+
+def test_golden_closed_form_on_gpu(oracle_mod, lib_built, tmp_path):
+    """tests/golden/alpha_one_d32.txt through the GPU: estimates equal the
+    integer squared distances (alpha = 1, exact 4-bit query)."""
+    from test_oracle_pins import golden_index
+
+    from paper_2411_12229_gb300.api import Index
+    p = tmp_path / "golden.sqg"
+    x, q = golden_index(p)
+    ix = Index(p, 0)
+    S, est, key, dc = (_np(t) for t in ix.estimate_block(torch.from_numpy(q[None, :]).cuda(),
+                                                          torch.zeros(1, dtype=torch.int32)))
+    ids = oracle_mod.Index(p).vertex(0)["ids"]
+    exact = np.array([np.sum((x[j] - q).astype(np.int64) ** 2) for j in ids], dtype=np.float64)
+    np.testing.assert_allclose(est[0], exact, rtol=2e-6)
+    assert dc[0] == np.sum((x[0] - q).astype(np.int64) ** 2)
+
+
+def _check_search(ix, O, q, k, ef, **kw):
+    qd = torch.from_numpy(q).cuda()
+    ids, dists, st = ix.search(qd, k, ef, stats=True, **{a: b for a, b in kw.items() if a != "mlp_np"})
+    ids, dists, st = _np(ids).view(np.uint32), _np(dists), _np(st)
+    okw = dict(eps0=kw.get("eps0", 0.0), multi_estimate=kw.get("multi_estimate", True))
+    if kw.get("hop_cap"):
+        okw["hop_cap"] = kw["hop_cap"]
+    if kw.get("mlp_np") is not None:
+        okw.update(mlp=kw["mlp_np"], stop_logit=kw.get("stop_logit", 0.0), stop_every=kw.get("stop_every", 1))
+    for i in range(q.shape[0]):
+        oi, od, oh, os_ = O.search(q[i], k, ef, **okw)
+        np.testing.assert_array_equal(ids[i], oi, err_msg=f"query {i} ids")
+        np.testing.assert_array_equal(dists[i], od, err_msg=f"query {i} dists")
+        assert (st[i, 0], st[i, 1]) == (oh, os_), f"query {i}: hops/status {st[i]} vs {(oh, os_)}"
+    return ids, dists, st
+
+
+@pytest.mark.parametrize("ef", [10, 16, 33, 64, 128, 300])
+def test_search_parity_r32(gpu_tiny, oracle_mod, ef):
+    """Algorithm 1 with multiple estimates and implicit re-ranking: ids,
+    distances and hop counts identical to the oracle."""
+    ix, p, x, q = gpu_tiny
+    _check_search(ix, oracle_mod.Index(p), q, 10, ef)
+
+
+@pytest.mark.parametrize("ef", [16, 64, 200])
+def test_search_parity_r64(gpu_tiny64, oracle_mod, ef):
+    ix, p, x, q = gpu_tiny64
+    _check_search(ix, oracle_mod.Index(p), q, 10, ef)
+
+
+def test_search_variants(gpu_tiny, oracle_mod):
+    """eps0 admission key, the w/o-ME ablation and a binding hop cap."""
+    ix, p, x, q = gpu_tiny
+    O = oracle_mod.Index(p)
+    _check_search(ix, O, q, 10, 64, eps0=1.0)
+    _check_search(ix, O, q, 10, 64, multi_estimate=False)
+    _, _, st = _check_search(ix, O, q, 5, 64, hop_cap=7)
+    assert np.all(st[:, 0] <= 7) and np.any(st[:, 1] == 1)
+
+
+def test_search_k_equals_ef_and_k1(gpu_tiny, oracle_mod):
+    ix, p, x, q = gpu_tiny
+    O = oracle_mod.Index(p)
+    _check_search(ix, O, q, 1, 1)
+    _check_search(ix, O, q, 1, 40)
+    _check_search(ix, O, q, 100, 100)
+    _check_search(ix, O, q, 256, 256)
+
+
+def test_mixed_k_ef_ragged_batch(gpu_tiny, oracle_mod):
+    """One launch with per-query k and ef (the persistent work queue):
+    each query's slice of the ragged output equals the oracle's search."""
+    ix, p, x, q = gpu_tiny
+    O = oracle_mod.Index(p)
+    rng = np.random.default_rng(3)
+    nq = q.shape[0]
+    k = rng.choice([1, 10, 100], size=nq).astype(np.int32)
+    ef = np.array([rng.integers(kk, 8 * kk + 1) for kk in k], dtype=np.int32)
+    ids, dists, st = ix.search(torch.from_numpy(q).cuda(), torch.from_numpy(k), torch.from_numpy(ef), stats=True)
+    ids, dists, st = _np(ids).view(np.uint32), _np(dists), _np(st)
+    off = np.concatenate([[0], np.cumsum(k)])
+    assert ids.shape[0] == off[-1]
+    for i in range(nq):
+        oi, od, oh, os_ = O.search(q[i], int(k[i]), int(ef[i]))
+        np.testing.assert_array_equal(ids[off[i]:off[i + 1]], oi)
+        np.testing.assert_array_equal(dists[off[i]:off[i + 1]], od)
+        assert st[i, 0] == oh
+
+
+def test_plain_sqg_search_entry_point(gpu_tiny, oracle_mod):
+    """sqg_search (device k[], ef[], bounds read on the device)."""
+    ix, p, x, q = gpu_tiny
+    O = oracle_mod.Index(p)
+    nq = q.shape[0]
+    k = torch.full((nq,), 10, dtype=torch.int32, device="cuda")
+    ef = torch.full((nq,), 48, dtype=torch.int32, device="cuda")
+    ids = torch.empty(nq * 10, dtype=torch.int32, device="cuda")
+    dd = torch.empty(nq * 10, dtype=torch.float32, device="cuda")
+    ix.search_plain(torch.from_numpy(q).cuda(), k, ef, ids, dd)
+    ids = _np(ids).view(np.uint32).reshape(nq, 10)
+    for i in range(nq):
+        np.testing.assert_array_equal(ids[i], O.search(q[i], 10, 48)[0])
+
+
+def test_invalid_per_query_params_are_padding(gpu_tiny, oracle_mod):
+    ix, p, x, q = gpu_tiny
+    O = oracle_mod.Index(p)
+    k = np.array([10, 0, 10, 5, 300, 10], dtype=np.int32)
+    ef = np.array([32, 32, 5, 5, 400, 40], dtype=np.int32)
+    qq = torch.from_numpy(q[:6]).cuda()
+    ids, dists, st = ix.search(qq, torch.from_numpy(k), torch.from_numpy(ef), stats=True, max_k=10, max_ef=40)
+    ids, dists, st = _np(ids).view(np.uint32), _np(dists), _np(st)
+    kk = np.clip(k, 0, 256)
+    off = np.concatenate([[0], np.cumsum(kk)])
+    assert ids.shape[0] == off[-1]
+    bad = [1, 2, 4]
+    for i in range(6):
+        sl = slice(off[i], off[i + 1])
+        if i in bad:
+            assert st[i, 1] == 4 and np.all(ids[sl] == 0xFFFFFFFF) and np.all(np.isinf(dists[sl]))
+        else:
+            np.testing.assert_array_equal(ids[sl], O.search(q[i], int(k[i]), int(ef[i]))[0])
+    assert ix.status() & 4
+    assert ix.status() == 0  # cleared by the read
+
+
+def test_empty_batch_and_bad_arguments(gpu_tiny):
+    from paper_2411_12229_gb300._binding import SqgError
+    ix, p, x, q = gpu_tiny
+    ids, dists = ix.search(torch.empty((0, ix.d), device="cuda"), 10, 32)
+    assert ids.numel() == 0
+    with pytest.raises(SqgError):
+        ix.search(torch.from_numpy(q).cuda(), 10, 32, hop_cap=-1)
+    with pytest.raises(SqgError):
+        ix.search(torch.from_numpy(q).cuda(), 10, 32, max_k=300)
+    with pytest.raises(SqgError):  # workspace too small
+        ix.search(torch.from_numpy(q).cuda(), 10, 32, max_k=10, max_ef=32,
+                  workspace=torch.empty(16, dtype=torch.uint8, device="cuda"))
+
+
+def test_caller_workspace_matches_own_allocation(gpu_tiny):
+    ix, p, x, q = gpu_tiny
+    qd = torch.from_numpy(q).cuda()
+    a = ix.search(qd, 10, 64)
+    nbytes = ix.workspace_size(q.shape[0], 10, 64)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    b = ix.search(qd, 10, 64, max_k=10, max_ef=64, workspace=ws)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+def test_large_ef_uses_global_hash(gpu_tiny, oracle_mod):
+    """ef = 1024: the visited hash no longer fits the shared-memory budget
+    and lives in the workspace; results unchanged."""
+    ix, p, x, q = gpu_tiny
+    _check_search(ix, oracle_mod.Index(p), q[:16], 10, 1024)
+
+
+def test_learned_stop_constant_networks(gpu_tiny, oracle_mod):
+    ix, p, x, q = gpu_tiny
+    O = oracle_mod.Index(p)
+    mlp = np.zeros(5313, np.float32)
+    for b3, want in ((-100.0, 0), (100.0, 2)):
+        mlp[-1] = b3
+        dm = torch.from_numpy(mlp).cuda()
+        _, _, st = _check_search(ix, O, q, 10, 64, stop_mlp=dm, mlp_np=mlp, stop_logit=0.0, stop_every=4)
+        assert np.all(st[:, 1] == want)
+
+
+def test_learned_stop_random_network_parity(gpu_tiny, oracle_mod):
+    """A random network: the fused fp32 forward takes the same stop decision
+    at the same hop as the oracle's forward."""
+    ix, p, x, q = gpu_tiny
+    O = oracle_mod.Index(p)
+    rng = np.random.default_rng(5)
+    mlp = (rng.standard_normal(5313) * 0.3).astype(np.float32)
+    dm = torch.from_numpy(mlp).cuda()
+    for thr in (-1.0, 0.5, 2.0):
+        _check_search(ix, O, q, 10, 64, stop_mlp=dm, mlp_np=mlp, stop_logit=thr, stop_every=2)
+
+
+def test_trace_features_bit_exact(gpu_tiny, oracle_mod):
+    ix, p, x, q = gpu_tiny
+    O = oracle_mod.Index(p)
+    nq = 24
+    gt = np.stack([oracle_mod.bruteforce(x, q[i], 10)[0] for i in range(nq)]).astype(np.int32)
+    ids, dists, st, feats, hits, cnt = ix.search_trace(torch.from_numpy(q[:nq]).cuda(), 10, 64,
+                                                       torch.from_numpy(gt).cuda(), 256, stop_every=3)
+    feats, hits, cnt = _np(feats), _np(hits), _np(cnt)
+    for i in range(nq):
+        r = O.search(q[i], 10, 64, stop_every=3, gt=gt[i].view(np.uint32), trace_cap=256)
+        tf, th = r[4], r[5]
+        assert cnt[i] == len(tf)
+        np.testing.assert_array_equal(feats[i, :cnt[i]], tf)
+        np.testing.assert_array_equal(hits[i, :cnt[i]], th)
+
+
+def test_device_payload_corruption_is_rejected(tiny_index, tmp_path):
+    import pathlib
+
+    from paper_2411_12229_gb300._binding import SqgError
+    from paper_2411_12229_gb300.api import Index
+    data = bytearray(pathlib.Path(tiny_index[0]).read_bytes())
+    data[-200] ^= 1
+    bad = tmp_path / "bad.sqg"
+    bad.write_bytes(bytes(data))
+    with pytest.raises(SqgError) as e:
+        Index(bad, 0)
+    assert e.value.code == -3
+
+
+def test_host_buffers_end_to_end(gpu_tiny, oracle_mod):
+    ix, p, x, q = gpu_tiny
+    ids, dists = ix.search_host(q, 10, 64)
+    O = oracle_mod.Index(p)
+    for i in range(0, q.shape[0], 7):
+        np.testing.assert_array_equal(ids[i].view(np.uint32), O.search(q[i], 10, 64)[0])

@@ -1,0 +1,195 @@
+"""Host-side tests (no GPU): the C ABI's exports and host error paths, the
+index builder against the oracle's definitions, and the input generators."""
+
+import ctypes as C
+import pathlib
+import re
+
+import numpy as np
+import pytest
+
+ROOT = pathlib.Path(__file__).resolve().parents[1]
+
+
+def header_functions():
+    text = (ROOT / "include" / "sqg.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sqg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(lib_built):
+    from paper_2411_12229_gb300 import _binding
+    names = header_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib_built, n), f"libsqg.so does not export {n}"
+    assert set(names) == set(_binding.exported_symbols())
+
+
+def test_error_strings(lib_built):
+    for code in range(0, -9, -1):
+        s = lib_built.sqg_error_string(code)
+        assert s and s != b"unknown error"
+    assert lib_built.sqg_error_string(-99) == b"unknown error"
+
+
+def test_index_load_host_errors(lib_built, tmp_path, tiny_index):
+    h = C.c_void_p()
+    assert lib_built.sqg_index_load(str(tmp_path / "missing.sqg").encode(), 0, C.byref(h)) == -2
+    junk = tmp_path / "junk.sqg"
+    junk.write_bytes(b"NOPE" * 100)
+    assert lib_built.sqg_index_load(str(junk).encode(), 0, C.byref(h)) == -3
+    data = pathlib.Path(tiny_index[0]).read_bytes()
+    trunc = tmp_path / "trunc.sqg"
+    trunc.write_bytes(data[: len(data) - 128])
+    assert lib_built.sqg_index_load(str(trunc).encode(), 0, C.byref(h)) == -3
+    bad_hdr = bytearray(data[:4096])
+    bad_hdr[16] ^= 1  # d
+    hdr = tmp_path / "hdr.sqg"
+    hdr.write_bytes(bytes(bad_hdr) + data[4096:])
+    assert lib_built.sqg_index_load(str(hdr).encode(), 0, C.byref(h)) == -3
+    assert lib_built.sqg_index_load(None, 0, C.byref(h)) == -1
+    assert lib_built.sqg_index_load(str(tiny_index[0]).encode(), -1, C.byref(h)) == -1
+
+
+def test_oracle_rejects_corrupt_payload(oracle_mod, tiny_index, tmp_path):
+    data = bytearray(pathlib.Path(tiny_index[0]).read_bytes())
+    data[len(data) // 2] ^= 0x40
+    p = tmp_path / "flip.sqg"
+    p.write_bytes(bytes(data))
+    with pytest.raises(OSError):
+        oracle_mod.Index(p)
+
+
+def test_builder_codes_and_factors_match_the_definition(oracle_mod, tiny_index):
+    """The file's codes and factors (written by the library's host builder)
+    against the oracle's fp64 RaBitQ quantization of each edge (Eq. (3) with
+    the vertex as centre, Sec. 3.1.1)."""
+    p, x, _ = tiny_index
+    O = oracle_mod.Index(p)
+    rot = O.rotation()
+    rng = np.random.default_rng(0)
+    flips = 0
+    for v in rng.choice(O.n, 25, replace=False):
+        blk = O.vertex(int(v))
+        np.testing.assert_array_equal(O.raw(int(v)), x[v])
+        for j in range(O.R):
+            o = int(blk["ids"][j])
+            bits, f = oracle_mod.quantize_edge(rot, x[v], x[o])
+            vrot = rot.astype(np.float64) @ (x[o].astype(np.float64) - x[v]) / f["n_o"]
+            diff = bits != blk["bits"][j]
+            assert np.all(np.abs(vrot[diff]) < 1e-5), "a code bit differs away from a sign tie"
+            flips += int(diff.sum())
+            assert blk["popcount"][j] == blk["bits"][j].sum()
+            for name in ("f_add", "f_rescale", "f_err"):
+                assert blk[name][j] == pytest.approx(f[name], rel=2e-5, abs=2e-5 * abs(f["f_add"]))
+    assert flips <= 2
+
+
+def test_graph_invariants(oracle_mod, tiny_index):
+    """Every vertex has exactly R distinct out-neighbours, no self loop
+    (Sec. 3.2.2, degree aligned to the batch of 32), and every vertex is
+    reachable from the entry point."""
+    p, x, _ = tiny_index
+    O = oracle_mod.Index(p)
+    adj = np.stack([O.vertex(v)["ids"] for v in range(O.n)])
+    assert adj.shape == (O.n, 32)
+    assert np.all(adj < O.n)
+    assert np.all(adj != np.arange(O.n)[:, None])
+    s = np.sort(adj, axis=1)
+    assert np.all(s[:, 1:] != s[:, :-1])
+    seen = np.zeros(O.n, bool)
+    stack = [O.entry]
+    seen[O.entry] = True
+    while stack:
+        u = stack.pop()
+        for v in adj[u]:
+            if not seen[v]:
+                seen[v] = True
+                stack.append(v)
+    assert seen.all()
+
+
+def test_entry_is_the_medoid(oracle_mod, tiny_index):
+    p, x, _ = tiny_index
+    O = oracle_mod.Index(p)
+    mean = x.astype(np.float64).mean(axis=0)
+    d = np.sum((x - mean) ** 2, axis=1)
+    assert O.entry == int(np.argmin(d))
+
+
+def test_block_size_formula(oracle_mod, tiny_index, tiny_index_r64):
+    """Sec. 3.3: n(32D + 32R + DR) bits for vectors, ids and codes; the
+    block adds 3 fp32 factors and a popcount per neighbour, padded to 128 B."""
+    for p, R in ((tiny_index[0], 32), (tiny_index_r64[0], 64)):
+        O = oracle_mod.Index(p)
+        bits = 32 * O.d + 32 * R + O.d * R
+        assert O.block_bytes == -(-(bits // 8 + 16 * R) // 128) * 128
+    assert (4 * 128 + 4 * 32 + 128 * 32 // 8 + 16 * 32) == 1664  # d=128, R=32
+    assert (4 * 960 + 4 * 64 + 960 * 64 // 8 + 16 * 64) == 12800  # d=960, R=64
+
+
+def test_knn_host_matches_bruteforce(lib_built, oracle_mod):
+    from paper_2411_12229_gb300 import index_builder as ib
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((300, 64)).astype(np.float32)
+    nn = ib.knn_host(x, 8)
+    for i in range(0, 300, 37):
+        ids, _ = oracle_mod.bruteforce(x, x[i], 9)
+        assert ids[0] == i
+        np.testing.assert_array_equal(nn[i], ids[1:])
+
+
+def test_random_rotation_is_orthogonal():
+    from paper_2411_12229_gb300 import index_builder as ib
+    for d in (32, 128, 960):
+        R = ib.random_rotation(d, 2).astype(np.float64)
+        assert np.abs(R @ R.T - np.eye(d)).max() < 1e-5
+
+
+def test_random_graph_is_simple():
+    from paper_2411_12229_gb300 import index_builder as ib
+    adj = ib.random_graph(500, 32, 3)
+    assert np.all(adj != np.arange(500)[:, None])
+    s = np.sort(adj, axis=1)
+    assert np.all(s[:, 1:] != s[:, :-1])
+
+
+def test_synth_is_deterministic_and_chunk_independent():
+    from paper_2411_12229_gb300 import synth
+    w = synth.Workload("t", 70_000, 32, 16, 10, 32, dim_scale="loguniform")
+    full = synth.base(w)
+    np.testing.assert_array_equal(full[65_000:66_000], synth.base(w, 65_000, 66_000))
+    np.testing.assert_array_equal(synth.queries(w), synth.queries(w))
+    assert not np.array_equal(synth.queries(w)[0], full[0])
+
+
+def test_workload_recipes():
+    from paper_2411_12229_gb300 import synth
+    W = synth.WORKLOADS
+    t = W["tiny-10k-d128"]
+    assert (t.n, t.d, t.n_components, t.n_queries, t.degree, t.k, t.ef) == (10_000, 128, 64, 200, 32, 10,
+                                                                               (32, 64, 128))
+    b = W["batched-1m-d128"]
+    assert (b.n, b.d, b.n_components, b.n_queries, b.degree, b.dim_scale) == (1_000_000, 128, 1024, 10_000, 32,
+                                                                              "loguniform")
+    assert min(b.ef) == 16 and max(b.ef) == 512
+    h = W["highdim-1m-d960"]
+    assert (h.n, h.d, h.degree, h.n_train, h.dim_scale) == (1_000_000, 960, 64, 50_000, "power")
+    u = W["uneven-1m-d1536"]
+    assert (u.n, u.d, u.degree, u.n_queries, u.unit_norm, u.mixed_k) == (1_000_000, 1536, 32, 20_000, True,
+                                                                         (1, 10, 100))
+    s = W["serving-4m-d96"]
+    assert (s.n, s.d, s.n_components, s.degree) == (4_000_000, 96, 4096, 32)
+    # value distributions
+    hs = synth.small(h, 2000, 10)
+    xh = synth.base(hs)
+    assert xh.min() >= 0
+    v = xh.var(axis=0)
+    assert v[:10].mean() > v[-100:].mean()
+    xu = synth.base(synth.small(u, 500, 10))
+    np.testing.assert_allclose(np.linalg.norm(xu, axis=1), 1.0, rtol=1e-5)
+    k, ef = synth.query_k_ef(u, 1000)
+    assert set(np.unique(k)) == {1, 10, 100} and np.all(ef >= k) and np.all(ef <= 8 * k)
+    arr = synth.poisson_arrivals(1000.0, 5000)
+    assert np.all(np.diff(arr) > 0) and abs(5000 / arr[-1] - 1000) < 100
