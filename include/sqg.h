@@ -195,6 +195,26 @@ int sqg_search_trace(const sqg_index *ix, const float *queries, int nq, const in
                      const uint32_t *gt, int gt_k, float *trace_feat, int32_t *trace_hit, int32_t *trace_n,
                      int trace_cap, sqg_stream_t stream);
 
+/* ---- learned early stop: training kernels (not in the paper) ---- */
+
+/* Gradient of the weighted binary cross-entropy of the stop MLP:
+ *   loss = sum_b w_b [softplus(z_b) - y_b z_b] / sum_b w_b,
+ *   z_b = MLP(x_b) (16 -> 64 -> 64 -> 1, ReLU; parameter order as above).
+ * params SQG_MLP_NPARAM; x n x 16; y, w n floats (labels 0/1, weights > 0);
+ * grad (out) SQG_MLP_NPARAM; loss (out, optional) 1 float; scratch: 4
+ * bytes of caller memory for sum(w).  Overwrites grad and loss. */
+int sqg_mlp_grad(const float *params, const float *x, const float *y, const float *w, int n, float *grad,
+                 float *loss, float *scratch, sqg_stream_t stream);
+
+/* One Adam step (Kingma & Ba) on all SQG_MLP_NPARAM parameters, in place:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr (m/(1-b1^step)) / (sqrt(v/(1-b2^step)) + eps).  step >= 1. */
+int sqg_mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr, float beta1,
+                 float beta2, float eps, sqg_stream_t stream);
+
+/* Logits of the stop MLP for n feature rows (x n x 16 -> logits n). */
+int sqg_mlp_forward(const float *params, const float *x, int n, float *logits, sqg_stream_t stream);
+
 /* OR of the status bits every search on this index has raised since the
  * last call, then cleared.  Synchronizes `stream`. */
 int sqg_get_status(const sqg_index *ix, sqg_stream_t stream, uint32_t *status);

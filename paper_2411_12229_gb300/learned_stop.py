@@ -1,0 +1,158 @@
+"""Learned early termination of the search (not in the paper).
+
+A 16 -> 64 -> 64 -> 1 MLP reads the search state every `every` expansions
+and predicts whether the result set already holds everything the full
+fixed-ef search would return.  Training data are traces of the plain search
+(``sqg_search_trace``): features at every evaluation point plus the number
+of true top-k ids found so far.  A row is labelled 1 when that count already
+equals the count at the end of the full search -- stopping there loses no
+recall against the fixed-ef search, which stays the fallback cap.
+
+Training runs on the GPU with the library's own kernels (``sqg_mlp_grad``,
+``sqg_mlp_adam``); the stop itself is fused into the search kernel.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _binding as B
+
+
+@dataclasses.dataclass
+class StopModel:
+    params: torch.Tensor   # SQG_MLP_NPARAM fp32 on the device
+    logit: float           # stop when the network's logit exceeds this
+    every: int             # evaluation period in expansions
+    ef_cap: int            # fixed-ef fallback cap used with the stop
+    info: dict
+
+
+def _sp(stream=None) -> int:
+    return int((stream or torch.cuda.current_stream()).cuda_stream)
+
+
+def collect(ix, queries: np.ndarray, gt: np.ndarray, k: int, ef_cap: int, every: int, chunk: int = 8192):
+    """Features and labels from traces of the plain search at ef_cap."""
+    cap = max(1, (8 * ef_cap + 64) // every + 1)
+    feats, labels, qidx = [], [], []
+    gt_d = torch.from_numpy(np.ascontiguousarray(gt[:, :k], dtype=np.int32)).cuda()
+    for a in range(0, queries.shape[0], chunk):
+        b = min(queries.shape[0], a + chunk)
+        qd = torch.from_numpy(np.ascontiguousarray(queries[a:b])).cuda()
+        ids, _, st, f, h, n = ix.search_trace(qd, k, ef_cap, gt_d[a:b], cap, stop_every=every)
+        ids = ids.cpu().numpy()
+        f, h, n = f.cpu().numpy(), h.cpu().numpy(), n.cpu().numpy()
+        for i in range(b - a):
+            final = len(np.intersect1d(ids[i], gt[a + i, :k]))
+            m = n[i]
+            if m == 0:
+                continue
+            feats.append(f[i, :m])
+            labels.append((h[i, :m] >= final).astype(np.float32))
+            qidx.append(np.full(m, a + i, dtype=np.int32))
+    return np.concatenate(feats), np.concatenate(labels), np.concatenate(qidx)
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-initialized weights, zero biases (flat layout of include/sqg.h)."""
+    g = np.random.default_rng(seed)
+    W1 = g.standard_normal((64, 16)) * np.sqrt(2 / 16)
+    W2 = g.standard_normal((64, 64)) * np.sqrt(2 / 64)
+    W3 = g.standard_normal(64) * np.sqrt(1 / 64)
+    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), W3, [0.0]]).astype(np.float32)
+
+
+def grad(params: torch.Tensor, x: torch.Tensor, y: torch.Tensor, w: torch.Tensor, stream=None):
+    """(loss, gradient) of the weighted BCE through sqg_mlp_grad."""
+    g = torch.empty(B.MLP_NPARAM, device=params.device)
+    loss = torch.empty(1, device=params.device)
+    scratch = torch.empty(1, device=params.device)
+    B.check(B.lib().sqg_mlp_grad(params.data_ptr(), x.data_ptr(), y.data_ptr(), w.data_ptr(), x.shape[0],
+                                 g.data_ptr(), loss.data_ptr(), scratch.data_ptr(), _sp(stream)), "sqg_mlp_grad")
+    return loss, g
+
+
+def adam(params, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    B.check(B.lib().sqg_mlp_adam(params.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), step,
+                                 C.c_float(lr), C.c_float(b1), C.c_float(b2), C.c_float(eps), _sp(stream)),
+            "sqg_mlp_adam")
+
+
+def forward(params: torch.Tensor, x: torch.Tensor, stream=None) -> torch.Tensor:
+    z = torch.empty(x.shape[0], device=x.device)
+    B.check(B.lib().sqg_mlp_forward(params.data_ptr(), x.data_ptr(), x.shape[0], z.data_ptr(), _sp(stream)),
+            "sqg_mlp_forward")
+    return z
+
+
+def train(feats: np.ndarray, labels: np.ndarray, *, steps: int = 3000, batch: int = 8192, lr: float = 3e-3,
+          seed: int = 0, log=None) -> torch.Tensor:
+    """Minibatch Adam on the GPU; classes balanced by sample weights."""
+    dev = torch.device("cuda")
+    X = torch.from_numpy(np.ascontiguousarray(feats, dtype=np.float32)).to(dev)
+    Y = torch.from_numpy(np.ascontiguousarray(labels, dtype=np.float32)).to(dev)
+    pos = float(labels.mean())
+    wpos, wneg = 0.5 / max(pos, 1e-6), 0.5 / max(1 - pos, 1e-6)
+    W = torch.where(Y > 0.5, torch.tensor(wpos, device=dev), torch.tensor(wneg, device=dev)).float()
+    P = torch.from_numpy(init_params(seed)).to(dev)
+    m, v = torch.zeros_like(P), torch.zeros_like(P)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    n = X.shape[0]
+    for t in range(1, steps + 1):
+        idx = torch.randint(0, n, (min(batch, n),), device=dev, generator=gen)
+        loss, g = grad(P, X[idx].contiguous(), Y[idx].contiguous(), W[idx].contiguous())
+        adam(P, g, m, v, t, lr * (0.1 if t > 0.8 * steps else 1.0))
+        if log and (t % 1000 == 0 or t == steps):
+            log(f"stop-mlp step {t}: loss {float(loss):.4f}")
+    return P
+
+
+def evaluate(ix, queries: torch.Tensor, gt: np.ndarray, k: int, ef: int, model: StopModel | None = None,
+             logit: float | None = None, reps: int = 3):
+    """(recall, qps, mean hops) of the search with or without the stop."""
+    from .eval import recall
+    kw = {}
+    if model is not None:
+        kw = dict(stop_mlp=model.params, stop_logit=model.logit if logit is None else logit,
+                  stop_every=model.every)
+    ids, _, st = ix.search(queries, k, ef, stats=True, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ix.search(queries, k, ef, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    qps = reps * queries.shape[0] / (e0.elapsed_time(e1) / 1e3)
+    return recall(ids.cpu().numpy(), gt, k), qps, float(st[:, 0].float().mean())
+
+
+def fit(ix, train_q: np.ndarray, train_gt: np.ndarray, k: int, ef_cap: int, target: float, *, every: int = 2,
+        val_frac: float = 0.2, steps: int = 3000, seed: int = 0, log=None) -> StopModel:
+    """Trace, train, then pick the stop threshold on held-out queries: the
+    most aggressive logit whose recall still reaches `target`."""
+    nv = max(1, int(train_q.shape[0] * val_frac))
+    tq, tg = train_q[nv:], train_gt[nv:]
+    vq, vg = train_q[:nv], train_gt[:nv]
+    f, y, _ = collect(ix, tq, tg, k, ef_cap, every)
+    P = train(f, y, steps=steps, seed=seed, log=log)
+    model = StopModel(P, 0.0, every, ef_cap, dict(rows=int(f.shape[0]), positive=float(y.mean())))
+    vqd = torch.from_numpy(np.ascontiguousarray(vq)).cuda()
+    best = None
+    for thr in (4.0, 3.0, 2.0, 1.5, 1.0, 0.5, 0.0, -0.5, -1.0, -2.0):
+        r, qps, hops = evaluate(ix, vqd, vg, k, ef_cap, model, logit=thr, reps=2)
+        if log:
+            log(f"stop threshold {thr:+.1f}: recall {r:.4f} hops {hops:.1f} qps {qps:.0f}")
+        if r >= target:
+            best = thr
+        else:
+            break
+    model.logit = 4.0 if best is None else best
+    model.info.update(threshold=model.logit, val_queries=nv)
+    return model
