@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--ef-build", type=int, default=64)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--ef", type=int, default=0, help="fixed ef: skip the sweep (profiling runs)")
+    ap.add_argument("--skip-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -286,7 +288,7 @@ def main():
 
     # ---- sweep (untimed for the metric): recall, hops and QPS per ef
     sweep = []
-    for ef in w.ef:
+    for ef in ([args.ef] if args.ef else w.ef):
         ids, dists, st = ix.search(qd, k, ef, stats=True)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -303,7 +305,7 @@ def main():
         if rec >= 0.995:
             break
     pick = lambda t: next((s["ef"] for s in sweep if s["recall"] >= t), None)  # noqa: E731
-    ef_sel = pick(args.target) or sweep[-1]["ef"]
+    ef_sel = args.ef or pick(args.target) or sweep[-1]["ef"]
     if dist:
         t = torch.tensor([ef_sel], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -340,7 +342,7 @@ def main():
     ih = torch.empty((nq, k), dtype=torch.int32).pin_memory()
     dh = torch.empty((nq, k), dtype=torch.float32).pin_memory()
     e2e_ms = []
-    for s in range(args.warmup + args.steps):
+    for s in range(0 if args.skip_e2e else args.warmup + args.steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
@@ -354,11 +356,12 @@ def main():
             e2e_ms.append(a.elapsed_time(b))
     clk = clocks.stop()
     rec_sel = E.recall(out[0].view(nq, k).cpu().numpy(), gt_ids, k)
-    rec_e2e = E.recall(ih.numpy(), gt_ids, k)
+    rec_e2e = E.recall(ih.numpy(), gt_ids, k) if e2e_ms else None
     hops = st[:, 0].double().cpu().numpy()
 
     step_mean = float(np.mean(step_ms))
-    t_local = torch.tensor([step_mean, float(np.mean(e2e_ms))], device="cuda", dtype=torch.float64)
+    t_local = torch.tensor([step_mean, float(np.mean(e2e_ms)) if e2e_ms else step_mean], device="cuda",
+                           dtype=torch.float64)
     if dist:
         dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
     step_max, e2e_max = float(t_local[0]), float(t_local[1])

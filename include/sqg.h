@@ -81,7 +81,7 @@ typedef struct {
     float eps0;              /* admission key = estimate - eps0 * bound; 0 = Algorithm 1 */
     int32_t multi_estimate;  /* 1: every unvisited neighbour enters the beam (Sec. 3.1.2);
                                 0: ablation "w/o ME", the first estimate only (Sec. 5.4) */
-    int32_t hop_cap;         /* expansions per query; 0 = 8*ef + 64 */
+    int32_t hop_cap;         /* expansions per query; 0 = 4*ef + 64 */
     int32_t max_k, max_ef;   /* bounds of the batch's k[] and ef[]; 0 = read them from the
                                 device (sqg_search then synchronizes the stream once) */
     const float *stop_mlp;   /* device, SQG_MLP_NPARAM floats, or NULL: learned stop off */
@@ -182,18 +182,23 @@ int sqg_prepare_queries(const sqg_index *ix, const float *queries, int nq, float
 int sqg_estimate_block(const sqg_index *ix, const float *queries, int nq, const uint32_t *v, float eps0,
                        int32_t *out_S, float *out_est, float *out_key, float *out_dist_c, sqg_stream_t stream);
 
-/* sqg_search_ex that also records the learned stop's training data (not in
- * the paper).  At every stop_every-th expansion once the result holds k
- * entries, query i appends the 16 search-state features (fp32) to
+/* sqg_search_ex that also records what the search did.
+ * Learned-stop training data (not in the paper; trace_feat may be NULL): at
+ * every stop_every-th expansion once the result holds k entries, query i
+ * appends the 16 search-state features (fp32) to
  * trace_feat[(i*trace_cap + t)*16 ...] and, when gt is given (nq x gt_k
  * ground-truth ids, gt_k >= every k[i]), the number of the first k[i] gt ids
  * present in its current result to trace_hit[i*trace_cap + t]; trace_n[i]
- * receives the number of rows written (at most trace_cap).  Scratch comes
- * from the stream-ordered allocator. */
+ * receives the number of rows written (at most trace_cap).
+ * Expansion order (path may be NULL): path[i*path_cap + h] = id of the h-th
+ * vertex query i expanded (Algorithm 1, line 3), for h < min(hops,
+ * path_cap); the rest is left untouched.  Used by the index builder
+ * (search-path candidates) and by parity tests.  At least one of trace_feat
+ * and path must be given.  Scratch comes from the stream-ordered allocator. */
 int sqg_search_trace(const sqg_index *ix, const float *queries, int nq, const int32_t *k, const int32_t *ef,
                      uint32_t *out_ids, float *out_dists, const sqg_search_params *params, sqg_query_stats *stats,
                      const uint32_t *gt, int gt_k, float *trace_feat, int32_t *trace_hit, int32_t *trace_n,
-                     int trace_cap, sqg_stream_t stream);
+                     int trace_cap, uint32_t *path, int path_cap, sqg_stream_t stream);
 
 /* ---- learned early stop: training kernels (not in the paper) ---- */
 

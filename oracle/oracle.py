@@ -184,7 +184,7 @@ class Index:
 
 def default_hop_cap(ef: int) -> int:
     """Hop cap used when the caller gives none (a safety bound, R6)."""
-    return 8 * int(ef) + 64
+    return 4 * int(ef) + 64
 
 
 def rotate_f64(rot, q) -> np.ndarray:

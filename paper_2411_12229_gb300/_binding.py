@@ -55,7 +55,8 @@ _SIGS = {
     "sqg_workspace_size": (SZ, [P, I32, I32, I32]),
     "sqg_search": (I32, [P, P, I32, P, P, P, P, P]),
     "sqg_search_ex": (I32, [P, P, I32, P, P, P, P, C.POINTER(SearchParams), P, SZ, P, P]),
-    "sqg_search_trace": (I32, [P, P, I32, P, P, P, P, C.POINTER(SearchParams), P, P, I32, P, P, P, I32, P]),
+    "sqg_search_trace": (I32, [P, P, I32, P, P, P, P, C.POINTER(SearchParams), P, P, I32, P, P, P, I32, P, I32,
+                              P]),
     "sqg_prepare_queries": (I32, [P, P, I32, P, P, P, P]),
     "sqg_estimate_block": (I32, [P, P, I32, P, F32, P, P, P, P, P]),
     "sqg_get_status": (I32, [P, P, C.POINTER(U32)]),

@@ -126,26 +126,32 @@ class Index:
         B.check(rc, "sqg_search")
 
     def search_trace(self, queries: torch.Tensor, k: int, ef: int, gt: torch.Tensor | None, trace_cap: int,
-                     stream=None, **kw):
+                     stream=None, path_cap: int = 0, **kw):
         """Search that records the learned stop's features (and hits against
-        gt) at every evaluation point.  Returns ids, dists, stats, feats
-        (nq, cap, 16), hits (nq, cap), counts (nq,)."""
+        gt) at every evaluation point, and/or the expansion order.  Returns
+        ids, dists, stats, feats (nq, cap, 16), hits (nq, cap), counts (nq,)
+        and, with path_cap > 0, path (nq, path_cap; -1 past the last hop)."""
         nq, dev = queries.shape[0], queries.device
         kt, et = _i32(k, nq, dev), _i32(ef, nq, dev)
         ids = torch.empty(nq * k, dtype=torch.int32, device=dev)
         dists = torch.empty(nq * k, dtype=torch.float32, device=dev)
         st = torch.empty((nq, 2), dtype=torch.int32, device=dev)
-        feats = torch.zeros((nq, trace_cap, B.MLP_IN), dtype=torch.float32, device=dev)
-        hits = torch.full((nq, trace_cap), -1, dtype=torch.int32, device=dev)
-        cnt = torch.zeros(nq, dtype=torch.int32, device=dev)
+        feats = hits = cnt = None
+        if trace_cap > 0:
+            feats = torch.zeros((nq, trace_cap, B.MLP_IN), dtype=torch.float32, device=dev)
+            hits = torch.full((nq, trace_cap), -1, dtype=torch.int32, device=dev)
+            cnt = torch.zeros(nq, dtype=torch.int32, device=dev)
+        path = torch.full((nq, path_cap), -1, dtype=torch.int32, device=dev) if path_cap > 0 else None
         p = self.params(max_k=k, max_ef=ef, **kw)
         gtp, gtk = (gt.data_ptr(), gt.shape[1]) if gt is not None else (None, 0)
+        ptr = lambda t: t.data_ptr() if t is not None else None  # noqa: E731
         rc = B.lib().sqg_search_trace(self._h, queries.contiguous().data_ptr(), nq, kt.data_ptr(), et.data_ptr(),
                                       ids.data_ptr(), dists.data_ptr(), C.byref(p), st.data_ptr(), gtp, gtk,
-                                      feats.data_ptr(), hits.data_ptr(), cnt.data_ptr(), trace_cap,
+                                      ptr(feats), ptr(hits), ptr(cnt), trace_cap, ptr(path), path_cap,
                                       _stream_ptr(stream))
         B.check(rc, "sqg_search_trace")
-        return ids.view(nq, k), dists.view(nq, k), st, feats, hits, cnt
+        out = (ids.view(nq, k), dists.view(nq, k), st, feats, hits, cnt)
+        return out + (path,) if path_cap > 0 else out
 
     def workspace_size(self, nq: int, max_k: int, max_ef: int) -> int:
         n = B.lib().sqg_workspace_size(self._h, nq, max_k, max_ef)

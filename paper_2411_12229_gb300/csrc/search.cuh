@@ -64,6 +64,8 @@ struct SearchArgs {
     int trace_cap;
     const uint32_t *gt; // nq x gt_k ground-truth ids (trace mode)
     int gt_k;
+    uint32_t *path;     // nq x path_cap: ids of the first expanded vertices, or null
+    int path_cap;
     uint32_t warp_bytes, cta_bytes;
     uint32_t o_buf0, o_buf1, o_bar, o_pkey, o_pid, o_hash, o_rkey, o_rid, o_planes;
 };
@@ -303,7 +305,7 @@ __device__ __forceinline__ float mlp_logit_warp(const float *w, const float (&f)
 
 // ---------------------------------------------------------------- the kernel
 template <int CH, int NB>
-__global__ void __launch_bounds__(128, 1) search_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(128, (CH <= 2 ? 5 : 3)) search_kernel(const SearchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t R = a.R, d = a.d, nch = d / 4, nw = d / 32;
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(128, 1) search_kernel(const SearchArgs a) {
             }
             continue;
         }
-        const int hop_cap = a.hop_cap > 0 ? a.hop_cap : 8 * ef + 64;
+        const int hop_cap = a.hop_cap > 0 ? a.hop_cap : 4 * ef + 64;
 
         // ---- query setup: raw query in registers, quantized rotated query planes
         float4 qv[CH];
@@ -408,7 +410,10 @@ __global__ void __launch_bounds__(128, 1) search_kernel(const SearchArgs a) {
             const uint32_t p = pid[cur] & kIdMask;
             for (int i = cur + lane; i < m; i += 32)
                 if ((pid[i] & kIdMask) == p) pid[i] = p | kVisited;
-            if (lane == 0) hash_insert(H, a.hash_bits, p);
+            if (lane == 0) {
+                hash_insert(H, a.hash_bits, p);
+                if (a.path && hops < a.path_cap) a.path[(size_t)qi * a.path_cap + hops] = p;
+            }
             __syncwarp();
             ++hops;
             // next unvisited beam entry after cur

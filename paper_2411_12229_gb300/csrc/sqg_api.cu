@@ -236,7 +236,7 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     pl.ch = pick_ch(d);
     pl.nb = (int)(R / 32);
     if (pl.ch < 0 || (pl.nb != 1 && pl.nb != 2)) return SQG_ERR_UNSUPPORTED;
-    const long long cap = p.hop_cap > 0 ? p.hop_cap : 8LL * max_ef + 64;
+    const long long cap = p.hop_cap > 0 ? p.hop_cap : 4LL * max_ef + 64;
     uint32_t bits = 5;
     while ((1ull << bits) < 2ull * (unsigned long long)cap + 1) ++bits;
     if (bits > 26) return SQG_ERR_CAPACITY;
@@ -465,7 +465,8 @@ extern "C" size_t sqg_workspace_size(const sqg_index *ix, int nq, int max_k, int
 static int search_impl(const sqg_index *ix, const float *queries, int nq, const int32_t *k, const int32_t *ef,
                        uint32_t *out_ids, float *out_dists, const sqg_search_params *params, void *workspace,
                        size_t ws_bytes, sqg_query_stats *stats, cudaStream_t stream, float *trace_feat,
-                       int32_t *trace_hit, int32_t *trace_n, int trace_cap, const uint32_t *gt, int gt_k) {
+                       int32_t *trace_hit, int32_t *trace_n, int trace_cap, const uint32_t *gt, int gt_k,
+                       uint32_t *path = nullptr, int path_cap = 0) {
     if (!ix || nq < 0) return SQG_ERR_INVALID_ARG;
     if (nq == 0) return SQG_OK;
     if (!queries || !k || !ef || !out_ids || !out_dists) return SQG_ERR_INVALID_ARG;
@@ -535,6 +536,8 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     a.trace_cap = trace_cap;
     a.gt = gt;
     a.gt_k = gt_k;
+    a.path = path;
+    a.path_cap = path_cap;
 
     plan_kernel<<<1, kPlanThreads, 0, stream>>>(k, ef, nq, const_cast<long long *>(a.offsets),
                                                 reinterpret_cast<int *>(ws + pl.ws_maxes));
@@ -572,10 +575,14 @@ extern "C" int sqg_search_trace(const sqg_index *ix, const float *queries, int n
                                 const int32_t *ef, uint32_t *out_ids, float *out_dists,
                                 const sqg_search_params *params, sqg_query_stats *stats, const uint32_t *gt,
                                 int gt_k, float *trace_feat, int32_t *trace_hit, int32_t *trace_n, int trace_cap,
-                                sqg_stream_t stream) {
-    if (!trace_feat || !trace_n || trace_cap < 1 || (gt && (!trace_hit || gt_k < 1))) return SQG_ERR_INVALID_ARG;
+                                uint32_t *path, int path_cap, sqg_stream_t stream) {
+    if (trace_feat && (!trace_n || trace_cap < 1)) return SQG_ERR_INVALID_ARG;
+    if (gt && (!trace_feat || !trace_hit || gt_k < 1)) return SQG_ERR_INVALID_ARG;
+    if ((path && path_cap < 1) || (!path && !trace_feat)) return SQG_ERR_INVALID_ARG;
+    if (!trace_feat) trace_cap = 0;
     return search_impl(ix, queries, nq, k, ef, out_ids, out_dists, params, nullptr, 0, stats,
-                       reinterpret_cast<cudaStream_t>(stream), trace_feat, trace_hit, trace_n, trace_cap, gt, gt_k);
+                       reinterpret_cast<cudaStream_t>(stream), trace_feat, trace_hit, trace_n, trace_cap, gt, gt_k,
+                       path, path ? path_cap : 0);
 }
 
 extern "C" int sqg_prepare_queries(const sqg_index *ix, const float *queries, int nq, float *out_qrot,

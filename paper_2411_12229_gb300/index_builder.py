@@ -101,13 +101,16 @@ def random_graph(n: int, R: int, seed: int) -> np.ndarray:
 
 
 def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None, ef_build: int = 128,
-                cand_k: int | None = None, rot_seed: int = 2, graph_seed: int = 3, device: int | None = None,
-                init: str = "auto", threads: int = 0, log=None) -> dict:
+                cand_k: int | None = None, path_cand: int | None = None, rot_seed: int = 2, graph_seed: int = 3,
+                device: int | None = None, init: str = "auto", threads: int = 0, log=None) -> dict:
     """Build an index file at `path` from base vectors `data` (n x d).
 
     device=None: host-only build from an exact kNN (small n).
-    device given: Algorithm 2 with the GPU search providing the candidates;
-    init "random" (the paper) or "knn" (host brute force, small n)."""
+    device given: Algorithm 2 with the GPU search providing the candidates
+    of every vertex: the cand_k nearest vertices the search expanded plus
+    the first path_cand vertices on its path from the entry point (as NSG
+    takes the visited set, so that long edges between regions survive the
+    pruning); init "random" (the paper) or "knn" (host brute force)."""
     t0 = time.time()
     data = np.ascontiguousarray(data, dtype=np.float32)
     n, d = data.shape
@@ -134,15 +137,22 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
         dev = torch.device("cuda", device)
         xd = torch.from_numpy(data).to(dev)
         k_res = min(cand_k, n)
+        pc = R if path_cand is None else path_cand
         for it in range(iterations):
             t1 = time.time()
             ix = Index(tmp, device)
-            cand = np.empty((n, k_res), dtype=np.uint32)
+            cand = np.empty((n, k_res + pc), dtype=np.uint32)
             step = 1 << 18
-            for a in range(0, n, step):
-                b = min(n, a + step)
-                ids, _ = ix.search(xd[a:b], k_res, max(ef_build, k_res))
-                cand[a:b] = ids.cpu().numpy().view(np.uint32)
+            with torch.cuda.device(dev):
+                for a in range(0, n, step):
+                    b = min(n, a + step)
+                    if pc > 0:
+                        r = ix.search_trace(xd[a:b], k_res, max(ef_build, k_res), None, 0, path_cap=pc)
+                        ids, path = r[0], r[-1]
+                        cand[a:b] = torch.cat([ids, path], 1).cpu().numpy().view(np.uint32)
+                    else:
+                        ids, _ = ix.search(xd[a:b], k_res, max(ef_build, k_res))
+                        cand[a:b] = ids.cpu().numpy().view(np.uint32)
             ix.close()
             adj, st = build_graph(data, cand, R, entry, graph_seed + it + 1, threads)
             final = it == iterations - 1

@@ -38,7 +38,7 @@ def _sp(stream=None) -> int:
 
 def collect(ix, queries: np.ndarray, gt: np.ndarray, k: int, ef_cap: int, every: int, chunk: int = 8192):
     """Features and labels from traces of the plain search at ef_cap."""
-    cap = max(1, (8 * ef_cap + 64) // every + 1)
+    cap = max(1, (4 * ef_cap + 64) // every + 1)
     feats, labels, qidx = [], [], []
     gt_d = torch.from_numpy(np.ascontiguousarray(gt[:, :k], dtype=np.int32)).cuda()
     for a in range(0, queries.shape[0], chunk):

@@ -1,0 +1,102 @@
+"""Learned early stop on the GPU: the training kernels against the oracle's
+fp64 forward/backward/Adam, and what the trained stop gains over the plain
+fixed-ef search at equal recall."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    P = (rng.standard_normal(5313) * 0.3).astype(np.float32)
+    x = rng.standard_normal((n, 16)).astype(np.float32)
+    y = (rng.uniform(size=n) > 0.4).astype(np.float32)
+    w = rng.uniform(0.2, 3.0, size=n).astype(np.float32)
+    return P, x, y, w
+
+
+@pytest.mark.parametrize("n", [1, 127, 1000])
+def test_mlp_gradient_matches_oracle(lib_built, oracle_mod, n):
+    from paper_2411_12229_gb300 import learned_stop as L
+    P, x, y, w = _data(n, n)
+    loss, g = L.grad(torch.from_numpy(P).cuda(), torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(),
+                     torch.from_numpy(w).cuda())
+    lref, gref = oracle_mod.mlp_loss_grad_f64(P.astype(np.float64), x, y, w)
+    assert float(loss) == pytest.approx(lref, rel=1e-4)
+    g = g.cpu().numpy().astype(np.float64)
+    scale = np.abs(gref).max()
+    assert np.abs(g - gref).max() <= 1e-4 * scale + 1e-7
+
+
+def test_mlp_adam_matches_oracle(lib_built, oracle_mod):
+    from paper_2411_12229_gb300 import learned_stop as L
+    rng = np.random.default_rng(1)
+    p = rng.standard_normal(5313)
+    m = rng.standard_normal(5313) * 0.01
+    v = np.abs(rng.standard_normal(5313)) * 0.01
+    g = rng.standard_normal(5313)
+    pd, md, vd, gd = (torch.from_numpy(a.astype(np.float32)).cuda() for a in (p, m, v, g))
+    for t in (1, 7):
+        L.adam(pd, gd, md, vd, t, 1e-3)
+        oracle_mod.adam_step_f64(p, m, v, g, t, 1e-3)
+        np.testing.assert_allclose(pd.cpu().numpy(), p, rtol=1e-5, atol=1e-6)
+        np.testing.assert_allclose(md.cpu().numpy(), m, rtol=1e-5, atol=1e-7)
+        np.testing.assert_allclose(vd.cpu().numpy(), v, rtol=1e-5, atol=1e-7)
+
+
+def test_mlp_forward_matches_oracle(lib_built, oracle_mod):
+    from paper_2411_12229_gb300 import learned_stop as L
+    P, x, _, _ = _data(300, 3)
+    z = L.forward(torch.from_numpy(P).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = np.array([oracle_mod.mlp_logit_f32(P, x[i]) for i in range(300)])
+    np.testing.assert_allclose(z, ref, rtol=1e-5, atol=1e-5)
+
+
+def test_training_lowers_the_loss(lib_built, oracle_mod):
+    """A few hundred Adam steps with the library's kernels fit a separable
+    toy labelling (loss well below log 2)."""
+    from paper_2411_12229_gb300 import learned_stop as L
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((20000, 16)).astype(np.float32)
+    y = ((x[:, 0] + 0.5 * x[:, 3] - x[:, 7]) > 0.2).astype(np.float32)
+    P = L.train(x, y, steps=600, batch=4096, lr=3e-3)
+    lref, _ = oracle_mod.mlp_loss_grad_f64(P.cpu().numpy().astype(np.float64), x, y, np.ones(20000, np.float32))
+    assert lref < 0.2
+
+
+@pytest.fixture(scope="module")
+def stop_setup(tmp_path_factory, lib_built):
+    """A 30,000-vertex index built on the GPU (Algorithm 2) with test and
+    training queries and their exact ground truth."""
+    from paper_2411_12229_gb300 import eval as E
+    from paper_2411_12229_gb300 import index_builder as ib
+    from paper_2411_12229_gb300 import synth
+    from paper_2411_12229_gb300.api import Index
+    w = synth.small(synth.BATCHED_1M_D128, 30_000, 1000)
+    x = synth.base(w)
+    p = tmp_path_factory.mktemp("stop") / "s.sqg"
+    ib.build_index(p, x, 32, device=0, init="random", iterations=3, ef_build=64)
+    q, tq = synth.queries(w), synth.train_queries(w, 6000)
+    g, _ = E.ground_truth(x, q, 10, device=0)
+    tg, _ = E.ground_truth(x, tq, 10, device=0)
+    return Index(p, 0), q, g, tq, tg
+
+
+def test_learned_stop_saves_work_at_equal_recall(stop_setup):
+    """The trained stop (fused in the search kernel, fixed-ef fallback cap)
+    reaches the plain search's recall with fewer expansions."""
+    from paper_2411_12229_gb300 import learned_stop as L
+    ix, q, g, tq, tg = stop_setup
+    qd = torch.from_numpy(q).cuda()
+    plain = {ef: L.evaluate(ix, qd, g, 10, ef, reps=1) for ef in (16, 24, 32, 48, 64, 96, 128)}
+    ef_t = next((ef for ef, r in plain.items() if r[0] >= 0.95), 128)
+    target = plain[ef_t][0]
+    model = L.fit(ix, tq, tg, 10, 2 * ef_t, target, every=2, steps=2000)
+    r, qps, hops = L.evaluate(ix, qd, g, 10, model.ef_cap, model, reps=1)
+    print(f"plain ef={ef_t}: recall {target:.4f} hops {plain[ef_t][2]:.1f}; "
+          f"stop (cap {model.ef_cap}, logit {model.logit}): recall {r:.4f} hops {hops:.1f}")
+    assert r >= target - 0.01
+    assert hops < plain[ef_t][2]

@@ -266,6 +266,21 @@ def test_trace_features_bit_exact(gpu_tiny, oracle_mod):
         np.testing.assert_array_equal(hits[i, :cnt[i]], th)
 
 
+@pytest.mark.parametrize("ef", [16, 64])
+def test_expansion_order_identical(gpu_tiny, oracle_mod, ef):
+    """Algorithm 1 line 3: the sequence of expanded vertices, hop by hop,
+    is the oracle's (the strongest form of search-path parity)."""
+    ix, p, x, q = gpu_tiny
+    O = oracle_mod.Index(p)
+    r = ix.search_trace(torch.from_numpy(q).cuda(), 10, ef, None, 0, path_cap=512)
+    st, path = _np(r[2]), _np(r[-1]).view(np.uint32)
+    for i in range(q.shape[0]):
+        opath = O.search(q[i], 10, ef, path_cap=512)[-1]
+        assert st[i, 0] == len(opath)
+        np.testing.assert_array_equal(path[i, :len(opath)], opath)
+        assert np.all(path[i, len(opath):] == 0xFFFFFFFF)
+
+
 def test_device_payload_corruption_is_rejected(tiny_index, tmp_path):
     import pathlib
 
