@@ -96,8 +96,8 @@ class Index:
         nq, dev = queries.shape[0], queries.device
         kt, et = _i32(k, nq, dev), _i32(ef, nq, dev)
         uniform = not isinstance(k, torch.Tensor) and np.ndim(k) == 0
-        total = int(k) * nq if uniform else int(kt.clamp(0, B.MAX_K).sum().item())
-        if out is None:
+        if out is None:  # (with `out` given nothing here waits on the device)
+            total = int(k) * nq if uniform else int(kt.clamp(0, B.MAX_K).sum().item())
             ids = torch.empty(total, dtype=torch.int32, device=dev)
             dists = torch.empty(total, dtype=torch.float32, device=dev)
         else:

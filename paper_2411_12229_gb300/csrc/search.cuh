@@ -51,8 +51,9 @@ struct SearchArgs {
     uint32_t *status_word;   // OR of all status bits
     unsigned int *queue_head;
     int max_k, max_ef, hop_cap;
-    uint32_t hash_bits;
-    uint32_t *ghash;  // per-warp hash tables in global memory, or null (shared)
+    uint32_t hash_bits;   // full visited table: 2^hash_bits >= 2 * hop cap + 1
+    uint32_t shash_bits;  // shared-memory table (<= hash_bits)
+    uint32_t *ghash;      // per-warp full tables in global memory when shash_bits < hash_bits
     float eps0;
     int multi_estimate;
     const float *mlp;
@@ -135,6 +136,21 @@ __device__ __forceinline__ void hash_insert(uint32_t *H, uint32_t bits, uint32_t
         if (v == kEmpty) { H[s] = id; return; }
         s = (s + 1) & mask;
     }
+}
+// Warp: move every id of the shared table `S` into the cleared global table
+// `G` (concurrent inserts by compare-and-swap).
+__device__ __forceinline__ void hash_migrate(const uint32_t *S, uint32_t sbits, uint32_t *G, uint32_t gbits,
+                                             int lane) {
+    const uint32_t gsize = 1u << gbits, gmask = gsize - 1u;
+    for (uint32_t i = lane; i < gsize; i += 32) G[i] = kEmpty;
+    __syncwarp();
+    for (uint32_t i = lane; i < (1u << sbits); i += 32) {
+        const uint32_t id = S[i];
+        if (id == kEmpty) continue;
+        uint32_t s = hslot(id, gbits);
+        while (atomicCAS(&G[s], kEmpty, id) != kEmpty) s = (s + 1) & gmask;
+    }
+    __syncwarp();
 }
 __device__ __forceinline__ bool hash_contains(const uint32_t *H, uint32_t bits, uint32_t id) {
     const uint32_t mask = (1u << bits) - 1u;
@@ -340,8 +356,10 @@ __global__ void __launch_bounds__(128, (CH <= 2 ? 5 : 3)) search_kernel(const Se
     uint32_t *rid = reinterpret_cast<uint32_t *>(ws + a.o_rid);
     uint32_t *planes = reinterpret_cast<uint32_t *>(ws + a.o_planes);
     const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
-    uint32_t *H = a.ghash ? a.ghash + ((size_t)gwarp << a.hash_bits) : reinterpret_cast<uint32_t *>(ws + a.o_hash);
-    const uint32_t hsize = 1u << a.hash_bits;
+    // visited set: a shared-memory table, moved once to this warp's global
+    // table if a query's expansions fill half of it
+    uint32_t *const Hs = reinterpret_cast<uint32_t *>(ws + a.o_hash);
+    uint32_t *const Hg = a.ghash ? a.ghash + ((size_t)gwarp << a.hash_bits) : nullptr;
 
     if (lane == 0) {
         mbar_init(&bar[0], 1);
@@ -385,7 +403,9 @@ __global__ void __launch_bounds__(128, (CH <= 2 ? 5 : 3)) search_kernel(const Se
             qv[t] = c < nch ? reinterpret_cast<const float4 *>(q)[c] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const QuerySide qs = quantize_warp(a.qrot + (size_t)qi * d, d, planes, lane);
-        for (uint32_t i = lane; i < hsize; i += 32) H[i] = kEmpty;
+        uint32_t *H = Hs;
+        uint32_t hbits = a.shash_bits;
+        for (uint32_t i = lane; i < (1u << hbits); i += 32) H[i] = kEmpty;
 
         // ---- Algorithm 1, line 1: the beam and the result start from the entry
         int m = 1, cur = 0, rc = 0;
@@ -411,11 +431,16 @@ __global__ void __launch_bounds__(128, (CH <= 2 ? 5 : 3)) search_kernel(const Se
             for (int i = cur + lane; i < m; i += 32)
                 if ((pid[i] & kIdMask) == p) pid[i] = p | kVisited;
             if (lane == 0) {
-                hash_insert(H, a.hash_bits, p);
+                hash_insert(H, hbits, p);
                 if (a.path && hops < a.path_cap) a.path[(size_t)qi * a.path_cap + hops] = p;
             }
             __syncwarp();
             ++hops;
+            if (Hg && H == Hs && (uint32_t)hops >= (1u << hbits) / 2) {
+                hash_migrate(Hs, hbits, Hg, a.hash_bits, lane);
+                H = Hg;
+                hbits = a.hash_bits;
+            }
             // next unvisited beam entry after cur
             int nxt = m;
             for (int base = cur + 1; base < m; base += 32) {
@@ -491,7 +516,7 @@ __global__ void __launch_bounds__(128, (CH <= 2 ? 5 : 3)) search_kernel(const Se
                 // line 6: only unvisited neighbours enter; an entry that the cut
                 // to ef would drop at once is skipped early
                 adm[t] = !full || kless(ck[t], cid[t], wk, wi);
-                if (adm[t]) adm[t] = !hash_contains(H, a.hash_bits, cid[t]);
+                if (adm[t]) adm[t] = !hash_contains(H, hbits, cid[t]);
             }
             if (!a.multi_estimate) {  // ablation w/o ME: skip ids already in the beam
 #pragma unroll

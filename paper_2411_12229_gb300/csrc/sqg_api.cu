@@ -253,18 +253,16 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     a.o_pid = (uint32_t)o; o = align_up(o + 4 * (size_t)max_ef, 16);
     a.o_rkey = (uint32_t)o; o = align_up(o + 4 * (size_t)max_k, 16);
     a.o_rid = (uint32_t)o; o = align_up(o + 4 * (size_t)max_k, 16);
-    const size_t base = o;
-    pl.ghash = hash_bytes > 16384;
+    // visited set: up to 2^10 slots in shared memory; a longer search moves
+    // to its warp's full-size table in the workspace
+    a.shash_bits = std::min<uint32_t>(bits, 10);
+    pl.ghash = a.shash_bits < bits;
     a.o_hash = (uint32_t)o;
-    size_t warp_bytes = align_up(base + (pl.ghash ? 0 : hash_bytes), 128);
+    const size_t warp_bytes = align_up(o + ((size_t)4 << a.shash_bits), 128);
     const size_t cta = p.stop_mlp ? align_up(sizeof(float) * SQG_MLP_NPARAM, 128) : 0;
     int warps = p.warps_per_block > 0 ? p.warps_per_block : 4;
     warps = std::min(warps, 4);
     while (warps > 1 && cta + warps * warp_bytes > ix->smem_optin) --warps;
-    if (cta + warps * warp_bytes > ix->smem_optin && !pl.ghash) {
-        pl.ghash = true;
-        warp_bytes = align_up(base, 128);
-    }
     if (cta + warps * warp_bytes > ix->smem_optin) return SQG_ERR_CAPACITY;
     a.warp_bytes = (uint32_t)warp_bytes;
     a.cta_bytes = (uint32_t)cta;

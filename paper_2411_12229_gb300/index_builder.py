@@ -148,8 +148,7 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
                     b = min(n, a + step)
                     if pc > 0:
                         r = ix.search_trace(xd[a:b], k_res, max(ef_build, k_res), None, 0, path_cap=pc)
-                        ids, path = r[0], r[-1]
-                        cand[a:b] = torch.cat([ids, path], 1).cpu().numpy().view(np.uint32)
+                        cand[a:b] = torch.cat([r[0], r[-1]], 1).cpu().numpy().view(np.uint32)
                     else:
                         ids, _ = ix.search(xd[a:b], k_res, max(ef_build, k_res))
                         cand[a:b] = ids.cpu().numpy().view(np.uint32)

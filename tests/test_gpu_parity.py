@@ -220,11 +220,13 @@ def test_caller_workspace_matches_own_allocation(gpu_tiny):
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
 
 
-def test_large_ef_uses_global_hash(gpu_tiny, oracle_mod):
-    """ef = 1024: the visited hash no longer fits the shared-memory budget
-    and lives in the workspace; results unchanged."""
+@pytest.mark.parametrize("ef", [1024, 2048])
+def test_large_ef_migrates_the_visited_set(gpu_tiny, oracle_mod, ef):
+    """Past 512 expansions the visited set moves from shared memory to the
+    warp's table in the workspace; the search is unchanged."""
     ix, p, x, q = gpu_tiny
-    _check_search(ix, oracle_mod.Index(p), q[:16], 10, 1024)
+    _, _, st = _check_search(ix, oracle_mod.Index(p), q[:16], 10, ef)
+    assert st[:, 0].max() > 512
 
 
 def test_learned_stop_constant_networks(gpu_tiny, oracle_mod):
