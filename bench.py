@@ -402,7 +402,8 @@ def main():
                    "queries_per_step": nq, "recall@10": round(rec_sel, 4), "parallelism": f"replicas{world}",
                    "l2": "flushed (512 MiB write) between timed steps"},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(nq * w.d * 4),
-                "d2h_bytes_per_step": int(nq * k * 8), "recall@10": round(rec_e2e, 4)},
+                "d2h_bytes_per_step": int(nq * k * 8),
+                "recall@10": round(rec_e2e, 4) if rec_e2e is not None else None},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "gpu_launches": 3 * args.steps,

@@ -91,6 +91,12 @@ typedef struct {
     int32_t warps_per_block; /* 0 = library default */
     void *timing_events[2];  /* optional cudaEvent_t pair recorded on the stream right before
                                 and right after the search kernel; NULL = none */
+    int32_t visited_smem_log2; /* log2 of the visited set's shared-memory slots (5..12;
+                                  0 = 10); a search past half of them continues in a
+                                  full-size table in the workspace */
+    int32_t prefetch;        /* 1 (default, 0): next block copied into a second shared
+                                buffer during the merge; 2: also L2-prefetch the
+                                runner-up candidate's block */
 } sqg_search_params;
 
 typedef struct {

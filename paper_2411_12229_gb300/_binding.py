@@ -34,7 +34,8 @@ class SearchParams(C.Structure):
     _fields_ = [("eps0", C.c_float), ("multi_estimate", C.c_int32), ("hop_cap", C.c_int32),
                 ("max_k", C.c_int32), ("max_ef", C.c_int32), ("stop_mlp", C.c_void_p),
                 ("stop_logit", C.c_float), ("stop_every", C.c_int32), ("team", C.c_int32),
-                ("warps_per_block", C.c_int32), ("timing_events", C.c_void_p * 2)]
+                ("warps_per_block", C.c_int32), ("timing_events", C.c_void_p * 2),
+                ("visited_smem_log2", C.c_int32), ("prefetch", C.c_int32)]
 
 
 class Info(C.Structure):

@@ -59,6 +59,7 @@ struct SearchArgs {
     const float *mlp;
     float stop_logit;
     int stop_every;
+    int prefetch;       // 1: next block only; 2: also L2-prefetch the runner-up
     float *trace_feat;  // nq x trace_cap x 16, or null
     int32_t *trace_hit; // nq x trace_cap
     int32_t *trace_n;   // nq
@@ -552,8 +553,9 @@ __global__ void __launch_bounds__(128, (CH <= 2 ? 5 : 3)) search_kernel(const Se
             int rank[NB];
 #pragma unroll
             for (int t = 0; t < NB; ++t) rank[t] = 0;
-            float bk = __int_as_float(0x7f800000);
-            uint32_t bi = kEmpty;
+            const float kInf = __int_as_float(0x7f800000);
+            float bk = kInf, b2k = kInf;  // best and second-best admitted candidates
+            uint32_t bi = kEmpty, b2i = kEmpty;
 #pragma unroll
             for (int t2 = 0; t2 < NB; ++t2) {
                 uint32_t mm = am[t2];
@@ -564,20 +566,47 @@ __global__ void __launch_bounds__(128, (CH <= 2 ? 5 : 3)) search_kernel(const Se
                     const uint32_t oi = __shfl_sync(kFull, cid[t2], src);
 #pragma unroll
                     for (int t = 0; t < NB; ++t) rank[t] += kless(ok, oi, ck[t], cid[t]) ? 1 : 0;
-                    if (kless(ok, oi, bk, bi)) { bk = ok; bi = oi; }
+                    if (kless(ok, oi, bk, bi)) {
+                        b2k = bk; b2i = bi; bk = ok; bi = oi;
+                    } else if (kless(ok, oi, b2k, b2i)) {
+                        b2k = ok; b2i = oi;
+                    }
                 }
             }
             // ---- memory prefetching (Sec. 3.1.4): the next vertex is the smaller
             // of the first unvisited beam entry and the best admitted candidate
-            uint32_t next_id = kEmpty;
-            if (nxt < m) {
-                const float nk = pkey[nxt];
-                const uint32_t ni = pid[nxt] & kIdMask;
-                next_id = (nadm > 0 && kless(bk, bi, nk, ni)) ? bi : ni;
-            } else if (nadm > 0) {
-                next_id = bi;
+            uint32_t next_id = kEmpty, runner_id = kEmpty;
+            {
+                const float nk = nxt < m ? pkey[nxt] : kInf;
+                const uint32_t ni = nxt < m ? (pid[nxt] & kIdMask) : kEmpty;
+                const bool cand_first = nadm > 0 && kless(bk, bi, nk, ni);
+                next_id = cand_first ? bi : ni;
+                if (a.prefetch == 2) {  // speculative: the runner-up, if no better candidate appears
+                    float rk = cand_first ? nk : bk;
+                    uint32_t ri = cand_first ? ni : bi;
+                    if (cand_first) {
+                        if (kless(b2k, b2i, rk, ri)) { rk = b2k; ri = b2i; }
+                    } else {
+                        int n2 = m;  // the unvisited beam entry after nxt
+                        for (int base = nxt + 1; base < m; base += 32) {
+                            const int i = base + lane;
+                            const uint32_t bb2 = __ballot_sync(kFull, i < m && !(pid[i] & kVisited));
+                            if (bb2) { n2 = base + __ffs(bb2) - 1; break; }
+                        }
+                        if (n2 < m && kless(pkey[n2], pid[n2] & kIdMask, rk, ri)) {
+                            rk = pkey[n2];
+                            ri = pid[n2] & kIdMask;
+                        }
+                    }
+                    runner_id = ri;
+                }
             }
             __syncwarp();
+            if (runner_id != kEmpty && lane == 0)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                                 a.blocks + (size_t)runner_id * a.block_bytes),
+                             "r"(a.block_bytes)
+                             : "memory");
             if (next_id != kEmpty) {
                 const int nb = cb ^ 1;
                 if (lane == 0) {

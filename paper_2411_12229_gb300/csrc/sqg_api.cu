@@ -255,7 +255,7 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     a.o_rid = (uint32_t)o; o = align_up(o + 4 * (size_t)max_k, 16);
     // visited set: up to 2^10 slots in shared memory; a longer search moves
     // to its warp's full-size table in the workspace
-    a.shash_bits = std::min<uint32_t>(bits, 10);
+    a.shash_bits = std::min<uint32_t>(bits, p.visited_smem_log2 > 0 ? (uint32_t)p.visited_smem_log2 : 10u);
     pl.ghash = a.shash_bits < bits;
     a.o_hash = (uint32_t)o;
     const size_t warp_bytes = align_up(o + ((size_t)4 << a.shash_bits), 128);
@@ -300,6 +300,8 @@ int check_params(const sqg_search_params &p) {
     if (p.hop_cap < 0 || p.max_k < 0 || p.max_ef < 0 || p.max_k > SQG_MAX_K || p.max_ef > SQG_MAX_EF ||
         (p.max_k > 0 && p.max_ef > 0 && p.max_ef < p.max_k) || p.stop_every < 0 ||
         (p.team != 0 && p.team != 32) || p.warps_per_block < 0 || !std::isfinite(p.eps0) ||
+        (p.visited_smem_log2 != 0 && (p.visited_smem_log2 < 5 || p.visited_smem_log2 > 12)) ||
+        p.prefetch < 0 || p.prefetch > 2 ||
         (p.stop_mlp && p.stop_every < 1))
         return SQG_ERR_INVALID_ARG;
     return SQG_OK;
@@ -528,6 +530,7 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     a.mlp = p.stop_mlp;
     a.stop_logit = p.stop_logit;
     a.stop_every = p.stop_every;
+    a.prefetch = p.prefetch == 0 ? 1 : p.prefetch;
     a.trace_feat = trace_feat;
     a.trace_hit = trace_hit;
     a.trace_n = trace_n;

@@ -220,13 +220,21 @@ def test_caller_workspace_matches_own_allocation(gpu_tiny):
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
 
 
-@pytest.mark.parametrize("ef", [1024, 2048])
-def test_large_ef_migrates_the_visited_set(gpu_tiny, oracle_mod, ef):
-    """Past 512 expansions the visited set moves from shared memory to the
-    warp's table in the workspace; the search is unchanged."""
+@pytest.mark.parametrize("ef,smem_log2", [(64, 5), (300, 6), (1024, 0)])
+def test_visited_set_migration(gpu_tiny, oracle_mod, ef, smem_log2):
+    """A search whose expansions fill half of the shared-memory visited table
+    continues in the warp's full-size table in the workspace; the search is
+    unchanged (32- and 64-slot tables force the move on this index)."""
     ix, p, x, q = gpu_tiny
-    _, _, st = _check_search(ix, oracle_mod.Index(p), q[:16], 10, ef)
-    assert st[:, 0].max() > 512
+    _, _, st = _check_search(ix, oracle_mod.Index(p), q, 10, ef, visited_smem_log2=smem_log2)
+    if smem_log2:
+        assert st[:, 0].min() > (1 << smem_log2) // 2
+
+
+def test_speculative_prefetch_changes_nothing(gpu_tiny, oracle_mod):
+    ix, p, x, q = gpu_tiny
+    _check_search(ix, oracle_mod.Index(p), q, 10, 64, prefetch=2)
+    _check_search(ix, oracle_mod.Index(p), q, 10, 64, prefetch=2, warps_per_block=1)
 
 
 def test_learned_stop_constant_networks(gpu_tiny, oracle_mod):
