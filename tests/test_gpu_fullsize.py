@@ -1,0 +1,39 @@
+"""Parity at the benchmark's full size and launch configuration: the
+1,000,000 x 128 workload (Algorithm 2 index built on the GPU, cached where
+bench.py caches it), the whole 10,000-query batch in one launch, and a
+sample of queries recomputed one by one by the oracle."""
+
+import os
+import types
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def full_index(lib_built):
+    import bench
+    from paper_2411_12229_gb300 import synth
+    from paper_2411_12229_gb300.api import Index
+    args = types.SimpleNamespace(cache=os.environ.get("SQG_CACHE", "/tmp/sqg_cache"), build_iters=3, ef_build=64)
+    w = synth.BATCHED_1M_D128
+    idx, _ = bench.ensure_index(args, w, 0, 0)
+    return Index(idx, 0), idx, synth.queries(w)
+
+
+@pytest.mark.parametrize("ef", [48, 128])
+def test_full_size_sampled_parity(full_index, oracle_mod, ef):
+    ix, path, q = full_index
+    ids, dists, st = ix.search(torch.from_numpy(q).cuda(), 10, ef, stats=True)
+    ids, dists, st = ids.cpu().numpy().view(np.uint32), dists.cpu().numpy(), st.cpu().numpy()
+    O = oracle_mod.Index(path)
+    rng = np.random.default_rng(ef)
+    for i in rng.choice(q.shape[0], 150, replace=False):
+        oi, od, oh, os_ = O.search(q[i], 10, ef)
+        np.testing.assert_array_equal(ids[i], oi)
+        np.testing.assert_array_equal(dists[i], od)
+        assert (st[i, 0], st[i, 1]) == (oh, os_)
+    assert np.all(st[:, 1] == 0)  # no query reached the hop cap

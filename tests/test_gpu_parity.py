@@ -276,6 +276,49 @@ def test_trace_features_bit_exact(gpu_tiny, oracle_mod):
         np.testing.assert_array_equal(hits[i, :cnt[i]], th)
 
 
+SHAPES = {  # name: (workload, n, d, R): the other workloads' vector shapes at small n
+    "highdim-d960-R64": ("highdim-1m-d960", 3000, 960, 64),
+    "uneven-d1536-R32": ("uneven-1m-d1536", 2000, 1536, 32),
+    "serving-d96-R32": ("serving-4m-d96", 4000, 96, 32),
+    "d256-R32": ("batched-1m-d128", 2000, 256, 32),
+}
+
+
+@pytest.fixture(scope="module", params=list(SHAPES))
+def shaped_index(request, tmp_path_factory, lib_built):
+    from paper_2411_12229_gb300 import index_builder as ib
+    from paper_2411_12229_gb300 import synth
+    from paper_2411_12229_gb300.api import Index
+    name, n, d, R = SHAPES[request.param]
+    w = synth.small(synth.WORKLOADS[name].with_(d=d), n, 48)
+    x, q = synth.base(w), synth.queries(w)
+    p = tmp_path_factory.mktemp(request.param) / "s.sqg"
+    ib.build_index(p, x, R, device=0, init="random", iterations=2, ef_build=48)
+    return Index(p, 0), p, x, q
+
+
+def test_other_shapes_parity(shaped_index, oracle_mod):
+    """The kernel instantiations for d = 96 (24 of 32 lanes hold the raw
+    vector), 256, 960 (R = 64) and 1536: prepared queries, estimates and
+    searches identical to the oracle."""
+    ix, p, x, q = shaped_index
+    O = oracle_mod.Index(p)
+    qd = torch.from_numpy(q).cuda()
+    qrot, planes, scal = ix.prepare_queries(qd)
+    qrot = _np(qrot)
+    for i in range(0, q.shape[0], 5):
+        np.testing.assert_array_equal(qrot[i], O.prepare_query(q[i])["qrot"])
+    v = (np.arange(q.shape[0]) * 37 % ix.n).astype(np.int32)
+    S, est, key, dc = (_np(t) for t in ix.estimate_block(qd, torch.from_numpy(v), 1.0))
+    for i in range(0, q.shape[0], 3):
+        r = O.estimate_block(q[i], int(v[i]), 1.0)
+        np.testing.assert_array_equal(S[i], r["S"])
+        np.testing.assert_array_equal(est[i], r["est"])
+        np.testing.assert_array_equal(key[i], r["key"])
+    for ef in (10, 40, 100):
+        _check_search(ix, O, q, 10, ef)
+
+
 @pytest.mark.parametrize("ef", [16, 64])
 def test_expansion_order_identical(gpu_tiny, oracle_mod, ef):
     """Algorithm 1 line 3: the sequence of expanded vertices, hop by hop,
