@@ -206,6 +206,31 @@ int sqg_search_trace(const sqg_index *ix, const float *queries, int nq, const in
                      const uint32_t *gt, int gt_k, float *trace_feat, int32_t *trace_hit, int32_t *trace_n,
                      int trace_cap, uint32_t *path, int path_cap, sqg_stream_t stream);
 
+/* sqg_search for callers that cannot allocate device memory while they
+ * search -- e.g. an application that reserved all GPU memory for its own
+ * pool at start-up, or a latency-critical thread that must not enter the
+ * allocator or meet an out-of-memory error mid-request.  The paper has no
+ * counterpart: this is a packaging of the same search.
+ *   Same arguments as sqg_search, with the batch's bounds given explicitly
+ *   (max_k, max_ef: every valid k[i] <= max_k, ef[i] <= max_ef), so nothing
+ *   is read back from the device either.
+ *   Scratch: one file-scope device array of sqg_noalloc_scratch_bytes()
+ *   (32 MiB) that every GPU loading the library holds until the process
+ *   exits.  A batch whose sqg_workspace_size(ix, nq, max_k, max_ef) exceeds
+ *   it is rejected with SQG_ERR_CAPACITY (for d = 128: about 60,000
+ *   queries with max_ef <= 112; larger ef also needs the visited tables).
+ *   The call performs no cudaMalloc, cudaFree or stream-ordered allocation.
+ *   The first call on a device looks the array's address up
+ *   (cudaGetSymbolAddress) and caches it; make that first call before any
+ *   stream capture.  All calls share the array and it keeps the last call's
+ *   contents (the search resets what must start at zero); calls whose work
+ *   overlaps on one GPU race on it and must be serialized by the caller. */
+int sqg_search_noalloc(const sqg_index *ix, const float *queries, int nq, const int32_t *k, const int32_t *ef,
+                       int max_k, int max_ef, uint32_t *out_ids, float *out_dists, sqg_stream_t stream);
+
+/* Size in bytes of the fixed scratch array used by sqg_search_noalloc. */
+size_t sqg_noalloc_scratch_bytes(void);
+
 /* ---- learned early stop: training kernels (not in the paper) ---- */
 
 /* Gradient of the weighted binary cross-entropy of the stop MLP:
