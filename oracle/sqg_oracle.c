@@ -593,10 +593,16 @@ static void stop_features(const orc_stop_state *s, const orc_entry *pool, int m,
     float rk = res[nres - 1].key;
     float den = rk > 1e-20f ? rk : 1e-20f;
     float fef = (float)s->ef;
-    int u = 0;
+    int u = 0, near1 = 0, near2 = 0; /* unvisited; of them with key <= rk, <= 1.25 rk */
     float fu = 0.0f;
+    const float rk2 = 1.25f * rk;
     for (int i = m - 1; i >= 0; --i)
-        if (!visited_flags[i]) { ++u; fu = pool[i].key; }
+        if (!visited_flags[i]) {
+            ++u;
+            fu = pool[i].key;
+            near1 += pool[i].key <= rk;
+            near2 += pool[i].key <= rk2;
+        }
     float since = (float)(s->hops - s->last_improve_hop);
     f[0] = (float)s->hops / fef;
     f[1] = since / fef;
@@ -609,8 +615,8 @@ static void stop_features(const orc_stop_state *s, const orc_entry *pool, int m,
     f[8] = (float)s->k / fef;
     f[9] = s->ema_improve;
     f[10] = s->ema_insert;
-    f[11] = pool[0].key / den;
-    f[12] = pool[m - 1].key / den;
+    f[11] = (float)near1 / (float)s->k;
+    f[12] = (float)near2 / (float)s->k;
     f[13] = since / ((float)s->hops + 1.0f);
     f[14] = s->dist_c <= rk ? 1.0f : 0.0f;
     f[15] = (float)s->k / 100.0f;

@@ -111,12 +111,25 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// try_wait that may suspend the warp for up to `hint_ns` (it resumes as soon
+// as the phase completes), so a waiting warp does not spin on issue slots.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait for phase `parity` of `bar`; false on timeout (never hangs).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
-    unsigned long long t0 = global_ns();
+    const unsigned long long t0 = global_ns();
     for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_suspend(bar, parity, 200000u)) return true;
         if (global_ns() - t0 > kWaitLimitNs) return false;
     }
 }
@@ -206,10 +219,8 @@ __device__ __forceinline__ QuerySide quantize_warp(const float *qr, uint32_t d, 
         uint32_t b0 = __ballot_sync(kFull, t & 1), b1 = __ballot_sync(kFull, t & 2);
         uint32_t b2 = __ballot_sync(kFull, t & 4), b3 = __ballot_sync(kFull, t & 8);
         if (lane == 0) {
-            planes[w] = b0;
-            planes[nw + w] = b1;
-            planes[2 * nw + w] = b2;
-            planes[3 * nw + w] = b3;
+            // word-major: the 4 planes of word w share one 16-byte slot
+            reinterpret_cast<uint4 *>(planes)[w] = make_uint4(b0, b1, b2, b3);
         }
     }
 #pragma unroll
@@ -257,10 +268,11 @@ __device__ __forceinline__ Est estimate(const unsigned char *blk, const SearchAr
 #pragma unroll 4
     for (uint32_t w = 0; w < nw; ++w) {
         uint32_t c = codes[w * R];
-        s0 += __popc(c & planes[w]);
-        s1 += __popc(c & planes[nw + w]);
-        s2 += __popc(c & planes[2 * nw + w]);
-        s3 += __popc(c & planes[3 * nw + w]);
+        const uint4 pl = reinterpret_cast<const uint4 *>(planes)[w];
+        s0 += __popc(c & pl.x);
+        s1 += __popc(c & pl.y);
+        s2 += __popc(c & pl.z);
+        s3 += __popc(c & pl.w);
     }
     const int S = s0 + 2 * s1 + 4 * s2 + 8 * s3;
     const float *fac = reinterpret_cast<const float *>(blk + a.off_factors);
@@ -685,12 +697,17 @@ __global__ void __launch_bounds__(128, (CH <= 2 ? 5 : 3)) search_kernel(const Se
             st.ema_insert = __fadd_rn(__fmul_rn(0.75f, st.ema_insert),
                                       __fmul_rn(0.25f, __fdiv_rn((float)inserted, (float)R)));
             if ((a.mlp || a.trace_feat) && a.stop_every > 0 && hops % a.stop_every == 0 && rc == k) {
-                int u = 0;
-                for (int base = 0; base < m; base += 32) {
-                    int i = base + lane;
-                    u += __popc(__ballot_sync(kFull, i < m && !(pid[i] & kVisited)));
-                }
                 const float rk = rkey[k - 1];
+                const float rk2 = __fmul_rn(1.25f, rk);
+                int u = 0, near1 = 0, near2 = 0;  // unvisited; of them with key <= rk, <= 1.25 rk
+                for (int base = 0; base < m; base += 32) {
+                    const int i = base + lane;
+                    const bool un = i < m && !(pid[i] & kVisited);
+                    const float kk = un ? pkey[i] : 0.0f;
+                    u += __popc(__ballot_sync(kFull, un));
+                    near1 += __popc(__ballot_sync(kFull, un && kk <= rk));
+                    near2 += __popc(__ballot_sync(kFull, un && kk <= rk2));
+                }
                 const float den = rk > 1e-20f ? rk : 1e-20f;
                 const float fef = (float)ef;
                 const float since = (float)(hops - st.last_improve);
@@ -706,8 +723,8 @@ __global__ void __launch_bounds__(128, (CH <= 2 ? 5 : 3)) search_kernel(const Se
                 f[8] = __fdiv_rn((float)k, fef);
                 f[9] = st.ema_improve;
                 f[10] = st.ema_insert;
-                f[11] = __fdiv_rn(pkey[0], den);
-                f[12] = __fdiv_rn(pkey[m - 1], den);
+                f[11] = __fdiv_rn((float)near1, (float)k);
+                f[12] = __fdiv_rn((float)near2, (float)k);
                 f[13] = __fdiv_rn(since, __fadd_rn((float)hops, 1.0f));
                 f[14] = dist_c <= rk ? 1.0f : 0.0f;
                 f[15] = __fdiv_rn((float)k, 100.0f);

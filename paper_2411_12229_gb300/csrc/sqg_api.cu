@@ -157,11 +157,15 @@ __global__ void quantize_kernel(const float *qrot, int nq, int d, uint32_t *plan
     const int lane = threadIdx.x & 31;
     const int qi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (qi >= nq) return;
-    extern __shared__ uint32_t pl_smem[];
+    extern __shared__ __align__(16) uint32_t pl_smem[];
     uint32_t *pl = pl_smem + (threadIdx.x >> 5) * (4 * (d / 32));
     const QuerySide qs = quantize_warp(qrot + (size_t)qi * d, (uint32_t)d, pl, lane);
     __syncwarp();
-    for (int i = lane; i < 4 * (d / 32); i += 32) planes[(size_t)qi * 4 * (d / 32) + i] = pl[i];
+    // shared layout is word-major ([w][b]); the export is plane-major ([b][w])
+    for (int i = lane; i < 4 * (d / 32); i += 32) {
+        const int b = i / (d / 32), w = i % (d / 32);
+        planes[(size_t)qi * 4 * (d / 32) + i] = pl[4 * w + b];
+    }
     if (lane == 0) {
         scal[qi * 4 + 0] = qs.vl;
         scal[qi * 4 + 1] = qs.delta;
