@@ -97,6 +97,8 @@ typedef struct {
     int32_t prefetch;        /* 1 (default, 0): next block copied into a second shared
                                 buffer during the merge; 2: also L2-prefetch the
                                 runner-up candidate's block */
+    int32_t lean;            /* 1: for d <= 256, the kernel build capped at 64 registers
+                                (more resident warps, a few spills); 0: default build */
 } sqg_search_params;
 
 typedef struct {

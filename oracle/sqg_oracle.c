@@ -604,22 +604,25 @@ static void stop_features(const orc_stop_state *s, const orc_entry *pool, int m,
             near2 += pool[i].key <= rk2;
         }
     float since = (float)(s->hops - s->last_improve_hop);
-    f[0] = (float)s->hops / fef;
-    f[1] = since / fef;
-    f[2] = (float)u / fef;
-    f[3] = (float)m / fef;
-    f[4] = res[0].key / den;
-    f[5] = u > 0 ? fu / den : 0.0f;
-    f[6] = s->dist_c / den;
-    f[7] = (float)s->inserted_last / (float)s->R;
-    f[8] = (float)s->k / fef;
+    /* ratios as products with four reciprocals */
+    const float inv_ef = 1.0f / fef, inv_den = 1.0f / den, inv_k = 1.0f / (float)s->k;
+    const float inv_h1 = 1.0f / ((float)s->hops + 1.0f);
+    f[0] = (float)s->hops * inv_ef;
+    f[1] = since * inv_ef;
+    f[2] = (float)u * inv_ef;
+    f[3] = (float)m * inv_ef;
+    f[4] = res[0].key * inv_den;
+    f[5] = u > 0 ? fu * inv_den : 0.0f;
+    f[6] = s->dist_c * inv_den;
+    f[7] = (float)s->inserted_last * (1.0f / (float)s->R);
+    f[8] = (float)s->k * inv_ef;
     f[9] = s->ema_improve;
     f[10] = s->ema_insert;
-    f[11] = (float)near1 / (float)s->k;
-    f[12] = (float)near2 / (float)s->k;
-    f[13] = since / ((float)s->hops + 1.0f);
+    f[11] = (float)near1 * inv_k;
+    f[12] = (float)near2 * inv_k;
+    f[13] = since * inv_h1;
     f[14] = s->dist_c <= rk ? 1.0f : 0.0f;
-    f[15] = (float)s->k / 100.0f;
+    f[15] = (float)s->k * 0.01f;
     for (int i = 0; i < MLP_IN; ++i) f[i] = clampf8(f[i]);
 }
 
@@ -730,7 +733,7 @@ int orc_search(const orc_index *ix, const float *q, uint32_t k, uint32_t ef, flo
         st.dist_c = dist_c;
         if (improved) st.last_improve_hop = (int)hops;
         st.ema_improve = 0.75f * st.ema_improve + 0.25f * (improved ? 1.0f : 0.0f);
-        st.ema_insert = 0.75f * st.ema_insert + 0.25f * ((float)inserted / (float)R);
+        st.ema_insert = 0.75f * st.ema_insert + 0.25f * ((float)inserted * (1.0f / (float)R));
         if ((mlp || trace_feat) && stop_every > 0 && hops % stop_every == 0 && nres == (int)k) {
             float f[MLP_IN];
             for (int i = 0; i < m; ++i) vflag[i] = visited[pool[i].id];

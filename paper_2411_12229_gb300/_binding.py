@@ -35,7 +35,7 @@ class SearchParams(C.Structure):
                 ("max_k", C.c_int32), ("max_ef", C.c_int32), ("stop_mlp", C.c_void_p),
                 ("stop_logit", C.c_float), ("stop_every", C.c_int32), ("team", C.c_int32),
                 ("warps_per_block", C.c_int32), ("timing_events", C.c_void_p * 2),
-                ("visited_smem_log2", C.c_int32), ("prefetch", C.c_int32)]
+                ("visited_smem_log2", C.c_int32), ("prefetch", C.c_int32), ("lean", C.c_int32)]
 
 
 class Info(C.Structure):

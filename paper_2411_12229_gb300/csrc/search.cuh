@@ -333,11 +333,14 @@ __device__ __forceinline__ float mlp_logit_warp(const float *w, const float (&f)
 }
 
 // ---------------------------------------------------------------- the kernel
-template <int CH, int NB>
-__global__ void __launch_bounds__(128, (CH <= 2 ? 5 : 3)) search_kernel(const SearchArgs a) {
+// LEAN: a build capped at 64 registers (8 resident blocks of 4 warps) for
+// d <= 256, trading a few spills for more warps in flight.
+template <int CH, int NB, bool LEAN = false>
+__global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_kernel(const SearchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t R = a.R, d = a.d, nch = d / 4, nw = d / 32;
+    const uint32_t R = a.R, d = a.d, nch = d / 4;
+    const float inv_R = __fdiv_rn(1.0f, (float)R);
 
     float *wts = reinterpret_cast<float *>(smem);
     if (a.mlp) {  // transpose W1, W2 into [in][out]
@@ -689,14 +692,18 @@ __global__ void __launch_bounds__(128, (CH <= 2 ? 5 : 3)) search_kernel(const Se
             __syncwarp();
 
             // ---- learned early stop (not in the paper) / trace
-            st.hops = hops;
-            st.inserted_last = inserted;
-            st.dist_c = dist_c;
-            if (improved) st.last_improve = hops;
-            st.ema_improve = __fadd_rn(__fmul_rn(0.75f, st.ema_improve), __fmul_rn(0.25f, improved ? 1.0f : 0.0f));
-            st.ema_insert = __fadd_rn(__fmul_rn(0.75f, st.ema_insert),
-                                      __fmul_rn(0.25f, __fdiv_rn((float)inserted, (float)R)));
-            if ((a.mlp || a.trace_feat) && a.stop_every > 0 && hops % a.stop_every == 0 && rc == k) {
+            const bool stop_on = a.mlp || a.trace_feat;  // the state below feeds the stop only
+            if (stop_on) {
+                st.hops = hops;
+                st.inserted_last = inserted;
+                st.dist_c = dist_c;
+                if (improved) st.last_improve = hops;
+                st.ema_improve =
+                    __fadd_rn(__fmul_rn(0.75f, st.ema_improve), __fmul_rn(0.25f, improved ? 1.0f : 0.0f));
+                st.ema_insert = __fadd_rn(__fmul_rn(0.75f, st.ema_insert),
+                                          __fmul_rn(0.25f, __fmul_rn((float)inserted, inv_R)));
+            }
+            if (stop_on && a.stop_every > 0 && hops % a.stop_every == 0 && rc == k) {
                 const float rk = rkey[k - 1];
                 const float rk2 = __fmul_rn(1.25f, rk);
                 int u = 0, near1 = 0, near2 = 0;  // unvisited; of them with key <= rk, <= 1.25 rk
@@ -711,23 +718,27 @@ __global__ void __launch_bounds__(128, (CH <= 2 ? 5 : 3)) search_kernel(const Se
                 const float den = rk > 1e-20f ? rk : 1e-20f;
                 const float fef = (float)ef;
                 const float since = (float)(hops - st.last_improve);
+                // ratios as products with four reciprocals
+                const float inv_ef = __fdiv_rn(1.0f, fef), inv_den = __fdiv_rn(1.0f, den);
+                const float inv_k = __fdiv_rn(1.0f, (float)k);
+                const float inv_h1 = __fdiv_rn(1.0f, __fadd_rn((float)hops, 1.0f));
                 float f[SQG_MLP_IN];
-                f[0] = __fdiv_rn((float)hops, fef);
-                f[1] = __fdiv_rn(since, fef);
-                f[2] = __fdiv_rn((float)u, fef);
-                f[3] = __fdiv_rn((float)m, fef);
-                f[4] = __fdiv_rn(rkey[0], den);
-                f[5] = u > 0 ? __fdiv_rn(pkey[cur], den) : 0.0f;
-                f[6] = __fdiv_rn(dist_c, den);
-                f[7] = __fdiv_rn((float)inserted, (float)R);
-                f[8] = __fdiv_rn((float)k, fef);
+                f[0] = __fmul_rn((float)hops, inv_ef);
+                f[1] = __fmul_rn(since, inv_ef);
+                f[2] = __fmul_rn((float)u, inv_ef);
+                f[3] = __fmul_rn((float)m, inv_ef);
+                f[4] = __fmul_rn(rkey[0], inv_den);
+                f[5] = u > 0 ? __fmul_rn(pkey[cur], inv_den) : 0.0f;
+                f[6] = __fmul_rn(dist_c, inv_den);
+                f[7] = __fmul_rn((float)inserted, __fdiv_rn(1.0f, (float)R));
+                f[8] = __fmul_rn((float)k, inv_ef);
                 f[9] = st.ema_improve;
                 f[10] = st.ema_insert;
-                f[11] = __fdiv_rn((float)near1, (float)k);
-                f[12] = __fdiv_rn((float)near2, (float)k);
-                f[13] = __fdiv_rn(since, __fadd_rn((float)hops, 1.0f));
+                f[11] = __fmul_rn((float)near1, inv_k);
+                f[12] = __fmul_rn((float)near2, inv_k);
+                f[13] = __fmul_rn(since, inv_h1);
                 f[14] = dist_c <= rk ? 1.0f : 0.0f;
-                f[15] = __fdiv_rn((float)k, 100.0f);
+                f[15] = __fmul_rn((float)k, 0.01f);
 #pragma unroll
                 for (int i = 0; i < SQG_MLP_IN; ++i) f[i] = clamp8(f[i]);
                 if (a.trace_feat && tn < a.trace_cap) {

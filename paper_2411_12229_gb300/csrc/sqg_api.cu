@@ -240,6 +240,7 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     pl.ch = pick_ch(d);
     pl.nb = (int)(R / 32);
     if (pl.ch < 0 || (pl.nb != 1 && pl.nb != 2)) return SQG_ERR_UNSUPPORTED;
+    if (p.lean && pl.ch <= 2) pl.ch = -pl.ch;  // the 64-register build
     const long long cap = p.hop_cap > 0 ? p.hop_cap : 4LL * max_ef + 64;
     uint32_t bits = 5;
     while ((1ull << bits) < 2ull * (unsigned long long)cap + 1) ++bits;
@@ -305,7 +306,7 @@ int check_params(const sqg_search_params &p) {
         (p.max_k > 0 && p.max_ef > 0 && p.max_ef < p.max_k) || p.stop_every < 0 ||
         (p.team != 0 && p.team != 32) || p.warps_per_block < 0 || !std::isfinite(p.eps0) ||
         (p.visited_smem_log2 != 0 && (p.visited_smem_log2 < 5 || p.visited_smem_log2 > 12)) ||
-        p.prefetch < 0 || p.prefetch > 2 ||
+        p.prefetch < 0 || p.prefetch > 2 || p.lean < 0 || p.lean > 1 ||
         (p.stop_mlp && p.stop_every < 1))
         return SQG_ERR_INVALID_ARG;
     return SQG_OK;

@@ -1,0 +1,47 @@
+"""The persistent batched form: autotuned launch knobs change nothing in the
+results, and a CUDA-graph-captured batch replays the same search."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_every_tuning_knob_gives_identical_results(tiny_index, tmp_path, monkeypatch):
+    from paper_2411_12229_gb300 import autotune
+    from paper_2411_12229_gb300.api import Index
+    monkeypatch.setenv("SQG_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    p, x, q = tiny_index
+    ix = Index(p, 0)
+    qd = torch.from_numpy(q).cuda()
+    ref = ix.search(qd, 10, 64)
+    import itertools
+    names = list(autotune.KNOBS)
+    for combo in itertools.product(*(autotune.KNOBS[n] for n in names)):
+        got = ix.search(qd, 10, 64, **dict(zip(names, combo)))
+        assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]), dict(zip(names, combo))
+    res = autotune.autotune(ix, qd, 10, 64, reps=2)
+    assert len(res["table"]) == 24
+    assert autotune.tuned(ix, 64) == res["best"]
+    assert autotune.tuned(ix, 1000) == autotune.DEFAULT
+
+
+def test_graph_captured_batch_replays_the_search(tiny_index, oracle_mod):
+    from paper_2411_12229_gb300.api import Index
+    from paper_2411_12229_gb300.autotune import GraphSearch
+    p, x, q = tiny_index
+    ix = Index(p, 0)
+    nq = 32
+    rng = np.random.default_rng(2)
+    k = rng.choice([1, 10, 30], size=nq).astype(np.int32)
+    ef = (k * rng.integers(1, 5, size=nq)).astype(np.int32) + 8
+    g = GraphSearch(ix, nq, k, ef, max_k=30, max_ef=int(ef.max()))
+    off = np.concatenate([[0], np.cumsum(k)])
+    O = oracle_mod.Index(p)
+    for a in (0, 32):  # two replays with different queries
+        ids, dists = g(torch.from_numpy(q[a:a + nq]).cuda())
+        torch.cuda.synchronize()
+        ids = ids.cpu().numpy().view(np.uint32)
+        for i in range(nq):
+            np.testing.assert_array_equal(ids[off[i]:off[i + 1]], O.search(q[a + i], int(k[i]), int(ef[i]))[0])
