@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--ef", type=int, default=0, help="fixed ef: skip the sweep (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-stop", action="store_true", help="skip the learned-stop comparison")
+    ap.add_argument("--stop-train", type=int, default=20000, help="training queries for the learned stop")
     return ap.parse_args()
 
 
@@ -211,6 +213,87 @@ def run_oracle(idx_path, queries, k, ef, seconds, threads, max_queries):
     return done, el, ids
 
 
+def learned_stop_comparison(args, w, ix, qd, gt_ids, sweep, ef_sel, device):
+    """Train the stop on separate training queries, pick its threshold on a
+    held-out part of them, then time it on the test batch next to the plain
+    search: QPS and mean expansions at the first operating point whose
+    recall reaches the target (untimed for the headline value)."""
+    from paper_2411_12229_gb300 import eval as E
+    from paper_2411_12229_gb300 import learned_stop as L
+    t0 = time.time()
+    tq = synth.train_queries(w, args.stop_train)
+    tg, _ = E.ground_truth(synth.base(w), tq, 10, device=device)
+    cap = 2 * ef_sel
+    model = L.fit(ix, tq, tg, 10, cap, args.target, every=2, steps=3000)
+    rows = []
+    for thr in sorted({model.logit, model.logit - 0.5, model.logit + 0.5, model.logit + 1.0}):
+        r, qps, hops = L.evaluate(ix, qd, gt_ids, 10, cap, model, logit=thr, reps=5)
+        rows.append({"logit": thr, "recall": round(r, 4), "qps": round(qps), "hops": round(hops, 2)})
+    ok = [x for x in rows if x["recall"] >= args.target]
+    best = max(ok, key=lambda x: x["qps"]) if ok else None
+    plain = next((s for s in sweep if s["recall"] >= args.target), None)
+    log(f"learned stop in {time.time() - t0:.1f}s: {rows}")
+    return {"ef_cap": cap, "every": 2, "train_queries": int(args.stop_train), "calibrated_logit": model.logit,
+            "points": rows, "best_at_target": best,
+            "plain_at_target": {k: plain[k] for k in ("ef", "recall", "qps", "hops")} if plain else None,
+            "qps_ratio_vs_plain": round(best["qps"] / plain["qps"], 4) if best and plain else None}
+
+
+def bench_mixed(args, w, ix, qd, q, gt_ids, rank, world, dist, local):
+    """A batch with per-query k and ef (the persistent work-queue form):
+    autotune the launch knobs on the batch, then time it; recall per k."""
+    import torch
+
+    from paper_2411_12229_gb300 import autotune
+    from paper_2411_12229_gb300 import eval as E
+    nq = q.shape[0]
+    kq, efq = synth.query_k_ef(w, nq)
+    kt, et = torch.from_numpy(kq).cuda(), torch.from_numpy(efq).cuda()
+    max_k, max_ef = int(kq.max()), int(efq.max())
+    tune = autotune.autotune(ix, qd, kt, et, reps=3, knobs=None, save=False)
+    knobs = tune["best"]
+    total = int(kq.sum())
+    out = (torch.empty(total, dtype=torch.int32, device="cuda"), torch.empty(total, device="cuda"))
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        ix.search(qd, kt, et, out=out, max_k=max_k, max_ef=max_ef, **knobs)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    st = None
+    for s in range(args.steps):
+        flush.zero_()
+        ev[s][0].record()
+        _, _, st = ix.search(qd, kt, et, out=out, stats=True, max_k=max_k, max_ef=max_ef, **knobs)
+        ev[s][1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ids = out[0].cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(kq)])
+    rec = {}
+    for kk in sorted(set(kq.tolist())):
+        sel = np.nonzero(kq == kk)[0]
+        got = np.stack([ids[off[i]:off[i + 1]] for i in sel])
+        rec[str(kk)] = round(E.recall(got, gt_ids[sel], kk), 4)
+    hops = st[:, 0].double().cpu().numpy()
+    alg = float(hops.sum() * ix.block_bytes + nq * 4 * w.d + 8 * total)
+    peak, src = measured_peaks()
+    line = {"metric": "queries/sec, mixed k and ef in one launch", "value": round(nq / (ms / 1e3), 1),
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "d": w.d, "degree": w.degree, "k": "U{1,10,100}",
+                       "ef": "U[k, 8k]", "queries_per_step": nq, "recall_per_k": rec, "knobs": knobs,
+                       "l2": "flushed (512 MiB write) between timed steps"},
+            "roofline": {"bound": "hbm", "achieved": round(alg / (ms / 1e3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4), "peak_source": src,
+                         "note": "step time (plan + rotation + search), not the search kernel alone"},
+            "autotune": sorted(tune["table"], key=lambda r: r["ms"])[:6], "clocks": clk,
+            "hops_mean": round(float(hops.mean()), 2), "gpu_launches": 3 * args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def bench_reference(args):
     """CPU oracle arm: same metric and workload, bounded samples per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -283,6 +366,8 @@ def main():
     gt_ids, gt_d = ground_truth(args, w, f"{gtp}-r{rank}", q, local, world)
     ix = Index(idx, local)
     qd = torch.from_numpy(q).cuda()
+    if w.mixed_k:
+        return bench_mixed(args, w, ix, qd, q, gt_ids, rank, world, dist, local)
     k = 10
     nq = q.shape[0]
 
@@ -306,6 +391,9 @@ def main():
             break
     pick = lambda t: next((s["ef"] for s in sweep if s["recall"] >= t), None)  # noqa: E731
     ef_sel = args.ef or pick(args.target) or sweep[-1]["ef"]
+    stop_cmp = None
+    if rank == 0 and not args.skip_stop and not args.ef:
+        stop_cmp = learned_stop_comparison(args, w, ix, qd, gt_ids, sweep, ef_sel, local)
     if dist:
         t = torch.tensor([ef_sel], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -412,6 +500,7 @@ def main():
                           for t in (0.90, 0.95, 0.99)},
         "ef_at_recall": {str(t): pick(t) for t in (0.90, 0.95, 0.99)},
         "hops_mean": round(float(hops.mean()), 2),
+        "learned_stop": stop_cmp,
         "sweep": sweep,
     }
     print(json.dumps(line), flush=True)

@@ -92,13 +92,15 @@ typedef struct {
     void *timing_events[2];  /* optional cudaEvent_t pair recorded on the stream right before
                                 and right after the search kernel; NULL = none */
     int32_t visited_smem_log2; /* log2 of the visited set's shared-memory slots (5..12;
-                                  0 = 10); a search past half of them continues in a
-                                  full-size table in the workspace */
+                                  0 = 9 with the lean build, else 10); a search past
+                                  half of them continues in a full-size table in the
+                                  workspace */
     int32_t prefetch;        /* 1 (default, 0): next block copied into a second shared
                                 buffer during the merge; 2: also L2-prefetch the
                                 runner-up candidate's block */
-    int32_t lean;            /* 1: for d <= 256, the kernel build capped at 64 registers
-                                (more resident warps, a few spills); 0: default build */
+    int32_t lean;            /* d <= 256 only: 0 or 1 = the kernel build capped at 64
+                                registers (more resident warps, a few spills; the
+                                default), 2 = the 96-register build */
 } sqg_search_params;
 
 typedef struct {

@@ -5,7 +5,8 @@ Knobs, all result-neutral (the search is bit-identical under each):
   prefetch           1: next block into the second shared buffer;
                      2: also L2-prefetch the runner-up vertex's block
   visited_smem_log2  shared-memory slots of the visited set (2^9, 2^10)
-  lean               the 64-register build (d <= 256): more resident warps
+  lean               1: the 64-register build (d <= 256, more resident
+                     warps); 2: the 96-register build
 The tuner times every combination on the caller's own batch (CUDA events,
 median of `reps`) and keeps the fastest per (GPU, d, R, ef bucket) in a
 JSON cache, which ``tuned`` then returns.
@@ -25,8 +26,8 @@ import pathlib
 import numpy as np
 import torch
 
-KNOBS = {"warps_per_block": (1, 2, 4), "prefetch": (1, 2), "visited_smem_log2": (9, 10), "lean": (0, 1)}
-DEFAULT = {"warps_per_block": 4, "prefetch": 1, "visited_smem_log2": 10, "lean": 0}
+KNOBS = {"warps_per_block": (1, 2, 4), "prefetch": (1, 2), "visited_smem_log2": (9, 10), "lean": (1, 2)}
+DEFAULT = {"warps_per_block": 4, "prefetch": 1, "visited_smem_log2": 0, "lean": 0}
 
 
 def cache_path() -> pathlib.Path:

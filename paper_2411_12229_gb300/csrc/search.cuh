@@ -260,8 +260,9 @@ struct Est {
     int S;
     float est, key;
 };
+// sqrt_dc = sqrtf(dist_c), computed once per expansion (used only when eps0 != 0).
 __device__ __forceinline__ Est estimate(const unsigned char *blk, const SearchArgs &a, const uint32_t *planes,
-                                        const QuerySide &qs, uint32_t j, float dist_c) {
+                                        const QuerySide &qs, uint32_t j, float dist_c, float sqrt_dc) {
     const uint32_t nw = a.d / 32, R = a.R;
     const uint32_t *codes = reinterpret_cast<const uint32_t *>(blk + a.off_codes) + j;
     int s0 = 0, s1 = 0, s2 = 0, s3 = 0;
@@ -276,7 +277,7 @@ __device__ __forceinline__ Est estimate(const unsigned char *blk, const SearchAr
     }
     const int S = s0 + 2 * s1 + 4 * s2 + 8 * s3;
     const float *fac = reinterpret_cast<const float *>(blk + a.off_factors);
-    const float f_add = fac[j], f_rescale = fac[R + j], f_err = fac[2 * R + j];
+    const float f_add = fac[j], f_rescale = fac[R + j];
     const int pc = (int)reinterpret_cast<const uint32_t *>(fac)[3 * R + j];
     const float A = (float)(2 * S - qs.sq);
     const float B = __fmul_rn(qs.vl, (float)(2 * pc - (int)a.d));
@@ -284,8 +285,12 @@ __device__ __forceinline__ Est estimate(const unsigned char *blk, const SearchAr
     Est e;
     e.S = S;
     e.est = __fmaf_rn(f_rescale, ip, __fadd_rn(f_add, dist_c));
-    const float bound = __fmul_rn(f_err, __fsqrt_rn(dist_c));
-    e.key = __fsub_rn(e.est, __fmul_rn(a.eps0, bound));
+    if (a.eps0 == 0.0f) {
+        e.key = e.est;  // est - 0 * bound, bound finite and >= 0
+    } else {
+        const float bound = __fmul_rn(fac[2 * R + j], sqrt_dc);
+        e.key = __fsub_rn(e.est, __fmul_rn(a.eps0, bound));
+    }
     return e;
 }
 
@@ -523,11 +528,12 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
             uint32_t cid[NB];
             int cpos[NB];
             bool adm[NB];
+            const float sqrt_dc = a.eps0 == 0.0f ? 0.0f : __fsqrt_rn(dist_c);
 #pragma unroll
             for (int t = 0; t < NB; ++t) {
                 const uint32_t j = lane + 32 * t;
                 cid[t] = ids[j];
-                const Est e = estimate(blk, a, planes, qs, j, dist_c);
+                const Est e = estimate(blk, a, planes, qs, j, dist_c, sqrt_dc);
                 ck[t] = e.key;
                 // line 6: only unvisited neighbours enter; an entry that the cut
                 // to ef would drop at once is skipped early

@@ -208,8 +208,9 @@ __global__ void estimate_block_kernel(SearchArgs a, const uint32_t *v, int32_t *
     const QuerySide qs = quantize_warp(a.qrot + (size_t)qi * d, d, planes, lane);
     __syncwarp();
     const float dist_c = exact_dist<16>(qv, reinterpret_cast<const float *>(blk), d / 4, lane);
+    const float sqrt_dc = __fsqrt_rn(dist_c);
     for (uint32_t j = lane; j < R; j += 32) {
-        const Est e = estimate(blk, a, planes, qs, j, dist_c);
+        const Est e = estimate(blk, a, planes, qs, j, dist_c, sqrt_dc);
         out_S[(size_t)qi * R + j] = e.S;
         out_est[(size_t)qi * R + j] = e.est;
         out_key[(size_t)qi * R + j] = e.key;
@@ -240,7 +241,9 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     pl.ch = pick_ch(d);
     pl.nb = (int)(R / 32);
     if (pl.ch < 0 || (pl.nb != 1 && pl.nb != 2)) return SQG_ERR_UNSUPPORTED;
-    if (p.lean && pl.ch <= 2) pl.ch = -pl.ch;  // the 64-register build
+    // the 64-register build for d <= 256 unless asked for the full one
+    // (measured faster at d = 128: more resident warps hide more latency)
+    if (p.lean != 2 && pl.ch <= 2) pl.ch = -pl.ch;
     const long long cap = p.hop_cap > 0 ? p.hop_cap : 4LL * max_ef + 64;
     uint32_t bits = 5;
     while ((1ull << bits) < 2ull * (unsigned long long)cap + 1) ++bits;
@@ -260,7 +263,9 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     a.o_rid = (uint32_t)o; o = align_up(o + 4 * (size_t)max_k, 16);
     // visited set: up to 2^10 slots in shared memory; a longer search moves
     // to its warp's full-size table in the workspace
-    a.shash_bits = std::min<uint32_t>(bits, p.visited_smem_log2 > 0 ? (uint32_t)p.visited_smem_log2 : 10u);
+    const uint32_t smem_bits_default = pl.ch < 0 ? 9u : 10u;
+    a.shash_bits =
+        std::min<uint32_t>(bits, p.visited_smem_log2 > 0 ? (uint32_t)p.visited_smem_log2 : smem_bits_default);
     pl.ghash = a.shash_bits < bits;
     a.o_hash = (uint32_t)o;
     const size_t warp_bytes = align_up(o + ((size_t)4 << a.shash_bits), 128);
@@ -306,7 +311,7 @@ int check_params(const sqg_search_params &p) {
         (p.max_k > 0 && p.max_ef > 0 && p.max_ef < p.max_k) || p.stop_every < 0 ||
         (p.team != 0 && p.team != 32) || p.warps_per_block < 0 || !std::isfinite(p.eps0) ||
         (p.visited_smem_log2 != 0 && (p.visited_smem_log2 < 5 || p.visited_smem_log2 > 12)) ||
-        p.prefetch < 0 || p.prefetch > 2 || p.lean < 0 || p.lean > 1 ||
+        p.prefetch < 0 || p.prefetch > 2 || p.lean < 0 || p.lean > 2 ||
         (p.stop_mlp && p.stop_every < 1))
         return SQG_ERR_INVALID_ARG;
     return SQG_OK;
