@@ -213,6 +213,24 @@ def run_oracle(idx_path, queries, k, ef, seconds, threads, max_queries):
     return done, el, ids
 
 
+def replica_queries(w, rank: int, world: int) -> np.ndarray:
+    """Rank `rank`'s own batch: rows [rank*nq, (rank+1)*nq) of one seeded
+    query stream, so the N replicas search N disjoint batches (weak scaling)."""
+    allq = synth.queries(w, w.n_queries * world)
+    return np.ascontiguousarray(allq[rank * w.n_queries:(rank + 1) * w.n_queries])
+
+
+def aggregate_replicas(local_ms, nq: int, world: int, dist, device):
+    """Max over ranks of each per-step time (ms), and the whole-job rate:
+    all ranks' queries divided by the slowest rank's step time."""
+    import torch
+    t = torch.tensor(local_ms, dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    worst = [float(x) for x in t.tolist()]
+    return worst, [world * nq / (m / 1e3) for m in worst]
+
+
 def learned_stop_comparison(args, w, ix, qd, gt_ids, sweep, ef_sel, device):
     """Train the stop on separate training queries, pick its threshold on a
     held-out part of them, then time it on the test batch next to the plain
@@ -361,8 +379,7 @@ def main():
     if dist:
         dist.barrier()
     # each rank serves its own query batch (replicas, weak scaling)
-    allq = synth.queries(w, w.n_queries * world)
-    q = np.ascontiguousarray(allq[rank * w.n_queries:(rank + 1) * w.n_queries])
+    q = replica_queries(w, rank, world)
     gt_ids, gt_d = ground_truth(args, w, f"{gtp}-r{rank}", q, local, world)
     ix = Index(idx, local)
     qd = torch.from_numpy(q).cuda()
@@ -448,13 +465,8 @@ def main():
     hops = st[:, 0].double().cpu().numpy()
 
     step_mean = float(np.mean(step_ms))
-    t_local = torch.tensor([step_mean, float(np.mean(e2e_ms)) if e2e_ms else step_mean], device="cuda",
-                           dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    step_max, e2e_max = float(t_local[0]), float(t_local[1])
-    value = world * nq / (step_max / 1e3)
-    e2e_value = world * nq / (e2e_max / 1e3)
+    (step_max, e2e_max), (value, e2e_value) = aggregate_replicas(
+        [step_mean, float(np.mean(e2e_ms)) if e2e_ms else step_mean], nq, world, dist, "cuda")
     if rank != 0:
         if dist:
             dist.destroy_process_group()

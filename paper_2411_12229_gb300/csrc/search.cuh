@@ -223,9 +223,7 @@ __device__ __forceinline__ QuerySide quantize_warp(const float *qr, uint32_t d, 
             reinterpret_cast<uint4 *>(planes)[w] = make_uint4(b0, b1, b2, b3);
         }
     }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) sq += __shfl_xor_sync(kFull, sq, o);
-    qs.sq = sq;
+    qs.sq = __reduce_add_sync(kFull, sq);
     return qs;
 }
 
@@ -449,8 +447,25 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
         while (cur < m) {
             if (hops >= hop_cap) { status |= SQG_STATUS_CAPACITY; break; }
             const uint32_t p = pid[cur] & kIdMask;
-            for (int i = cur + lane; i < m; i += 32)
-                if ((pid[i] & kIdMask) == p) pid[i] = p | kVisited;
+            // one pass over [cur, m): mark every copy of p visited (copies lie
+            // after cur, which is the first unvisited entry) and find the next
+            // unvisited entry after cur
+            int nxt = m;
+            for (int base = cur; base < m; base += 32) {
+                const int i = base + lane;
+                uint32_t v = kVisited;
+                if (i < m) {
+                    v = pid[i];
+                    if ((v & kIdMask) == p) {
+                        v = p | kVisited;
+                        pid[i] = v;
+                    }
+                }
+                if (nxt == m) {
+                    const uint32_t b = __ballot_sync(kFull, i > cur && !(v & kVisited));
+                    if (b) nxt = base + __ffs(b) - 1;
+                }
+            }
             if (lane == 0) {
                 hash_insert(H, hbits, p);
                 if (a.path && hops < a.path_cap) a.path[(size_t)qi * a.path_cap + hops] = p;
@@ -461,13 +476,6 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                 hash_migrate(Hs, hbits, Hg, a.hash_bits, lane);
                 H = Hg;
                 hbits = a.hash_bits;
-            }
-            // next unvisited beam entry after cur
-            int nxt = m;
-            for (int base = cur + 1; base < m; base += 32) {
-                int i = base + lane;
-                uint32_t b = __ballot_sync(kFull, i < m && !(pid[i] & kVisited));
-                if (b) { nxt = base + __ffs(b) - 1; break; }
             }
             if (!inflight || pend != p) {  // the prefetch always targets p; kept as a safeguard
                 if (inflight) {
@@ -587,10 +595,24 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                     const uint32_t oi = __shfl_sync(kFull, cid[t2], src);
 #pragma unroll
                     for (int t = 0; t < NB; ++t) rank[t] += kless(ok, oi, ck[t], cid[t]) ? 1 : 0;
-                    if (kless(ok, oi, bk, bi)) {
-                        b2k = bk; b2i = bi; bk = ok; bi = oi;
-                    } else if (kless(ok, oi, b2k, b2i)) {
-                        b2k = ok; b2i = oi;
+                }
+            }
+            // the best admitted candidate has rank 0 (ranks are distinct), the
+            // runner-up rank 1 (needed for the speculative prefetch only)
+#pragma unroll
+            for (int t = 0; t < NB; ++t) {
+                const uint32_t m0 = __ballot_sync(kFull, adm[t] && rank[t] == 0);
+                if (m0) {
+                    const int s = __ffs(m0) - 1;
+                    bk = __shfl_sync(kFull, ck[t], s);
+                    bi = __shfl_sync(kFull, cid[t], s);
+                }
+                if (a.prefetch == 2) {
+                    const uint32_t m1 = __ballot_sync(kFull, adm[t] && rank[t] == 1);
+                    if (m1) {
+                        const int s = __ffs(m1) - 1;
+                        b2k = __shfl_sync(kFull, ck[t], s);
+                        b2i = __shfl_sync(kFull, cid[t], s);
                     }
                 }
             }
@@ -646,8 +668,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
 #pragma unroll
                 for (int t = 0; t < NB; ++t)
                     if (adm[t]) minpos = min(minpos, cpos[t]);
-#pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) minpos = min(minpos, __shfl_xor_sync(kFull, minpos, o));
+                minpos = __reduce_min_sync(kFull, minpos);
                 int nxt_shift = 0;
                 for (int base = ((m - 1) & ~31); base >= (minpos & ~31); base -= 32) {
                     const int i = base + lane;
@@ -669,8 +690,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                     if (valid && cnt > 0 && i + cnt < ef) { pkey[i + cnt] = kk; pid[i + cnt] = ii; }
                     __syncwarp();
                 }
-#pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) nxt_shift += __shfl_xor_sync(kFull, nxt_shift, o);
+                nxt_shift = __reduce_add_sync(kFull, nxt_shift);
                 int newcur = m + nadm;  // "none"
 #pragma unroll
                 for (int t = 0; t < NB; ++t) {
@@ -683,8 +703,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                     }
                     inserted += __popc(__ballot_sync(kFull, keep));
                 }
-#pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) newcur = min(newcur, __shfl_xor_sync(kFull, newcur, o));
+                newcur = __reduce_min_sync(kFull, newcur);
                 if (nxt < m && nxt >= minpos) {
                     if (nxt + nxt_shift < ef) newcur = min(newcur, nxt + nxt_shift);
                 } else if (nxt < m) {
