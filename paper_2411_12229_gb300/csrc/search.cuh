@@ -69,7 +69,7 @@ struct SearchArgs {
     uint32_t *path;     // nq x path_cap: ids of the first expanded vertices, or null
     int path_cap;
     uint32_t warp_bytes, cta_bytes;
-    uint32_t o_buf0, o_buf1, o_bar, o_pkey, o_pid, o_hash, o_rkey, o_rid, o_planes;
+    uint32_t o_buf0, o_buf1, o_bar, o_pkey, o_pid, o_hash, o_rkey, o_rid, o_planes, o_spos;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -664,33 +664,35 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
             // ---- line 6: merge the admitted candidates and cut the beam to ef
             int inserted = 0;
             if (nadm > 0) {
-                int minpos = m;
+                // beam positions of the admitted candidates in rank order: a
+                // smaller key never has a larger position, so this is sorted
+                int *spos = reinterpret_cast<int *>(ws + a.o_spos);
 #pragma unroll
                 for (int t = 0; t < NB; ++t)
-                    if (adm[t]) minpos = min(minpos, cpos[t]);
-                minpos = __reduce_min_sync(kFull, minpos);
-                int nxt_shift = 0;
+                    if (adm[t]) spos[rank[t]] = cpos[t];
+                __syncwarp();
+                const int minpos = spos[0];
+                // number of admitted candidates placed at or before beam entry i
+                auto count_le = [&](int i) {
+                    int lo = 0, hi = nadm;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (spos[mid] <= i) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    return lo;
+                };
                 for (int base = ((m - 1) & ~31); base >= (minpos & ~31); base -= 32) {
                     const int i = base + lane;
                     const bool valid = i >= minpos && i < m;
-                    int cnt = 0;
-#pragma unroll
-                    for (int t2 = 0; t2 < NB; ++t2) {
-                        uint32_t mm = am[t2];
-                        while (mm) {
-                            const int src = __ffs(mm) - 1;
-                            mm &= mm - 1;
-                            cnt += __shfl_sync(kFull, cpos[t2], src) <= i ? 1 : 0;
-                        }
-                    }
-                    if (i == nxt) nxt_shift = cnt;
+                    const int cnt = valid ? count_le(i) : 0;
                     const float kk = valid ? pkey[i] : 0.0f;
                     const uint32_t ii = valid ? pid[i] : 0u;
                     __syncwarp();
                     if (valid && cnt > 0 && i + cnt < ef) { pkey[i + cnt] = kk; pid[i + cnt] = ii; }
                     __syncwarp();
                 }
-                nxt_shift = __reduce_add_sync(kFull, nxt_shift);
+                const int nxt_shift = nxt < m ? count_le(nxt) : 0;
                 int newcur = m + nadm;  // "none"
 #pragma unroll
                 for (int t = 0; t < NB; ++t) {

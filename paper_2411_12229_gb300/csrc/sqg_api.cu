@@ -261,6 +261,7 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     a.o_pid = (uint32_t)o; o = align_up(o + 4 * (size_t)max_ef, 16);
     a.o_rkey = (uint32_t)o; o = align_up(o + 4 * (size_t)max_k, 16);
     a.o_rid = (uint32_t)o; o = align_up(o + 4 * (size_t)max_k, 16);
+    a.o_spos = (uint32_t)o; o = align_up(o + 4 * (size_t)R, 16);
     // visited set: up to 2^10 slots in shared memory; a longer search moves
     // to its warp's full-size table in the workspace
     const uint32_t smem_bits_default = pl.ch < 0 ? 9u : 10u;

@@ -320,6 +320,31 @@ def test_learned_stop_constant_networks(tiny_index, oracle_mod):
         assert stop[2] >= 10 and stop[2] % 4 == 0 and stop[2] <= plain[2]
 
 
+def test_stop_features_partial_pins(tiny_index, oracle_mod):
+    """The learned stop's features are this project's definition (no paper
+    counterpart); what can be pinned from outside: rows appear exactly at
+    every `every`-th expansion once k results exist, f0 is that hop over
+    ef, f8 = k/ef, f15 = k/100, the counts are ordered (promising within
+    1.25 r_k >= within r_k, unvisited <= beam size <= ef), f14 is 0/1, and
+    the hit counts never decrease and end at the final recall."""
+    p, x, qs = tiny_index
+    O = oracle_mod.Index(p)
+    k, ef, every = 10, 40, 3
+    for i in range(6):
+        gt, _ = oracle_mod.bruteforce(x, qs[i], k)
+        ids, d, hops, st, F, hits, path = O.search(qs[i], k, ef, stop_every=every, gt=gt, trace_cap=1000,
+                                                   path_cap=1000)
+        assert len(F) > 0
+        rows_hops = np.rint(F[:, 0] * ef).astype(int)
+        assert np.all(rows_hops % every == 0) and np.all(np.diff(rows_hops) == every)
+        assert rows_hops[-1] <= hops < rows_hops[-1] + every
+        np.testing.assert_allclose(F[:, 8], k / ef, rtol=1e-6)
+        np.testing.assert_allclose(F[:, 15], k / 100, rtol=1e-6)
+        assert np.all(F[:, 12] >= F[:, 11]) and np.all(F[:, 2] <= F[:, 3] + 1e-6) and np.all(F[:, 3] <= 1 + 1e-6)
+        assert set(np.unique(F[:, 14])) <= {0.0, 1.0}
+        assert np.all(np.diff(hits) >= 0) and hits[-1] <= len(set(ids.tolist()) & set(gt.tolist()))
+
+
 # --------------------------------------------------------------- MLP training math
 
 def test_mlp_gradient_matches_finite_differences(oracle_mod):
