@@ -69,7 +69,7 @@ struct SearchArgs {
     uint32_t *path;     // nq x path_cap: ids of the first expanded vertices, or null
     int path_cap;
     uint32_t warp_bytes, cta_bytes;
-    uint32_t o_buf0, o_buf1, o_bar, o_pkey, o_pid, o_hash, o_rkey, o_rid, o_planes, o_spos;
+    uint32_t o_buf0, o_buf1, o_bar, o_beam, o_hash, o_res, o_planes, o_spos;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -369,10 +369,10 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
     unsigned char *ws = smem + a.cta_bytes + (size_t)warp * a.warp_bytes;
     unsigned char *buf[2] = {ws + a.o_buf0, ws + a.o_buf1};
     uint64_t *bar = reinterpret_cast<uint64_t *>(ws + a.o_bar);
-    float *pkey = reinterpret_cast<float *>(ws + a.o_pkey);
-    uint32_t *pid = reinterpret_cast<uint32_t *>(ws + a.o_pid);
-    float *rkey = reinterpret_cast<float *>(ws + a.o_rkey);
-    uint32_t *rid = reinterpret_cast<uint32_t *>(ws + a.o_rid);
+    // beam and result: (key bits, id) pairs; bit 31 of a beam id marks an
+    // expanded vertex
+    uint2 *beam = reinterpret_cast<uint2 *>(ws + a.o_beam);
+    uint2 *res = reinterpret_cast<uint2 *>(ws + a.o_res);
     uint32_t *planes = reinterpret_cast<uint32_t *>(ws + a.o_planes);
     const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
     // visited set: a shared-memory table, moved once to this warp's global
@@ -429,8 +429,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
         // ---- Algorithm 1, line 1: the beam and the result start from the entry
         int m = 1, cur = 0, rc = 0;
         if (lane == 0) {
-            pid[0] = a.entry;
-            pkey[0] = 0.0f;  // replaced by the entry's exact distance at its expansion
+            beam[0] = make_uint2(0u, a.entry);  // key: the entry's exact distance, set at its expansion
         }
         int cb = 0;                          // buffer holding the block to expand next
         uint32_t pend = a.entry;             // id whose block is in flight into buf[cb]
@@ -446,7 +445,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
 
         while (cur < m) {
             if (hops >= hop_cap) { status |= SQG_STATUS_CAPACITY; break; }
-            const uint32_t p = pid[cur] & kIdMask;
+            const uint32_t p = beam[cur].y & kIdMask;
             // one pass over [cur, m): mark every copy of p visited (copies lie
             // after cur, which is the first unvisited entry) and find the next
             // unvisited entry after cur
@@ -455,10 +454,10 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                 const int i = base + lane;
                 uint32_t v = kVisited;
                 if (i < m) {
-                    v = pid[i];
+                    v = beam[i].y;
                     if ((v & kIdMask) == p) {
                         v = p | kVisited;
-                        pid[i] = v;
+                        beam[i].y = v;
                     }
                 }
                 if (nxt == m) {
@@ -501,28 +500,28 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
 
             // ---- line 4: exact distance, implicit re-ranking
             const float dist_c = exact_dist<CH>(qv, reinterpret_cast<const float *>(blk), nch, lane);
-            if (hops == 1 && lane == 0) pkey[0] = dist_c;
+            if (hops == 1 && lane == 0) beam[0].x = __float_as_uint(dist_c);
             bool improved = false;
             {
                 const bool full = rc == k;
-                if (!full || kless(dist_c, p, rkey[k - 1], rid[k - 1])) {
+                if (!full || kless(dist_c, p, __uint_as_float(res[k - 1].x), res[k - 1].y)) {
                     improved = true;
                     int pos = 0;
                     for (int base = 0; base < rc; base += 32) {
                         int i = base + lane;
-                        pos += __popc(__ballot_sync(kFull, i < rc && kless(rkey[i], rid[i], dist_c, p)));
+                        const uint2 e = i < rc ? res[i] : make_uint2(0u, 0u);
+                        pos += __popc(__ballot_sync(kFull, i < rc && kless(__uint_as_float(e.x), e.y, dist_c, p)));
                     }
                     const int top = full ? k - 1 : rc;  // entries [pos, top) move up one
                     for (int base = ((top - 1) & ~31); base >= (pos & ~31) && top > pos; base -= 32) {
                         int i = base + lane;
                         bool mv = i >= pos && i < top;
-                        float kk = mv ? rkey[i] : 0.0f;
-                        uint32_t ii = mv ? rid[i] : 0u;
+                        const uint2 e = mv ? res[i] : make_uint2(0u, 0u);
                         __syncwarp();
-                        if (mv) { rkey[i + 1] = kk; rid[i + 1] = ii; }
+                        if (mv) res[i + 1] = e;
                         __syncwarp();
                     }
-                    if (lane == 0) { rkey[pos] = dist_c; rid[pos] = p; }
+                    if (lane == 0) res[pos] = make_uint2(__float_as_uint(dist_c), p);
                     rc = full ? k : rc + 1;
                 }
             }
@@ -530,8 +529,9 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
             // ---- line 5: estimates for all R neighbours from the same block
             const uint32_t *ids = reinterpret_cast<const uint32_t *>(blk + a.off_ids);
             const bool full = m == ef;
-            const float wk = pkey[ef - 1 < m ? ef - 1 : 0];
-            const uint32_t wi = pid[ef - 1 < m ? ef - 1 : 0] & kIdMask;
+            const uint2 we = beam[ef - 1 < m ? ef - 1 : 0];
+            const float wk = __uint_as_float(we.x);
+            const uint32_t wi = we.y & kIdMask;
             float ck[NB];
             uint32_t cid[NB];
             int cpos[NB];
@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
 #pragma unroll
                 for (int t = 0; t < NB; ++t) {
                     bool in = false;
-                    for (int i = 0; i < m && adm[t]; ++i) in |= (pid[i] & kIdMask) == cid[t];
+                    for (int i = 0; i < m && adm[t]; ++i) in |= (beam[i].y & kIdMask) == cid[t];
                     adm[t] = adm[t] && !in;
                 }
             }
@@ -564,11 +564,15 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                     int lo = 0, hi = m;
                     while (lo < hi) {
                         int mid = (lo + hi) >> 1;
-                        if (kless(pkey[mid], pid[mid] & kIdMask, ck[t], cid[t])) lo = mid + 1;
+                        const uint2 e = beam[mid];
+                        if (kless(__uint_as_float(e.x), e.y & kIdMask, ck[t], cid[t])) lo = mid + 1;
                         else hi = mid;
                     }
                     cpos[t] = lo;
-                    if (lo < m && pkey[lo] == ck[t] && (pid[lo] & kIdMask) == cid[t]) adm[t] = false;
+                    if (lo < m) {
+                        const uint2 e = beam[lo];
+                        if (__uint_as_float(e.x) == ck[t] && (e.y & kIdMask) == cid[t]) adm[t] = false;
+                    }
                 }
             }
             uint32_t am[NB];
@@ -620,8 +624,9 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
             // of the first unvisited beam entry and the best admitted candidate
             uint32_t next_id = kEmpty, runner_id = kEmpty;
             {
-                const float nk = nxt < m ? pkey[nxt] : kInf;
-                const uint32_t ni = nxt < m ? (pid[nxt] & kIdMask) : kEmpty;
+                const uint2 ne = nxt < m ? beam[nxt] : make_uint2(__float_as_uint(kInf), kEmpty);
+                const float nk = __uint_as_float(ne.x);
+                const uint32_t ni = nxt < m ? (ne.y & kIdMask) : kEmpty;
                 const bool cand_first = nadm > 0 && kless(bk, bi, nk, ni);
                 next_id = cand_first ? bi : ni;
                 if (a.prefetch == 2) {  // speculative: the runner-up, if no better candidate appears
@@ -633,12 +638,15 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                         int n2 = m;  // the unvisited beam entry after nxt
                         for (int base = nxt + 1; base < m; base += 32) {
                             const int i = base + lane;
-                            const uint32_t bb2 = __ballot_sync(kFull, i < m && !(pid[i] & kVisited));
+                            const uint32_t bb2 = __ballot_sync(kFull, i < m && !(beam[i].y & kVisited));
                             if (bb2) { n2 = base + __ffs(bb2) - 1; break; }
                         }
-                        if (n2 < m && kless(pkey[n2], pid[n2] & kIdMask, rk, ri)) {
-                            rk = pkey[n2];
-                            ri = pid[n2] & kIdMask;
+                        if (n2 < m) {
+                            const uint2 e2 = beam[n2];
+                            if (kless(__uint_as_float(e2.x), e2.y & kIdMask, rk, ri)) {
+                                rk = __uint_as_float(e2.x);
+                                ri = e2.y & kIdMask;
+                            }
                         }
                     }
                     runner_id = ri;
@@ -686,10 +694,9 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                     const int i = base + lane;
                     const bool valid = i >= minpos && i < m;
                     const int cnt = valid ? count_le(i) : 0;
-                    const float kk = valid ? pkey[i] : 0.0f;
-                    const uint32_t ii = valid ? pid[i] : 0u;
+                    const uint2 e = valid ? beam[i] : make_uint2(0u, 0u);
                     __syncwarp();
-                    if (valid && cnt > 0 && i + cnt < ef) { pkey[i + cnt] = kk; pid[i + cnt] = ii; }
+                    if (valid && cnt > 0 && i + cnt < ef) beam[i + cnt] = e;
                     __syncwarp();
                 }
                 const int nxt_shift = nxt < m ? count_le(nxt) : 0;
@@ -699,8 +706,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                     const int fp = cpos[t] + rank[t];
                     const bool keep = adm[t] && fp < ef;
                     if (keep) {
-                        pkey[fp] = ck[t];
-                        pid[fp] = cid[t];
+                        beam[fp] = make_uint2(__float_as_uint(ck[t]), cid[t]);
                         newcur = min(newcur, fp);
                     }
                     inserted += __popc(__ballot_sync(kFull, keep));
@@ -731,13 +737,14 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                                           __fmul_rn(0.25f, __fmul_rn((float)inserted, inv_R)));
             }
             if (stop_on && a.stop_every > 0 && hops % a.stop_every == 0 && rc == k) {
-                const float rk = rkey[k - 1];
+                const float rk = __uint_as_float(res[k - 1].x);
                 const float rk2 = __fmul_rn(1.25f, rk);
                 int u = 0, near1 = 0, near2 = 0;  // unvisited; of them with key <= rk, <= 1.25 rk
                 for (int base = 0; base < m; base += 32) {
                     const int i = base + lane;
-                    const bool un = i < m && !(pid[i] & kVisited);
-                    const float kk = un ? pkey[i] : 0.0f;
+                    const uint2 e = i < m ? beam[i] : make_uint2(0u, kVisited);
+                    const bool un = !(e.y & kVisited);
+                    const float kk = un ? __uint_as_float(e.x) : 0.0f;
                     u += __popc(__ballot_sync(kFull, un));
                     near1 += __popc(__ballot_sync(kFull, un && kk <= rk));
                     near2 += __popc(__ballot_sync(kFull, un && kk <= rk2));
@@ -754,8 +761,8 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                 f[1] = __fmul_rn(since, inv_ef);
                 f[2] = __fmul_rn((float)u, inv_ef);
                 f[3] = __fmul_rn((float)m, inv_ef);
-                f[4] = __fmul_rn(rkey[0], inv_den);
-                f[5] = u > 0 ? __fmul_rn(pkey[cur], inv_den) : 0.0f;
+                f[4] = __fmul_rn(__uint_as_float(res[0].x), inv_den);
+                f[5] = u > 0 ? __fmul_rn(__uint_as_float(beam[cur].x), inv_den) : 0.0f;
                 f[6] = __fmul_rn(dist_c, inv_den);
                 f[7] = __fmul_rn((float)inserted, __fdiv_rn(1.0f, (float)R));
                 f[8] = __fmul_rn((float)k, inv_ef);
@@ -780,7 +787,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                         int hit = 0;
                         const uint32_t *g = a.gt + (size_t)qi * a.gt_k;
                         for (int i = lane; i < rc; i += 32) {
-                            const uint32_t x = rid[i];
+                            const uint32_t x = res[i].y;
                             for (int b = 0; b < k; ++b) hit += g[b] == x ? 1 : 0;
                         }
 #pragma unroll
@@ -809,8 +816,9 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
         const bool ok = !(status & SQG_STATUS_TIMEOUT);
         for (int t = lane; t < k; t += 32) {
             const bool have = ok && t < rc;
-            a.out_ids[off + t] = have ? rid[t] : SQG_NO_ID;
-            a.out_dists[off + t] = have ? rkey[t] : __int_as_float(0x7f800000);
+            const uint2 e = have ? res[t] : make_uint2(0x7f800000u, SQG_NO_ID);
+            a.out_ids[off + t] = e.y;
+            a.out_dists[off + t] = __uint_as_float(e.x);
         }
         if (lane == 0) {
             if (a.stats) a.stats[qi] = sqg_query_stats{(uint32_t)hops, status};

@@ -257,10 +257,8 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     a.o_buf1 = (uint32_t)o; o += bb;
     a.o_bar = (uint32_t)o; o += 16;
     a.o_planes = (uint32_t)o; o = align_up(o + 16 * (d / 32), 16);
-    a.o_pkey = (uint32_t)o; o = align_up(o + 4 * (size_t)max_ef, 16);
-    a.o_pid = (uint32_t)o; o = align_up(o + 4 * (size_t)max_ef, 16);
-    a.o_rkey = (uint32_t)o; o = align_up(o + 4 * (size_t)max_k, 16);
-    a.o_rid = (uint32_t)o; o = align_up(o + 4 * (size_t)max_k, 16);
+    a.o_beam = (uint32_t)o; o = align_up(o + 8 * (size_t)max_ef, 16);
+    a.o_res = (uint32_t)o; o = align_up(o + 8 * (size_t)max_k, 16);
     a.o_spos = (uint32_t)o; o = align_up(o + 4 * (size_t)R, 16);
     // visited set: up to 2^10 slots in shared memory; a longer search moves
     // to its warp's full-size table in the workspace
