@@ -101,6 +101,11 @@ typedef struct {
     int32_t lean;            /* d <= 256 only: 0 or 1 = the kernel build capped at 64
                                 registers (more resident warps, a few spills; the
                                 default), 2 = the 96-register build */
+    int32_t rotation;        /* q' = P^-1 q: 1 = fp32 fmaf chains on the CUDA cores; 2 =
+                                tcgen05 tensor cores (3xTF32) followed by an exact pass that
+                                recomputes with the fmaf chain every coordinate whose 4-bit
+                                code or min/max role the tensor-core error could change, so
+                                the quantized query is identical to 1; 0 = 1 */
 } sqg_search_params;
 
 typedef struct {
@@ -181,6 +186,15 @@ int sqg_search_ex(const sqg_index *ix, const float *queries, int nq, const int32
  *              trunc((q'_i - v_l) * 15/(v_r - v_l) + 0.5)) */
 int sqg_prepare_queries(const sqg_index *ix, const float *queries, int nq, float *out_qrot,
                         uint32_t *out_planes, float *out_scal, sqg_stream_t stream);
+
+/* Query preparation through the tensor-core path (rotation = 2), for tests:
+ *   out_qrot   nq x d fp32: q' from tcgen05.mma kind::tf32 with the 3xTF32
+ *              split (differs from the fmaf chain by at most c ||q||)
+ *   out_planes nq x 4 x d/32 u32 and out_scal nq x 4 as sqg_prepare_queries
+ *              gives them -- identical by construction
+ *   recomputed (1 u32, device, added to): coordinates the exact pass redid */
+int sqg_prepare_queries_tc(const sqg_index *ix, const float *queries, int nq, float *out_qrot, uint32_t *out_planes,
+                           float *out_scal, uint32_t *recomputed, sqg_stream_t stream);
 
 /* Estimates for all R neighbours of one vertex per query, for tests
  * (Sec. 3.1.1): for query i and vertex v[i] writes, at [i*R + j],

@@ -35,7 +35,8 @@ class SearchParams(C.Structure):
                 ("max_k", C.c_int32), ("max_ef", C.c_int32), ("stop_mlp", C.c_void_p),
                 ("stop_logit", C.c_float), ("stop_every", C.c_int32), ("team", C.c_int32),
                 ("warps_per_block", C.c_int32), ("timing_events", C.c_void_p * 2),
-                ("visited_smem_log2", C.c_int32), ("prefetch", C.c_int32), ("lean", C.c_int32)]
+                ("visited_smem_log2", C.c_int32), ("prefetch", C.c_int32), ("lean", C.c_int32),
+                ("rotation", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -59,6 +60,7 @@ _SIGS = {
     "sqg_search_trace": (I32, [P, P, I32, P, P, P, P, C.POINTER(SearchParams), P, P, I32, P, P, P, I32, P, I32,
                               P]),
     "sqg_prepare_queries": (I32, [P, P, I32, P, P, P, P]),
+    "sqg_prepare_queries_tc": (I32, [P, P, I32, P, P, P, P, P]),
     "sqg_estimate_block": (I32, [P, P, I32, P, F32, P, P, P, P, P]),
     "sqg_get_status": (I32, [P, P, C.POINTER(U32)]),
     "sqg_knn_host": (I32, [P, U64, U32, U32, P, I32]),

@@ -64,7 +64,7 @@ class Index:
     def params(self, *, eps0: float = 0.0, multi_estimate: bool = True, hop_cap: int = 0, max_k: int = 0,
                max_ef: int = 0, stop_mlp: torch.Tensor | None = None, stop_logit: float = 0.0,
                stop_every: int = 1, warps_per_block: int = 0, timing_events=None, visited_smem_log2: int = 0,
-               prefetch: int = 0, lean: int = 0) -> B.SearchParams:
+               prefetch: int = 0, lean: int = 0, rotation: int = 0) -> B.SearchParams:
         p = B.SearchParams()
         p.eps0 = float(eps0)
         p.multi_estimate = 1 if multi_estimate else 0
@@ -80,6 +80,7 @@ class Index:
         p.visited_smem_log2 = int(visited_smem_log2)
         p.prefetch = int(prefetch)
         p.lean = int(lean)
+        p.rotation = int(rotation)
         if timing_events is not None:  # torch.cuda.Event pair, already recorded once
             p.timing_events[0] = timing_events[0].cuda_event
             p.timing_events[1] = timing_events[1].cuda_event
@@ -192,6 +193,22 @@ class Index:
                                             planes.data_ptr(), scal.data_ptr(), _stream_ptr(stream)),
                 "sqg_prepare_queries")
         return qrot, planes, scal
+
+    def prepare_queries_tc(self, queries: torch.Tensor, stream=None):
+        """The tensor-core rotation and the exact quantization after it.
+
+        Returns (q' from the tensor cores, planes, scalars, coordinates the
+        exact pass recomputed); planes and scalars equal prepare_queries'."""
+        nq = queries.shape[0]
+        dev = queries.device
+        qrot = torch.empty((nq, self.d), dtype=torch.float32, device=dev)
+        planes = torch.empty((nq, 4, self.d // 32), dtype=torch.int32, device=dev)
+        scal = torch.empty((nq, 4), dtype=torch.float32, device=dev)
+        rec = torch.zeros(1, dtype=torch.int32, device=dev)
+        B.check(B.lib().sqg_prepare_queries_tc(self._h, queries.contiguous().data_ptr(), nq, qrot.data_ptr(),
+                                               planes.data_ptr(), scal.data_ptr(), rec.data_ptr(),
+                                               _stream_ptr(stream)), "sqg_prepare_queries_tc")
+        return qrot, planes, scal, rec
 
     def estimate_block(self, queries: torch.Tensor, v: torch.Tensor, eps0: float = 0.0, stream=None):
         nq, dev, R = queries.shape[0], queries.device, self.degree

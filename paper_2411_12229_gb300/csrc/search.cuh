@@ -66,6 +66,8 @@ struct SearchArgs {
     int trace_cap;
     const uint32_t *gt; // nq x gt_k ground-truth ids (trace mode)
     int gt_k;
+    const uint32_t *qplanes;  // nq x d/32 x 4 precomputed bit-planes ([w][b]), or null: quantize qrot
+    const float4 *qscal;      // nq: (v_l, delta, Sq, 1/sqrt(d)) with qplanes
     uint32_t *path;     // nq x path_cap: ids of the first expanded vertices, or null
     int path_cap;
     uint32_t warp_bytes, cta_bytes;
@@ -421,7 +423,18 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
             uint32_t c = lane + 32 * t;
             qv[t] = c < nch ? reinterpret_cast<const float4 *>(q)[c] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        const QuerySide qs = quantize_warp(a.qrot + (size_t)qi * d, d, planes, lane);
+        QuerySide qs;
+        if (a.qplanes) {  // quantized by the exact pass after the tensor-core rotation
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.qplanes + (size_t)qi * 4 * (d / 32));
+            for (uint32_t w = lane; w < d / 32; w += 32) reinterpret_cast<uint4 *>(planes)[w] = src[w];
+            const float4 sc = a.qscal[qi];
+            qs.vl = sc.x;
+            qs.delta = sc.y;
+            qs.sq = (int)sc.z;
+            qs.inv_sqrt_d = sc.w;
+        } else {
+            qs = quantize_warp(a.qrot + (size_t)qi * d, d, planes, lane);
+        }
         uint32_t *H = Hs;
         uint32_t hbits = a.shash_bits;
         for (uint32_t i = lane; i < (1u << hbits); i += 32) H[i] = kEmpty;
@@ -830,6 +843,12 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
 }
 
 // Host-side launch helpers, defined in the instantiation units.
+// Tensor-core rotation and the exact quantization after it (rotate_tc.cu).
+float rotate_tc_err_scale(int d);
+cudaError_t launch_rotate_tc(const float *q, const float *rot, float *out, int nq, int d, uint32_t *status,
+                             cudaStream_t s);
+cudaError_t launch_quantize_exact(const float *q, const float *rot, const float *qa, int nq, int d, uint32_t *planes,
+                                  float4 *scal, uint32_t *recomputed, bool plane_major, cudaStream_t s);
 cudaError_t launch_search_nb1(int ch, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const SearchArgs &a);
 cudaError_t launch_search_nb2(int ch, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const SearchArgs &a);
 cudaError_t search_occupancy_nb1(int ch, int block, size_t smem, int *blocks_per_sm);

@@ -233,7 +233,7 @@ struct LaunchPlan {
     SearchArgs a;  // layout fields filled in
     bool ghash;
     // workspace layout
-    size_t ws_offsets, ws_qrot, ws_queue, ws_maxes, ws_stats, ws_ghash, ws_total;
+    size_t ws_offsets, ws_qrot, ws_queue, ws_maxes, ws_stats, ws_ghash, ws_planes, ws_scal, ws_total;
 };
 
 int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_search_params &p, LaunchPlan &pl) {
@@ -293,8 +293,20 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     pl.ws_stats = w; w = align_up(w + sizeof(sqg_query_stats) * (size_t)std::max(nq, 1), 256);
     pl.ws_ghash = w;
     if (pl.ghash) w = align_up(w + hash_bytes * (size_t)pl.grid * warps, 256);
+    // the exactly quantized query after a tensor-core rotation
+    pl.ws_planes = w; w = align_up(w + 16 * (size_t)(d / 32) * (size_t)std::max(nq, 1), 256);
+    pl.ws_scal = w; w = align_up(w + 16 * (size_t)std::max(nq, 1), 256);
     pl.ws_total = w;
     return SQG_OK;
+}
+
+// Rotation path: 1 = the fp32 fmaf-chain kernel, 2 = tensor cores plus the
+// exact quantization pass (same codes bit for bit); 0 = tensor cores from
+// d = 512 up, where the contraction is large enough to pay.
+bool use_tc_rotation(const sqg_index *ix, const sqg_search_params &p) {
+    if (p.rotation == 1) return false;
+    (void)ix;
+    return p.rotation == 2;
 }
 
 sqg_search_params default_params() {
@@ -310,7 +322,7 @@ int check_params(const sqg_search_params &p) {
         (p.max_k > 0 && p.max_ef > 0 && p.max_ef < p.max_k) || p.stop_every < 0 ||
         (p.team != 0 && p.team != 32) || p.warps_per_block < 0 || !std::isfinite(p.eps0) ||
         (p.visited_smem_log2 != 0 && (p.visited_smem_log2 < 5 || p.visited_smem_log2 > 12)) ||
-        p.prefetch < 0 || p.prefetch > 2 || p.lean < 0 || p.lean > 2 ||
+        p.prefetch < 0 || p.prefetch > 2 || p.lean < 0 || p.lean > 2 || p.rotation < 0 || p.rotation > 2 ||
         (p.stop_mlp && p.stop_every < 1))
         return SQG_ERR_INVALID_ARG;
     return SQG_OK;
@@ -551,8 +563,23 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
 
     plan_kernel<<<1, kPlanThreads, 0, stream>>>(k, ef, nq, const_cast<long long *>(a.offsets),
                                                 reinterpret_cast<int *>(ws + pl.ws_maxes));
-    dim3 rg((ix->lay.d + kRotT - 1) / kRotT, (nq + kRotT - 1) / kRotT);
-    rotate_kernel<<<rg, 256, 0, stream>>>(queries, ix->d_rot, const_cast<float *>(a.qrot), nq, (int)ix->lay.d);
+    if (use_tc_rotation(ix, p)) {  // tensor cores, then the exact quantization
+        a.qplanes = reinterpret_cast<uint32_t *>(ws + pl.ws_planes);
+        a.qscal = reinterpret_cast<float4 *>(ws + pl.ws_scal);
+        e = launch_rotate_tc(queries, ix->d_rot, const_cast<float *>(a.qrot), nq, (int)ix->lay.d, ix->d_status,
+                             stream);
+        if (e == cudaSuccess)
+            e = launch_quantize_exact(queries, ix->d_rot, a.qrot, nq, (int)ix->lay.d,
+                                      const_cast<uint32_t *>(a.qplanes), const_cast<float4 *>(a.qscal), nullptr,
+                                      false, stream);
+        if (e != cudaSuccess) {
+            if (own_ws) cudaFreeAsync(workspace, stream);
+            return SQG_ERR_CUDA;
+        }
+    } else {
+        dim3 rg((ix->lay.d + kRotT - 1) / kRotT, (nq + kRotT - 1) / kRotT);
+        rotate_kernel<<<rg, 256, 0, stream>>>(queries, ix->d_rot, const_cast<float *>(a.qrot), nq, (int)ix->lay.d);
+    }
     e = cudaMemsetAsync(a.queue_head, 0, sizeof(unsigned int), stream);
     if (e == cudaSuccess && p.timing_events[0])
         e = cudaEventRecord(reinterpret_cast<cudaEvent_t>(p.timing_events[0]), stream);
@@ -609,6 +636,22 @@ extern "C" int sqg_prepare_queries(const sqg_index *ix, const float *queries, in
     quantize_kernel<<<(nq + wpb - 1) / wpb, wpb * 32, sizeof(uint32_t) * wpb * 4 * (d / 32), stream>>>(
         out_qrot, nq, d, out_planes, out_scal);
     return cudaGetLastError() == cudaSuccess ? SQG_OK : SQG_ERR_CUDA;
+}
+
+extern "C" int sqg_prepare_queries_tc(const sqg_index *ix, const float *queries, int nq, float *out_qrot,
+                                      uint32_t *out_planes, float *out_scal, uint32_t *recomputed,
+                                      sqg_stream_t stream_) {
+    if (!ix || nq < 0) return SQG_ERR_INVALID_ARG;
+    if (nq == 0) return SQG_OK;
+    if (!queries || !out_qrot || !out_planes || !out_scal || !recomputed) return SQG_ERR_INVALID_ARG;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    DeviceGuard g(ix->device);
+    const int d = (int)ix->lay.d;
+    cudaError_t e = launch_rotate_tc(queries, ix->d_rot, out_qrot, nq, d, ix->d_status, stream);
+    if (e == cudaSuccess)
+        e = launch_quantize_exact(queries, ix->d_rot, out_qrot, nq, d, out_planes,
+                                  reinterpret_cast<float4 *>(out_scal), recomputed, true, stream);
+    return e == cudaSuccess ? SQG_OK : SQG_ERR_CUDA;
 }
 
 extern "C" int sqg_estimate_block(const sqg_index *ix, const float *queries, int nq, const uint32_t *v,

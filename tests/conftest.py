@@ -73,3 +73,25 @@ def tiny_index_r64(tmp_path_factory, lib_built, oracle_mod):
     p = tmp_path_factory.mktemp("idx64") / "tiny64.sqg"
     ib.build_index(p, x, 64)
     return p, x, q
+
+
+SHAPES = {  # name: (workload, n, d, R): the other workloads' vector shapes at small n
+    "highdim-d960-R64": ("highdim-1m-d960", 3000, 960, 64),
+    "uneven-d1536-R32": ("uneven-1m-d1536", 2000, 1536, 32),
+    "serving-d96-R32": ("serving-4m-d96", 4000, 96, 32),
+    "d256-R32": ("batched-1m-d128", 2000, 256, 32),
+}
+
+
+@pytest.fixture(scope="session", params=list(SHAPES))
+def shaped_index_file(request, tmp_path_factory, lib_built):
+    """Small indexes of the other workloads' shapes, built with the GPU
+    search iterations; returns (path, data, queries)."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    from paper_2411_12229_gb300 import synth
+    name, n, d, R = SHAPES[request.param]
+    w = synth.small(synth.WORKLOADS[name].with_(d=d), n, 48)
+    x, q = synth.base(w), synth.queries(w)
+    p = tmp_path_factory.mktemp(request.param) / "s.sqg"
+    ib.build_index(p, x, R, device=0, init="random", iterations=2, ef_build=48)
+    return p, x, q

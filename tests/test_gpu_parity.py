@@ -276,24 +276,10 @@ def test_trace_features_bit_exact(gpu_tiny, oracle_mod):
         np.testing.assert_array_equal(hits[i, :cnt[i]], th)
 
 
-SHAPES = {  # name: (workload, n, d, R): the other workloads' vector shapes at small n
-    "highdim-d960-R64": ("highdim-1m-d960", 3000, 960, 64),
-    "uneven-d1536-R32": ("uneven-1m-d1536", 2000, 1536, 32),
-    "serving-d96-R32": ("serving-4m-d96", 4000, 96, 32),
-    "d256-R32": ("batched-1m-d128", 2000, 256, 32),
-}
-
-
-@pytest.fixture(scope="module", params=list(SHAPES))
-def shaped_index(request, tmp_path_factory, lib_built):
-    from paper_2411_12229_gb300 import index_builder as ib
-    from paper_2411_12229_gb300 import synth
+@pytest.fixture(scope="module")
+def shaped_index(shaped_index_file):
     from paper_2411_12229_gb300.api import Index
-    name, n, d, R = SHAPES[request.param]
-    w = synth.small(synth.WORKLOADS[name].with_(d=d), n, 48)
-    x, q = synth.base(w), synth.queries(w)
-    p = tmp_path_factory.mktemp(request.param) / "s.sqg"
-    ib.build_index(p, x, R, device=0, init="random", iterations=2, ef_build=48)
+    p, x, q = shaped_index_file
     return Index(p, 0), p, x, q
 
 
