@@ -101,11 +101,13 @@ typedef struct {
     int32_t lean;            /* d <= 256 only: 0 or 1 = the kernel build capped at 64
                                 registers (more resident warps, a few spills; the
                                 default), 2 = the 96-register build */
-    int32_t rotation;        /* q' = P^-1 q: 1 = fp32 fmaf chains on the CUDA cores; 2 =
-                                tcgen05 tensor cores (3xTF32) followed by an exact pass that
-                                recomputes with the fmaf chain every coordinate whose 4-bit
-                                code or min/max role the tensor-core error could change, so
-                                the quantized query is identical to 1; 0 = 1 */
+    int32_t rotation;        /* q' = P^-1 q: 1 = the canonical fp32 order (see
+                                sqg_prepare_queries) on the CUDA cores; 2 = tcgen05 tensor
+                                cores (3xTF32) followed by an exact pass that recomputes in
+                                the canonical order every coordinate whose 4-bit code or
+                                min/max role the tensor-core error could change, so the
+                                quantized query is identical to 1; 0 = 2 for d >= 512,
+                                else 1 */
 } sqg_search_params;
 
 typedef struct {
@@ -177,8 +179,9 @@ int sqg_search_ex(const sqg_index *ix, const float *queries, int nq, const int32
                   size_t ws_bytes, sqg_query_stats *stats, sqg_stream_t stream);
 
 /* Query preparation alone (the first kernels of sqg_search), for tests:
- *   out_qrot   nq x d fp32: q' = P^-1 q (Eq. (4)), each coordinate an fmaf
- *              chain over j = 0..d-1 starting from 0
+ *   out_qrot   nq x d fp32: q' = P^-1 q (Eq. (4)) in the canonical order:
+ *              per 32-column chunk c an fmaf chain over j = 32c..32c+31 from
+ *              0, the chunk sums added in order c = 0, 1, ... to a total from 0
  *   out_planes nq x 4 x d/32 u32: bit (i mod 32) of word [b][i/32] = bit b
  *              of the 4-bit code qbar_i
  *   out_scal   nq x 4: (v_l, delta, Sq as float, 1/sqrt(d)) with
@@ -189,7 +192,7 @@ int sqg_prepare_queries(const sqg_index *ix, const float *queries, int nq, float
 
 /* Query preparation through the tensor-core path (rotation = 2), for tests:
  *   out_qrot   nq x d fp32: q' from tcgen05.mma kind::tf32 with the 3xTF32
- *              split (differs from the fmaf chain by at most c ||q||)
+ *              split (differs from the canonical order by at most c(d) ||q||)
  *   out_planes nq x 4 x d/32 u32 and out_scal nq x 4 as sqg_prepare_queries
  *              gives them -- identical by construction
  *   recomputed (1 u32, device, added to): coordinates the exact pass redid */

@@ -37,7 +37,8 @@
  * pins).  The search takes its decisions (which vertex to expand, what
  * enters the beam, when to stop) in fp32, in the same precision and order
  * as the device code, because a float decides an integer there:
- *   - rotation: q'_i = fmaf-chain over j = 0..D-1 of P^-1[i][j]*q_j from 0;
+ *   - rotation: q'_i = sum over chunks c = 0, 1, ... (in order, from 0) of
+ *     s_c = fmaf-chain over j = 32c..32c+31 of P^-1[i][j]*q_j from 0;
  *   - exact distance: 32 partial sums, partial l runs over float4 chunks
  *     l, l+32, ... (x, y, z, w in order, fmaf(d,d,acc)), then a pairwise
  *     tree that adds partials l and l^16, then ^8, ^4, ^2, ^1;
@@ -331,11 +332,18 @@ void orc_bruteforce(const float *data, uint64_t n, uint32_t d, const float *q, u
 /* Fp32 query side, in the device's precision and order                */
 /* ------------------------------------------------------------------ */
 
+/* q'_i = P^-1 q (Eq. (4)) in fp32: per chunk of 32 columns an fmaf chain
+ * started from 0, the chunk sums added to a total (from 0) in column order. */
 void orc_rotate_f32(const float *rot, uint32_t d, const float *q, float *y) {
     for (uint32_t i = 0; i < d; ++i) {
-        float acc = 0.0f;
-        for (uint32_t j = 0; j < d; ++j) acc = fmaf(rot[(uint64_t)i * d + j], q[j], acc);
-        y[i] = acc;
+        const float *row = rot + (uint64_t)i * d;
+        float total = 0.0f;
+        for (uint32_t c = 0; c < d; c += 32) {
+            float s = 0.0f;
+            for (uint32_t j = c; j < c + 32 && j < d; ++j) s = fmaf(row[j], q[j], s);
+            total = total + s;
+        }
+        y[i] = total;
     }
 }
 

@@ -1,51 +1,117 @@
 // rotate_tc.cu -- the batched query rotation q' = P^-1 q (Eq. (4)) on the
 // 5th-generation tensor cores, and the exact 4-bit quantization built on it.
 //
+// The canonical fp32 rotation (the one the CUDA-core kernel and the oracle
+// compute) is chunked: q'_i = (((0 + s_0) + s_1) + ... ) over the d/32
+// chunks, s_c an fmaf chain over j = 32c .. 32c+31 started from 0.
+//
 // rotate_tc_kernel: one CTA computes a 128-query x 128-output tile as
-// D = A B^T with A = the queries (K-major), B = the rows of P^-1 (K-major),
-// accumulated in tensor memory by tcgen05.mma kind::tf32.  fp32 accuracy
-// comes from splitting every operand into a tf32 high part and a tf32 low
-// part: a.b ~ hi(a)hi(b) + hi(a)lo(b) + lo(a)hi(b) (three MMAs per K step).
-// Operands are staged in shared memory by the CTA's threads (the split is
-// done on the way) in the no-swizzle K-major core-matrix layout; one thread
-// issues the MMAs and commits them to an mbarrier; four warps read the
-// accumulator back with tcgen05.ld.
+// D = A B^T with A = the queries and B = the rows of P^-1, both K-major,
+// with tcgen05.mma kind::tf32.  fp32 accuracy comes from the 3xTF32 split
+// a.b ~ hi(a)hi(b) + hi(a)lo(b) + lo(a)hi(b), hi = tf32(x), lo = tf32(x - hi).
+// Warp roles:
+//   warp 0      TMA producer: per 32-wide K chunk, the raw query tile and the
+//               pre-split hi/lo tiles of P^-1 (cp.async.bulk.tensor, 128-byte
+//               swizzle) into a 3-stage ring;
+//   warp 1      MMA issuer: 12 MMAs per chunk into one of two TMEM buffers;
+//   warps 2-5   split the query tile into hi (in place) and lo;
+//   warps 6-9   drain each chunk's 128 x 128 result from TMEM (tcgen05.ld)
+//               and add it to fp32 registers, one tile row per thread.
+// Draining per chunk keeps the tensor cores' accumulation short (96 products
+// per accumulator), which is what makes the error bound below tight.
 //
 // quantize_exact_kernel: the search's decisions depend on the 4-bit codes,
-// v_l and delta being exactly those of the canonical fp32 rotation (an
-// fmaf chain over j = 0..d-1).  The tensor-core q' differs from it by at
-// most err = c * ||q|| (a worst-case bound on both accumulations), so every
+// v_l and Delta being exactly those of the canonical rotation.  The
+// tensor-core q' differs from it by at most err = c(d) * ||q||, so every
 // coordinate whose code or whose role as min/max could change within err is
-// recomputed with the canonical chain; the rest are decided from q'.  The
-// result is bit-identical to quantizing the canonical rotation.
+// recomputed in the canonical order (one warp per coordinate, chunks on the
+// lanes); the rest are decided from q'.  The result is bit-identical to
+// quantizing the canonical rotation.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "../../include/sqg.h"
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 32, kThreads = 128;
-constexpr int kPiece = BM * BK * 4;                       // one 128 x 32 fp32 operand piece, bytes
-constexpr uint32_t kCoreRowGroupBytes = (BK / 4) * 128;   // stride between 8-row groups
+constexpr int BM = 128, BN = 128, BK = 32;  // BK fp32 = one 128-byte swizzled row
+constexpr int kStages = 3;
+constexpr int kTile = BM * BK * 4;          // 16 KB
+constexpr int kStageBytes = 4 * kTile;      // query raw->hi, query lo, P hi, P lo
+constexpr int kWarps = 10, kThreads = kWarps * 32;
+constexpr int kConvWarp0 = 2, kConvWarps = 4, kDrainWarp0 = 6;
+constexpr uint32_t kTmemCols = 2 * BN;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// byte offset of element (row, k) of a 128 x BK piece in the no-swizzle
-// K-major layout: 8 x 16-byte core matrices, K-adjacent ones 128 B apart,
-// row groups kCoreRowGroupBytes apart
-__device__ __forceinline__ uint32_t core_off(int row, int k) {
-    return (uint32_t)((row >> 3) * kCoreRowGroupBytes + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-// shared-memory matrix descriptor: start, leading (K) and stride (M/N)
-// byte offsets, the fixed 0b001 field at bits 46-48, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+__device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool bar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(20000u)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete; give up after
+// kWaitNs or as soon as another role has given up (abort flag).
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    const unsigned long long t0 = gtime();
+    for (;;) {
+        if (bar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtime() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand in the 128-byte
+// swizzle layout written by the tensor map: 8-row groups 1024 B apart
+// (stride byte offset), leading byte offset unused (1), the fixed 0b001 at
+// bits 46-48, layout type 2 (128-byte swizzle) at bits 61-63.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
     uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
@@ -69,152 +135,210 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
         : "memory");
 }
 
-__device__ __forceinline__ bool bar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(100000u)
-        : "memory");
-    return ok != 0;
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
 }
 
-__device__ __forceinline__ bool bar_wait_bounded(uint32_t bar, uint32_t parity) {
-    unsigned long long t0;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    for (;;) {
-        if (bar_try_wait(bar, parity)) return true;
-        unsigned long long t;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (t - t0 > kWaitNs) return false;
-    }
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+          "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+          "=r"(v[30]), "=r"(v[31])
+        : "r"(addr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    rotate_tc_kernel(const float *__restrict__ q, const float *__restrict__ rot, float *__restrict__ out, int nq,
-                     int d, uint32_t *status) {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *Ahi = sm, *Alo = sm + kPiece, *Bhi = sm + 2 * kPiece, *Blo = sm + 3 * kPiece;
-    __shared__ __align__(8) uint64_t bar;
+    rotate_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap phimap,
+                     const __grid_constant__ CUtensorMap plomap, float *__restrict__ out, int nq, int d,
+                     uint32_t *status) {
+    extern __shared__ unsigned char smraw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
+                                                          ~static_cast<uintptr_t>(1023));
+    __shared__ __align__(8) uint64_t full_bar[kStages], conv_bar[kStages], empty_bar[kStages];
+    __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], done_bar;
     __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    volatile int *abort_v = &abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;
+    const int c0 = blockIdx.x * BN, r0 = blockIdx.y * BM;  // column tiles vary fastest: query tile shared in L2
+    const int nchunk = d / BK;
 
-    if (warp == 0) {  // 128 fp32 accumulator columns in tensor memory
+    if (warp == 0) {  // two 128-column fp32 accumulators in tensor memory
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
-                     "r"(128)
+                     "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)) : "memory");
+    if (tid == 32) {
+        for (int s = 0; s < kStages; ++s) {
+            bar_init(saddr(&full_bar[s]), 1);
+            bar_init(saddr(&conv_bar[s]), kConvWarps);
+            bar_init(saddr(&empty_bar[s]), 1);
+        }
+        for (int t = 0; t < 2; ++t) {
+            bar_init(saddr(&tfull_bar[t]), 1);
+            bar_init(saddr(&tempty_bar[t]), 4);
+        }
+        bar_init(saddr(&done_bar), 1);
+        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
+    const uint32_t base = saddr(sm);
+    // stage s: [query hi | query lo | P hi | P lo], each 1024-byte aligned
+    auto tile = [&](int s, int which) -> uint32_t { return base + (uint32_t)(s * kStageBytes + which * kTile); };
 
-    uint32_t phase = 0;
-    bool ok = true;
-    for (int k0 = 0; k0 < d && ok; k0 += BK) {
-        // stage the four pieces: each thread moves float4 runs (4 consecutive k)
-        for (int e = tid; e < BM * (BK / 4); e += kThreads) {
-            const int row = e / (BK / 4), k = (e % (BK / 4)) * 4;
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-            if (r0 + row < nq) a = *reinterpret_cast<const float4 *>(q + (size_t)(r0 + row) * d + k0 + k);
-            if (c0 + row < d) b = *reinterpret_cast<const float4 *>(rot + (size_t)(c0 + row) * d + k0 + k);
-            float4 ah, al, bh, bl;
-            ah.x = tf32_round(a.x); al.x = tf32_round(a.x - ah.x);
-            ah.y = tf32_round(a.y); al.y = tf32_round(a.y - ah.y);
-            ah.z = tf32_round(a.z); al.z = tf32_round(a.z - ah.z);
-            ah.w = tf32_round(a.w); al.w = tf32_round(a.w - ah.w);
-            bh.x = tf32_round(b.x); bl.x = tf32_round(b.x - bh.x);
-            bh.y = tf32_round(b.y); bl.y = tf32_round(b.y - bh.y);
-            bh.z = tf32_round(b.z); bl.z = tf32_round(b.z - bh.z);
-            bh.w = tf32_round(b.w); bl.w = tf32_round(b.w - bh.w);
-            const uint32_t off = core_off(row, k);
-            *reinterpret_cast<float4 *>(Ahi + off) = ah;
-            *reinterpret_cast<float4 *>(Alo + off) = al;
-            *reinterpret_cast<float4 *>(Bhi + off) = bh;
-            *reinterpret_cast<float4 *>(Blo + off) = bl;
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int k = 0; k < nchunk; ++k) {
+                const int s = k % kStages, n = k / kStages;
+                if (n >= 1 && !bar_wait(saddr(&empty_bar[s]), (uint32_t)((n - 1) & 1), abort_v)) break;
+                bar_arrive_tx(saddr(&full_bar[s]), 3 * kTile);
+                tma_load_2d(tile(s, 0), &qmap, k * BK, r0, saddr(&full_bar[s]));
+                tma_load_2d(tile(s, 2), &phimap, k * BK, c0, saddr(&full_bar[s]));
+                tma_load_2d(tile(s, 3), &plomap, k * BK, c0, saddr(&full_bar[s]));
+            }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            for (int k = 0; k < nchunk; ++k) {
+                const int s = k % kStages, n = k / kStages, t = k & 1, m = k >> 1;
+                if (!bar_wait(saddr(&full_bar[s]), (uint32_t)(n & 1), abort_v)) break;
+                if (!bar_wait(saddr(&conv_bar[s]), (uint32_t)(n & 1), abort_v)) break;
+                if (m >= 1 && !bar_wait(saddr(&tempty_bar[t]), (uint32_t)((m - 1) & 1), abort_v)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dt = tmem + (uint32_t)(t * BN);
+#pragma unroll
+                for (int st = 0; st < BK / 8; ++st) {  // K = 8 per MMA = 32 bytes along the swizzled row
+                    const uint32_t ko = (uint32_t)st * 32;
+                    const uint64_t ah = desc_sw128(tile(s, 0) + ko), al = desc_sw128(tile(s, 1) + ko);
+                    const uint64_t bh = desc_sw128(tile(s, 2) + ko), bl = desc_sw128(tile(s, 3) + ko);
+                    mma_tf32(dt, ah, bh, st > 0 ? 1u : 0u);
+                    mma_tf32(dt, ah, bl, 1u);
+                    mma_tf32(dt, al, bh, 1u);
+                }
+                mma_commit(saddr(&empty_bar[s]));
+                mma_commit(saddr(&tfull_bar[t]));
+            }
+            // every MMA this thread issued has finished before TMEM is freed
+            mma_commit(saddr(&done_bar));
+            if (!bar_wait(saddr(&done_bar), 0u, abort_v)) {
+                const unsigned long long t0 = gtime();
+                while (!bar_try_wait(saddr(&done_bar), 0u) && gtime() - t0 < kWaitNs) {
+                }
+            }
+        }
+    } else if (warp < kDrainWarp0) {
+        const int ct = tid - kConvWarp0 * 32;
+        for (int k = 0; k < nchunk; ++k) {
+            const int s = k % kStages, n = k / kStages;
+            if (!bar_wait(saddr(&full_bar[s]), (uint32_t)(n & 1), abort_v)) break;
+            float4 *raw = reinterpret_cast<float4 *>(sm + s * kStageBytes);
+            float4 *lo = reinterpret_cast<float4 *>(sm + s * kStageBytes + kTile);
+            // elementwise, so the swizzled positions need no decoding
+            for (int i = ct; i < kTile / 16; i += kConvWarps * 32) {
+                const float4 x = raw[i];
+                float4 h, l;
+                h.x = tf32_round(x.x); l.x = tf32_round(__fsub_rn(x.x, h.x));
+                h.y = tf32_round(x.y); l.y = tf32_round(__fsub_rn(x.y, h.y));
+                h.z = tf32_round(x.z); l.z = tf32_round(__fsub_rn(x.z, h.z));
+                h.w = tf32_round(x.w); l.w = tf32_round(__fsub_rn(x.w, h.w));
+                raw[i] = h;
+                lo[i] = l;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) bar_arrive(saddr(&conv_bar[s]));
+        }
+    } else {
+        const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31 = tile rows
+        float acc[BN];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) acc[j] = 0.0f;
+        bool ok = true;
+        for (int k = 0; k < nchunk; ++k) {
+            const int t = k & 1, m = k >> 1;
+            if (!bar_wait(saddr(&tfull_bar[t]), (uint32_t)(m & 1), abort_v)) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-            for (int s = 0; s < BK / 8; ++s) {  // K = 8 per MMA: two core matrices
-                const uint32_t ko = (uint32_t)s * 2 * 128;
-                const uint64_t ah = smem_desc(saddr(Ahi) + ko, 128, kCoreRowGroupBytes);
-                const uint64_t al = smem_desc(saddr(Alo) + ko, 128, kCoreRowGroupBytes);
-                const uint64_t bh = smem_desc(saddr(Bhi) + ko, 128, kCoreRowGroupBytes);
-                const uint64_t bl = smem_desc(saddr(Blo) + ko, 128, kCoreRowGroupBytes);
-                mma_tf32(tmem, ah, bh, (k0 > 0 || s > 0) ? 1u : 0u);
-                mma_tf32(tmem, ah, bl, 1u);
-                mma_tf32(tmem, al, bh, 1u);
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             saddr(&bar))
-                         : "memory");
-        }
-        // the pieces are overwritten next: wait for the MMAs that read them
-        ok = bar_wait_bounded(saddr(&bar), phase);
-        if (!ok) bar_wait_bounded(saddr(&bar), phase);  // once more before giving up
-        phase ^= 1u;
-        ok = __syncthreads_and(ok);
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp w holds accumulator rows (TMEM lanes) 32w .. 32w+31
-    const int row = r0 + warp * 32 + lane;
-#pragma unroll 1
-    for (int cc = 0; cc < BN; cc += 32) {
-        uint32_t v[32];
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(ta)
-            : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (ok && row < nq) {
+            for (int cc = 0; cc < BN / 32; ++cc) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * BN + cc * 32), v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int col = c0 + cc + j;
-                if (col < d) out[(size_t)row * d + col] = __uint_as_float(v[j]);
+                for (int j = 0; j < 32; ++j) acc[cc * 32 + j] = __fadd_rn(acc[cc * 32 + j], __uint_as_float(v[j]));
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) bar_arrive(saddr(&tempty_bar[t]));
+        }
+        const int row = r0 + quarter * 32 + lane;
+        if (ok && !*abort_v && row < nq) {
+            float4 *o = reinterpret_cast<float4 *>(out + (size_t)row * d + c0);
+            const int ncol = d - c0 < BN ? d - c0 : BN;  // a multiple of 32
+#pragma unroll
+            for (int j = 0; j < BN / 4; ++j)
+                if (4 * j < ncol) o[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
-    if (!ok && tid == 0) atomicOr(status, SQG_STATUS_TIMEOUT);
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+    if (tid == 0 && *abort_v) atomicOr(status, SQG_STATUS_TIMEOUT);
 }
 
-// The canonical rotated coordinate i: fmaf chain over j = 0..d-1 from 0
-// (row and query read four at a time; the order of the chain is unchanged).
-__device__ __forceinline__ float canonical_coord(const float *__restrict__ rotrow, const float *__restrict__ q,
-                                                 int d) {
-    const float4 *r4 = reinterpret_cast<const float4 *>(rotrow);
-    const float4 *q4 = reinterpret_cast<const float4 *>(q);
-    float acc = 0.0f;
-    for (int j = 0; j < d / 4; ++j) {
-        const float4 r = r4[j], v = q4[j];
-        acc = __fmaf_rn(r.x, v.x, acc);
-        acc = __fmaf_rn(r.y, v.y, acc);
-        acc = __fmaf_rn(r.z, v.z, acc);
-        acc = __fmaf_rn(r.w, v.w, acc);
+// hi = tf32(x), lo = tf32(x - hi), elementwise (the rows of P^-1, once per index)
+__global__ void split_tf32_kernel(const float *__restrict__ x, float *__restrict__ hi, float *__restrict__ lo,
+                                  size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float h = tf32_round(x[i]);
+        hi[i] = h;
+        lo[i] = tf32_round(__fsub_rn(x[i], h));
     }
-    return acc;
+}
+
+// The canonical rotated coordinate of one row, computed by a whole warp:
+// lane c (and c + 32) runs the chunk chain s_c, then every lane adds the
+// chunk sums in order c = 0, 1, ...; all lanes return the same value.
+__device__ __forceinline__ float chunk_chain(const float *__restrict__ row, const float *__restrict__ q) {
+    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+    const float4 *q4 = reinterpret_cast<const float4 *>(q);
+    float s = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float4 r = r4[j], v = q4[j];
+        s = __fmaf_rn(r.x, v.x, s);
+        s = __fmaf_rn(r.y, v.y, s);
+        s = __fmaf_rn(r.z, v.z, s);
+        s = __fmaf_rn(r.w, v.w, s);
+    }
+    return s;
+}
+
+__device__ __forceinline__ float warp_canonical(const float *__restrict__ row, const float *__restrict__ q, int d,
+                                                int lane) {
+    const int nc = d / 32;
+    const float s0 = lane < nc ? chunk_chain(row + 32 * lane, q + 32 * lane) : 0.0f;
+    const float s1 = lane + 32 < nc ? chunk_chain(row + 32 * (lane + 32), q + 32 * (lane + 32)) : 0.0f;
+    float tot = 0.0f;
+    for (int c = 0; c < nc; ++c) tot = __fadd_rn(tot, __shfl_sync(0xFFFFFFFFu, c < 32 ? s0 : s1, c & 31));
+    return tot;
 }
 
 constexpr int kMaxWords = 64;  // d <= 2048
@@ -234,7 +358,7 @@ __global__ void quantize_exact_kernel(const float *__restrict__ q, const float *
     const float *qq = q + (size_t)qi * d;
     const float *qr = qa + (size_t)qi * d;
     float x[kMaxWords];
-    uint64_t exact = 0;  // bit w: x[w] already canonical
+    uint64_t exact = 0;  // bit w: x[w] is canonical
     float ss = 0.0f;
     for (int w = 0; w < nw; ++w) {
         x[w] = qr[w * 32 + lane];
@@ -242,27 +366,40 @@ __global__ void quantize_exact_kernel(const float *__restrict__ q, const float *
         ss = fmaf(v, v, ss);
     }
     for (int o = 16; o >= 1; o >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
-    const float err = err_scale * sqrtf(ss) * 1.0001f + 1e-30f;
+    const float err = err_scale * sqrtf(ss) + 1e-30f;
     int nrec = 0;
-    // candidates for the minimum and the maximum: recompute them exactly
+    // candidates for the minimum and the maximum (within 2 err of the
+    // tensor-core extremes): recompute them
     float lo = x[0], hi = x[0];
-    for (int w = 1; w < nw; ++w) { lo = fminf(lo, x[w]); hi = fmaxf(hi, x[w]); }
+    for (int w = 1; w < nw; ++w) {
+        lo = fminf(lo, x[w]);
+        hi = fmaxf(hi, x[w]);
+    }
     for (int o = 16; o >= 1; o >>= 1) {
         lo = fminf(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
         hi = fmaxf(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
     }
     for (int w = 0; w < nw; ++w) {
-        if (x[w] <= lo + 2.0f * err || x[w] >= hi - 2.0f * err) {
-            x[w] = canonical_coord(rot + (size_t)(w * 32 + lane) * d, qq, d);
-            exact |= 1ull << w;
-            ++nrec;
+        uint32_t m = __ballot_sync(0xFFFFFFFFu, x[w] <= lo + 2.0f * err || x[w] >= hi - 2.0f * err);
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            const float v = warp_canonical(rot + (size_t)(w * 32 + l) * d, qq, d, lane);
+            if (lane == l) {
+                x[w] = v;
+                exact |= 1ull << w;
+                ++nrec;
+            }
         }
     }
     // exact v_l, v_r: the same comparisons as the canonical quantizer
     const float inf = __int_as_float(0x7f800000);
     float vl = inf, vr = -inf;
     for (int w = 0; w < nw; ++w)
-        if (exact >> w & 1ull) { vl = x[w] < vl ? x[w] : vl; vr = x[w] > vr ? x[w] : vr; }
+        if (exact >> w & 1ull) {
+            vl = x[w] < vl ? x[w] : vl;
+            vr = x[w] > vr ? x[w] : vr;
+        }
     for (int o = 16; o >= 1; o >>= 1) {
         const float a = __shfl_xor_sync(0xFFFFFFFFu, vl, o), b = __shfl_xor_sync(0xFFFFFFFFu, vr, o);
         vl = a < vl ? a : vl;
@@ -274,18 +411,27 @@ __global__ void quantize_exact_kernel(const float *__restrict__ q, const float *
     const float margin = err * inv * 1.01f + 1e-4f;  // in units of the code
     int sq = 0;
     for (int w = 0; w < nw; ++w) {
+        float y = 0.0f;
+        bool redo = false;
+        if (range > 0.0f) {
+            y = __fadd_rn(__fmul_rn(__fsub_rn(x[w], vl), inv), 0.5f);
+            // an integer boundary (1 .. 15) within the margin: decide exactly
+            const float nearest = fminf(fmaxf(rintf(y), 1.0f), 15.0f);
+            redo = !(exact >> w & 1ull) && fabsf(y - nearest) <= margin;
+        }
+        uint32_t m = __ballot_sync(0xFFFFFFFFu, redo);
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            const float v = warp_canonical(rot + (size_t)(w * 32 + l) * d, qq, d, lane);
+            if (lane == l) {
+                x[w] = v;
+                ++nrec;
+                y = __fadd_rn(__fmul_rn(__fsub_rn(v, vl), inv), 0.5f);
+            }
+        }
         int t = 0;
         if (range > 0.0f) {
-            float y = __fadd_rn(__fmul_rn(__fsub_rn(x[w], vl), inv), 0.5f);
-            if (!(exact >> w & 1ull)) {
-                // an integer boundary (1 .. 15) within the margin: decide exactly
-                const float nearest = fminf(fmaxf(rintf(y), 1.0f), 15.0f);
-                if (fabsf(y - nearest) <= margin) {
-                    x[w] = canonical_coord(rot + (size_t)(w * 32 + lane) * d, qq, d);
-                    ++nrec;
-                    y = __fadd_rn(__fmul_rn(__fsub_rn(x[w], vl), inv), 0.5f);
-                }
-            }
             t = __float2int_rz(y);
             t = t > 15 ? 15 : t;
         }
@@ -312,38 +458,83 @@ __global__ void quantize_exact_kernel(const float *__restrict__ q, const float *
     }
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
+                cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// rows x cols fp32, row-major; boxes of 128 rows x 32 columns, 128-byte swizzle,
+// rows past the end read as zeros
+bool make_tile_map(CUtensorMap *m, const float *base, uint64_t rows, uint64_t cols) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * sizeof(float)};
+    cuuint32_t box[2] = {BK, BM};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 namespace sqg {
 
 // Bound on |tensor-core q'_i - canonical q'_i| per unit of ||q||, with
-// u = 2^-24 and sum_j |P_ij q_j| <= ||P_i|| ||q|| = ||q||:
+// u = 2^-24, C = d/32 chunks and sum_j |P_ij q_j| <= ||P_i|| ||q|| = ||q||:
 //  * the 3xTF32 split drops lo(a)lo(b) and the tf32 rounding of both low
 //    parts: at most 3 * 2^-22 = 12u of every |P_ij q_j|;
-//  * the tensor cores add 3d exact tf32 products in fp32; every addition is
-//    taken to err by at most 2u (one unit in the last place, so truncation
-//    is covered) of a partial sum bounded by the sum of magnitudes: 6d u;
-//  * the canonical chain rounds each of its d fmaf once: d u.
-// The total, (7d + 12) u, is doubled in case the tensor cores' internal
-// alignment drops one more bit than this model allows.
+//  * per chunk the tensor cores add 96 exact tf32 products into a fresh fp32
+//    accumulator; every addition is taken to err by at most 2u (one unit in
+//    the last place, so truncation is covered) of a partial sum bounded by
+//    the chunk's sum of magnitudes: 192u over all chunks;
+//  * adding the C chunk results in fp32 registers: C u;
+//  * the canonical order: 32-term chains (32u) and C chunk additions (C u).
+// The total, (236 + 2C) u, is taken twice and 5 % more, in case the tensor
+// cores' internal alignment drops one more bit than this model allows and
+// for the rounding of ||q|| itself.
 float rotate_tc_err_scale(int d) {
     const double u = 1.0 / 16777216.0;
-    return (float)(2.0 * (7.0 * d + 12.0) * u);
+    const double C = d / 32;
+    return (float)(2.1 * (236.0 + 2.0 * C) * u);
 }
 
-cudaError_t launch_rotate_tc(const float *q, const float *rot, float *out, int nq, int d, uint32_t *status,
-                             cudaStream_t s) {
-    const int smem = 4 * kPiece;
-    cudaError_t e = cudaFuncSetAttribute(rotate_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+cudaError_t launch_split_tf32(const float *x, float *hi, float *lo, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const size_t blocks = (n + 255) / 256;
+    split_tf32_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(x, hi, lo, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rotate_tc(const float *q, const float *rot_hi, const float *rot_lo, float *out, int nq, int d,
+                             uint32_t *status, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    if (d % BK != 0) return cudaErrorInvalidValue;
+    CUtensorMap qm, hm, lm;
+    if (!make_tile_map(&qm, q, (uint64_t)nq, (uint64_t)d) || !make_tile_map(&hm, rot_hi, (uint64_t)d, (uint64_t)d) ||
+        !make_tile_map(&lm, rot_lo, (uint64_t)d, (uint64_t)d))
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(rotate_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
-    dim3 grid((nq + BM - 1) / BM, (d + BN - 1) / BN);
-    rotate_tc_kernel<<<grid, kThreads, smem, s>>>(q, rot, out, nq, d, status);
+    dim3 grid((d + BN - 1) / BN, (nq + BM - 1) / BM);
+    rotate_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(qm, hm, lm, out, nq, d, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_quantize_exact(const float *q, const float *rot, const float *qa, int nq, int d, uint32_t *planes,
                                   float4 *scal, uint32_t *recomputed, bool plane_major, cudaStream_t s) {
     if (d / 32 > kMaxWords) return cudaErrorInvalidValue;
+    if (nq <= 0) return cudaSuccess;
     const int wpb = 4;
     quantize_exact_kernel<<<(nq + wpb - 1) / wpb, wpb * 32, 0, s>>>(q, rot, qa, nq, d, rotate_tc_err_scale(d),
                                                                    planes, scal, recomputed, plane_major ? 1 : 0);

@@ -845,8 +845,9 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
 // Host-side launch helpers, defined in the instantiation units.
 // Tensor-core rotation and the exact quantization after it (rotate_tc.cu).
 float rotate_tc_err_scale(int d);
-cudaError_t launch_rotate_tc(const float *q, const float *rot, float *out, int nq, int d, uint32_t *status,
-                             cudaStream_t s);
+cudaError_t launch_split_tf32(const float *x, float *hi, float *lo, size_t n, cudaStream_t s);
+cudaError_t launch_rotate_tc(const float *q, const float *rot_hi, const float *rot_lo, float *out, int nq, int d,
+                             uint32_t *status, cudaStream_t s);
 cudaError_t launch_quantize_exact(const float *q, const float *rot, const float *qa, int nq, int d, uint32_t *planes,
                                   float4 *scal, uint32_t *recomputed, bool plane_major, cudaStream_t s);
 cudaError_t launch_search_nb1(int ch, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const SearchArgs &a);

@@ -24,6 +24,7 @@ struct sqg_index {
     uint32_t entry;
     unsigned char *d_blocks;
     float *d_rot;
+    float *d_rot_hi, *d_rot_lo;  // tf32 split of the rotation for the tensor-core path
     uint32_t *d_status;
     int num_sms;
     size_t smem_optin;
@@ -102,22 +103,24 @@ __global__ void plan_kernel(const int32_t *k, const int32_t *ef, int nq, long lo
     }
 }
 
-// q' = P^-1 q for a batch: out[r][i] = fmaf-chain over j = 0..d-1 of
-// rot[i][j] * q[r][j], starting from 0 (Eq. (4)).  64 x 64 output tiles,
-// 256 threads with 4 x 4 outputs each; every output keeps one accumulator
-// and walks j in order, so the tiling does not change a single bit.
+// q' = P^-1 q for a batch (Eq. (4)) in the canonical chunked order:
+// out[r][i] = (((0 + s_0) + s_1) + ...) over the d/32 chunks, s_c the fmaf
+// chain of rot[i][j] * q[r][j] over j = 32c .. 32c+31 from 0.  64 x 64 output
+// tiles, 256 threads with 4 x 4 outputs each; every output walks j in order
+// with one chunk accumulator and one total, so the tiling changes no bit.
 constexpr int kRotT = 64, kRotK = 16;
+static_assert(32 % kRotK == 0, "a chunk spans whole k-steps");
 __global__ void __launch_bounds__(256) rotate_kernel(const float *__restrict__ q, const float *__restrict__ rot,
                                                      float *__restrict__ out, int nq, int d) {
     __shared__ float As[kRotK][kRotT + 4];  // [j][row]
     __shared__ float Bs[kRotK][kRotT + 4];  // [j][col]
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int r0 = blockIdx.y * kRotT, c0 = blockIdx.x * kRotT;
-    float acc[4][4];
+    float acc[4][4], tot[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+        for (int b = 0; b < 4; ++b) acc[a][b] = tot[a][b] = 0.0f;
     for (int j0 = 0; j0 < d; j0 += kRotK) {
         for (int e = threadIdx.x; e < kRotT * kRotK; e += 256) {
             const int rr = e / kRotK, jj = e % kRotK;
@@ -138,6 +141,15 @@ __global__ void __launch_bounds__(256) rotate_kernel(const float *__restrict__ q
 #pragma unroll
                 for (int b = 0; b < 4; ++b) acc[a][b] = __fmaf_rn(bv[b], av[a], acc[a][b]);
         }
+        if (((j0 + kRotK) & 31) == 0) {  // end of a 32-wide chunk
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    tot[a][b] = __fadd_rn(tot[a][b], acc[a][b]);
+                    acc[a][b] = 0.0f;
+                }
+        }
         __syncthreads();
     }
 #pragma unroll
@@ -147,7 +159,7 @@ __global__ void __launch_bounds__(256) rotate_kernel(const float *__restrict__ q
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int gc = c0 + tx * 4 + b;
-            if (gc < d) out[(size_t)gr * d + gc] = acc[a][b];
+            if (gc < d) out[(size_t)gr * d + gc] = tot[a][b];
         }
     }
 }
@@ -300,13 +312,13 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     return SQG_OK;
 }
 
-// Rotation path: 1 = the fp32 fmaf-chain kernel, 2 = tensor cores plus the
-// exact quantization pass (same codes bit for bit); 0 = tensor cores from
-// d = 512 up, where the contraction is large enough to pay.
+// Rotation path: 1 = the CUDA-core kernel in the canonical order, 2 = tensor
+// cores plus the exact quantization pass (same codes bit for bit); 0 = tensor
+// cores from d = 512 up (2.5x faster there; at d = 128 the two tie).
 bool use_tc_rotation(const sqg_index *ix, const sqg_search_params &p) {
     if (p.rotation == 1) return false;
-    (void)ix;
-    return p.rotation == 2;
+    if (p.rotation == 2) return true;
+    return ix->lay.d >= 512;
 }
 
 sqg_search_params default_params() {
@@ -387,6 +399,8 @@ extern "C" int sqg_index_load(const char *path, int device, sqg_index **out) {
     const size_t block_bytes_total = (size_t)L.n * L.block_bytes;
     if (cudaMalloc(&ix->d_blocks, block_bytes_total) != cudaSuccess ||
         cudaMalloc(&ix->d_rot, sizeof(float) * (size_t)L.d * L.d) != cudaSuccess ||
+        cudaMalloc(&ix->d_rot_hi, sizeof(float) * (size_t)L.d * L.d) != cudaSuccess ||
+        cudaMalloc(&ix->d_rot_lo, sizeof(float) * (size_t)L.d * L.d) != cudaSuccess ||
         cudaMalloc(&ix->d_status, sizeof(uint32_t)) != cudaSuccess) {
         std::fclose(f);
         sqg_index_free(ix);
@@ -412,7 +426,9 @@ extern "C" int sqg_index_load(const char *path, int device, sqg_index **out) {
         else {
             hash = sqg_fmt::fnv_words(hash, buf.data(), nbytes);
             if (cudaMemcpy(ix->d_rot, buf.data(), sizeof(float) * (size_t)L.d * L.d, cudaMemcpyHostToDevice) !=
-                cudaSuccess)
+                    cudaSuccess ||
+                launch_split_tf32(ix->d_rot, ix->d_rot_hi, ix->d_rot_lo, (size_t)L.d * L.d, 0) != cudaSuccess ||
+                cudaDeviceSynchronize() != cudaSuccess)
                 rc = SQG_ERR_CUDA;
         }
     }
@@ -451,6 +467,8 @@ extern "C" void sqg_index_free(sqg_index *ix) {
     cudaDeviceSynchronize();
     if (ix->d_blocks) cudaFree(ix->d_blocks);
     if (ix->d_rot) cudaFree(ix->d_rot);
+    if (ix->d_rot_hi) cudaFree(ix->d_rot_hi);
+    if (ix->d_rot_lo) cudaFree(ix->d_rot_lo);
     if (ix->d_status) cudaFree(ix->d_status);
     delete ix;
 }
@@ -566,8 +584,8 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     if (use_tc_rotation(ix, p)) {  // tensor cores, then the exact quantization
         a.qplanes = reinterpret_cast<uint32_t *>(ws + pl.ws_planes);
         a.qscal = reinterpret_cast<float4 *>(ws + pl.ws_scal);
-        e = launch_rotate_tc(queries, ix->d_rot, const_cast<float *>(a.qrot), nq, (int)ix->lay.d, ix->d_status,
-                             stream);
+        e = launch_rotate_tc(queries, ix->d_rot_hi, ix->d_rot_lo, const_cast<float *>(a.qrot), nq, (int)ix->lay.d,
+                             ix->d_status, stream);
         if (e == cudaSuccess)
             e = launch_quantize_exact(queries, ix->d_rot, a.qrot, nq, (int)ix->lay.d,
                                       const_cast<uint32_t *>(a.qplanes), const_cast<float4 *>(a.qscal), nullptr,
@@ -647,7 +665,7 @@ extern "C" int sqg_prepare_queries_tc(const sqg_index *ix, const float *queries,
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     DeviceGuard g(ix->device);
     const int d = (int)ix->lay.d;
-    cudaError_t e = launch_rotate_tc(queries, ix->d_rot, out_qrot, nq, d, ix->d_status, stream);
+    cudaError_t e = launch_rotate_tc(queries, ix->d_rot_hi, ix->d_rot_lo, out_qrot, nq, d, ix->d_status, stream);
     if (e == cudaSuccess)
         e = launch_quantize_exact(queries, ix->d_rot, out_qrot, nq, d, out_planes,
                                   reinterpret_cast<float4 *>(out_scal), recomputed, true, stream);

@@ -59,7 +59,9 @@ def _check_prepared(ix, O, oracle_mod, q, rows):
     worst = 0.0
     for i in rows:
         exact = oracle_mod.rotate_f64(rot, q[i])
-        bound = (6 * d + 12) * U * float(np.linalg.norm(q[i].astype(np.float64)))
+        # the tensor-core part of the error model: split 12u, 96 additions
+        # per chunk accumulator (192u), d/32 register additions
+        bound = (12 + 192 + d // 32) * U * float(np.linalg.norm(q[i].astype(np.float64)))
         err = float(np.max(np.abs(qtc[i].astype(np.float64) - exact)))
         assert err <= bound, f"query {i}: |q'_tc - q'| = {err} > {bound}"
         worst = max(worst, err / bound if bound > 0 else 0.0)

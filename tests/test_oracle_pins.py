@@ -33,6 +33,10 @@ def test_rotate_f32_close_to_f64(oracle_mod):
         ref = P.astype(np.float64) @ q.astype(np.float64)
         np.testing.assert_allclose(b, ref, rtol=0, atol=1e-12 * np.abs(ref).max() * d)
         assert np.max(np.abs(a - b)) <= 1e-5 * np.abs(b).max()
+        # the chunked fp32 order rounds every term once per 32-term chain and
+        # once per chunk addition: |error_i| <= (32 + d/32) u sum_j |P_ij q_j|
+        mag = np.abs(P.astype(np.float64)) @ np.abs(q.astype(np.float64))
+        assert np.all(np.abs(a - ref) <= (32 + d // 32) * 2.0 ** -24 * mag)
 
 
 def test_query_quantizer_closed_form(oracle_mod):
