@@ -257,6 +257,12 @@ def learned_stop_comparison(args, w, ix, qd, gt_ids, sweep, ef_sel, device):
             "qps_ratio_vs_plain": round(best["qps"] / plain["qps"], 4) if best and plain else None}
 
 
+def launches_per_step(d: int) -> int:
+    """Library kernels per search call: plan, rotation (tensor cores plus the
+    exact quantization from d = 512 up, else one CUDA-core kernel), search."""
+    return 4 if d >= 512 else 3
+
+
 def bench_mixed(args, w, ix, qd, q, gt_ids, rank, world, dist, local):
     """A batch with per-query k and ef (the persistent work-queue form):
     autotune the launch knobs on the batch, then time it; recall per k."""
@@ -273,20 +279,24 @@ def bench_mixed(args, w, ix, qd, q, gt_ids, rank, world, dist, local):
     total = int(kq.sum())
     out = (torch.empty(total, dtype=torch.int32, device="cuda"), torch.empty(total, device="cuda"))
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    gs = autotune.GraphSearch(ix, nq, kq, efq, max_k=max_k, max_ef=max_ef, **knobs)
+    gs.q.copy_(qd)
     for _ in range(max(3, args.warmup)):
-        ix.search(qd, kt, et, out=out, max_k=max_k, max_ef=max_ef, **knobs)
+        gs()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = Clocks(local)
     torch.cuda.synchronize()
-    st = None
     for s in range(args.steps):
         flush.zero_()
         ev[s][0].record()
-        _, _, st = ix.search(qd, kt, et, out=out, stats=True, max_k=max_k, max_ef=max_ef, **knobs)
+        gs.graph.replay()
         ev[s][1].record()
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    _, _, st = ix.search(qd, kt, et, out=out, stats=True, max_k=max_k, max_ef=max_ef, **knobs)
+    if not torch.equal(out[0], gs.ids):
+        raise RuntimeError("graph replay and direct search disagree")
     ids = out[0].cpu().numpy()
     off = np.concatenate([[0], np.cumsum(kq)])
     rec = {}
@@ -302,12 +312,12 @@ def bench_mixed(args, w, ix, qd, q, gt_ids, rank, world, dist, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "n": w.n, "d": w.d, "degree": w.degree, "k": "U{1,10,100}",
                        "ef": "U[k, 8k]", "queries_per_step": nq, "recall_per_k": rec, "knobs": knobs,
-                       "l2": "flushed (512 MiB write) between timed steps"},
+                       "l2": "flushed (512 MiB write) between timed steps", "launch": "one CUDA graph per step"},
             "roofline": {"bound": "hbm", "achieved": round(alg / (ms / 1e3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4), "peak_source": src,
                          "note": "step time (plan + rotation + search), not the search kernel alone"},
             "autotune": sorted(tune["table"], key=lambda r: r["ms"])[:6], "clocks": clk,
-            "hops_mean": round(float(hops.mean()), 2), "gpu_launches": 3 * args.steps}
+            "hops_mean": round(float(hops.mean()), 2), "gpu_launches": launches_per_step(w.d) * args.steps}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -416,17 +426,14 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ef_sel = int(t.item())
 
-    # ---- timed steps
+    # ---- timed steps: the whole step (plan, rotation, search) as one CUDA graph
+    from paper_2411_12229_gb300.autotune import GraphSearch
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    out = (torch.empty(nq * k, dtype=torch.int32, device="cuda"), torch.empty(nq * k, device="cuda"))
-    st = None
+    gs = GraphSearch(ix, nq, k, ef_sel, max_k=k, max_ef=ef_sel)
+    gs.q.copy_(qd)
     for _ in range(max(3, args.warmup)):
-        ix.search(qd, k, ef_sel, out=out)
+        gs()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for a, b in kev:  # create the underlying CUDA events
-        a.record()
-        b.record()
     torch.cuda.synchronize()
     clocks = Clocks(local)
     if dist:
@@ -435,13 +442,27 @@ def main():
     for s in range(args.steps):
         flush.zero_()
         ev[s][0].record()
-        _, _, st = ix.search(qd, k, ef_sel, out=out, stats=True, timing_events=kev[s])
+        gs.graph.replay()
         ev[s][1].record()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    out = (gs.ids, gs.dists)
+    # ---- the search kernel alone: events around its launch, same steps, outside a graph
+    out2 = (torch.empty(nq * k, dtype=torch.int32, device="cuda"), torch.empty(nq * k, device="cuda"))
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in kev:  # create the underlying CUDA events
+        a.record()
+        b.record()
+    st = None
+    for s in range(args.steps):
+        flush.zero_()
+        _, _, st = ix.search(qd, k, ef_sel, out=out2, stats=True, timing_events=kev[s])
+    torch.cuda.synchronize()
     kern_ms = [a.elapsed_time(b) for a, b in kev]
+    if not torch.equal(out2[0], out[0]):
+        raise RuntimeError("graph replay and direct search disagree")
     # ---- end to end through host buffers
     qh = torch.from_numpy(q).pin_memory()
     ih = torch.empty((nq, k), dtype=torch.int32).pin_memory()
@@ -500,13 +521,13 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "d": w.d, "degree": w.degree, "k": k, "ef": ef_sel,
                    "queries_per_step": nq, "recall@10": round(rec_sel, 4), "parallelism": f"replicas{world}",
-                   "l2": "flushed (512 MiB write) between timed steps"},
+                   "l2": "flushed (512 MiB write) between timed steps", "launch": "one CUDA graph per step"},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(nq * w.d * 4),
                 "d2h_bytes_per_step": int(nq * k * 8),
                 "recall@10": round(rec_e2e, 4) if rec_e2e is not None else None},
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": launches_per_step(w.d) * args.steps,
         "clocks": clk,
         "qps_at_recall": {str(t): next((s["qps"] for s in sweep if s["recall"] >= t), None)
                           for t in (0.90, 0.95, 0.99)},

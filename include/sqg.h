@@ -178,6 +178,13 @@ int sqg_search_ex(const sqg_index *ix, const float *queries, int nq, const int32
                   uint32_t *out_ids, float *out_dists, const sqg_search_params *params, void *workspace,
                   size_t ws_bytes, sqg_query_stats *stats, sqg_stream_t stream);
 
+/* Device workspace bytes sqg_search_ex needs for nq queries with the given
+ * bounds and these parameters (NULL = defaults; their max_k/max_ef fields are
+ * ignored).  The tuning fields (warps_per_block, visited_smem_log2, lean) set
+ * how many warps run at once and so how much room the spilled visited sets
+ * take; 0 on invalid arguments.  Host call, no device work. */
+size_t sqg_workspace_size_ex(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_search_params *params);
+
 /* Query preparation alone (the first kernels of sqg_search), for tests:
  *   out_qrot   nq x d fp32: q' = P^-1 q (Eq. (4)) in the canonical order:
  *              per 32-column chunk c an fmaf chain over j = 32c..32c+31 from

@@ -55,6 +55,7 @@ _SIGS = {
     "sqg_index_free": (None, [P]),
     "sqg_index_info": (I32, [P, C.POINTER(Info)]),
     "sqg_workspace_size": (SZ, [P, I32, I32, I32]),
+    "sqg_workspace_size_ex": (SZ, [P, I32, I32, I32, P]),
     "sqg_search": (I32, [P, P, I32, P, P, P, P, P]),
     "sqg_search_ex": (I32, [P, P, I32, P, P, P, P, C.POINTER(SearchParams), P, SZ, P, P]),
     "sqg_search_trace": (I32, [P, P, I32, P, P, P, P, C.POINTER(SearchParams), P, P, I32, P, P, P, I32, P, I32,

@@ -158,8 +158,14 @@ class Index:
         out = (ids.view(nq, k), dists.view(nq, k), st, feats, hits, cnt)
         return out + (path,) if path_cap > 0 else out
 
-    def workspace_size(self, nq: int, max_k: int, max_ef: int) -> int:
-        n = B.lib().sqg_workspace_size(self._h, nq, max_k, max_ef)
+    def workspace_size(self, nq: int, max_k: int, max_ef: int, **kw) -> int:
+        """Workspace bytes for a batch; keyword arguments are search
+        parameters (the tuning knobs change the size)."""
+        if kw:
+            p = self.params(**{a: b for a, b in kw.items() if a not in ("max_k", "max_ef")})
+            n = B.lib().sqg_workspace_size_ex(self._h, nq, max_k, max_ef, C.byref(p))
+        else:
+            n = B.lib().sqg_workspace_size(self._h, nq, max_k, max_ef)
         if n == 0:
             raise B.SqgError(-1, "sqg_workspace_size")
         return int(n)

@@ -96,7 +96,7 @@ class GraphSearch:
         total = int(self.k.sum())
         self.ids = torch.empty(total, dtype=torch.int32, device=dev)
         self.dists = torch.empty(total, dtype=torch.float32, device=dev)
-        self.ws = torch.empty(ix.workspace_size(nq, max_k, max_ef), dtype=torch.uint8, device=dev)
+        self.ws = torch.empty(ix.workspace_size(nq, max_k, max_ef, **kw), dtype=torch.uint8, device=dev)
         self.kw = dict(max_k=max_k, max_ef=max_ef, **kw)
         s = torch.cuda.Stream(device=dev)
         s.wait_stream(torch.cuda.current_stream(dev))

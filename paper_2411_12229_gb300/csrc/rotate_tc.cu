@@ -5,8 +5,8 @@
 // compute) is chunked: q'_i = (((0 + s_0) + s_1) + ... ) over the d/32
 // chunks, s_c an fmaf chain over j = 32c .. 32c+31 started from 0.
 //
-// rotate_tc_kernel: one CTA computes a 128-query x 128-output tile as
-// D = A B^T with A = the queries and B = the rows of P^-1, both K-major,
+// rotate_tc_kernel: persistent, one CTA per SM, walking 128-query x 128-output
+// tiles D = A B^T with A = the queries and B = the rows of P^-1, both K-major,
 // with tcgen05.mma kind::tf32.  fp32 accuracy comes from the 3xTF32 split
 // a.b ~ hi(a)hi(b) + hi(a)lo(b) + lo(a)hi(b), hi = tf32(x), lo = tf32(x - hi).
 // Warp roles:
@@ -24,9 +24,9 @@
 // v_l and Delta being exactly those of the canonical rotation.  The
 // tensor-core q' differs from it by at most err = c(d) * ||q||, so every
 // coordinate whose code or whose role as min/max could change within err is
-// recomputed in the canonical order (one warp per coordinate, chunks on the
-// lanes); the rest are decided from q'.  The result is bit-identical to
-// quantizing the canonical rotation.
+// recomputed in the canonical order (one lane per coordinate); the rest are
+// decided from q'.  The result is bit-identical to quantizing the canonical
+// rotation.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -168,8 +168,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ int abort_flag;
     volatile int *abort_v = &abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int c0 = blockIdx.x * BN, r0 = blockIdx.y * BM;  // column tiles vary fastest: query tile shared in L2
     const int nchunk = d / BK;
+    // persistent: this CTA takes tiles blockIdx.x, + gridDim.x, ...; column
+    // tiles vary fastest, so CTAs running together share query tiles in L2
+    const int ncol_tiles = (d + BN - 1) / BN;
+    const int ntiles = ncol_tiles * ((nq + BM - 1) / BM);
+    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int total = my_tiles * nchunk;  // chunks this CTA streams, across its tiles
+    auto tile_of = [&](int g, int &r0, int &c0) {
+        const int t = (int)blockIdx.x + (g / nchunk) * (int)gridDim.x;
+        r0 = (t / ncol_tiles) * BM;
+        c0 = (t % ncol_tiles) * BN;
+    };
 
     if (warp == 0) {  // two 128-column fp32 accumulators in tensor memory
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
@@ -201,8 +211,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            for (int k = 0; k < nchunk; ++k) {
-                const int s = k % kStages, n = k / kStages;
+            for (int g = 0; g < total; ++g) {
+                const int s = g % kStages, n = g / kStages, k = g % nchunk;
+                int r0, c0;
+                tile_of(g, r0, c0);
                 if (n >= 1 && !bar_wait(saddr(&empty_bar[s]), (uint32_t)((n - 1) & 1), abort_v)) break;
                 bar_arrive_tx(saddr(&full_bar[s]), 3 * kTile);
                 tma_load_2d(tile(s, 0), &qmap, k * BK, r0, saddr(&full_bar[s]));
@@ -212,8 +224,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            for (int k = 0; k < nchunk; ++k) {
-                const int s = k % kStages, n = k / kStages, t = k & 1, m = k >> 1;
+            for (int g = 0; g < total; ++g) {
+                const int s = g % kStages, n = g / kStages, t = g & 1, m = g >> 1;
                 if (!bar_wait(saddr(&full_bar[s]), (uint32_t)(n & 1), abort_v)) break;
                 if (!bar_wait(saddr(&conv_bar[s]), (uint32_t)(n & 1), abort_v)) break;
                 if (m >= 1 && !bar_wait(saddr(&tempty_bar[t]), (uint32_t)((m - 1) & 1), abort_v)) break;
@@ -241,8 +253,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp < kDrainWarp0) {
         const int ct = tid - kConvWarp0 * 32;
-        for (int k = 0; k < nchunk; ++k) {
-            const int s = k % kStages, n = k / kStages;
+        for (int g = 0; g < total; ++g) {
+            const int s = g % kStages, n = g / kStages;
             if (!bar_wait(saddr(&full_bar[s]), (uint32_t)(n & 1), abort_v)) break;
             float4 *raw = reinterpret_cast<float4 *>(sm + s * kStageBytes);
             float4 *lo = reinterpret_cast<float4 *>(sm + s * kStageBytes + kTile);
@@ -264,15 +276,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31 = tile rows
         float acc[BN];
+        for (int g = 0; g < total; ++g) {
+            const int t = g & 1, m = g >> 1, k = g % nchunk;
+            if (k == 0) {
 #pragma unroll
-        for (int j = 0; j < BN; ++j) acc[j] = 0.0f;
-        bool ok = true;
-        for (int k = 0; k < nchunk; ++k) {
-            const int t = k & 1, m = k >> 1;
-            if (!bar_wait(saddr(&tfull_bar[t]), (uint32_t)(m & 1), abort_v)) {
-                ok = false;
-                break;
+                for (int j = 0; j < BN; ++j) acc[j] = 0.0f;
             }
+            if (!bar_wait(saddr(&tfull_bar[t]), (uint32_t)(m & 1), abort_v)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int cc = 0; cc < BN / 32; ++cc) {
@@ -284,14 +294,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) bar_arrive(saddr(&tempty_bar[t]));
-        }
-        const int row = r0 + quarter * 32 + lane;
-        if (ok && !*abort_v && row < nq) {
-            float4 *o = reinterpret_cast<float4 *>(out + (size_t)row * d + c0);
-            const int ncol = d - c0 < BN ? d - c0 : BN;  // a multiple of 32
+            if (k == nchunk - 1) {  // the tile is complete: write its rows
+                int r0, c0;
+                tile_of(g, r0, c0);
+                const int row = r0 + quarter * 32 + lane;
+                if (row < nq) {
+                    float4 *o = reinterpret_cast<float4 *>(out + (size_t)row * d + c0);
+                    const int ncol = d - c0 < BN ? d - c0 : BN;  // a multiple of 32
 #pragma unroll
-            for (int j = 0; j < BN / 4; ++j)
-                if (4 * j < ncol) o[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+                    for (int j = 0; j < BN / 4; ++j)
+                        if (4 * j < ncol)
+                            o[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+                }
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -313,16 +328,14 @@ __global__ void split_tf32_kernel(const float *__restrict__ x, float *__restrict
     }
 }
 
-// The canonical rotated coordinate of one row, computed by a whole warp:
-// lane c (and c + 32) runs the chunk chain s_c, then every lane adds the
-// chunk sums in order c = 0, 1, ...; all lanes return the same value.
-__device__ __forceinline__ float chunk_chain(const float *__restrict__ row, const float *__restrict__ q) {
-    const float4 *r4 = reinterpret_cast<const float4 *>(row);
-    const float4 *q4 = reinterpret_cast<const float4 *>(q);
+// The canonical rotated coordinate of one row, by one thread: chunk chains
+// s_c (32 fmaf from 0) four at a time for instruction-level parallelism,
+// their sums added to the total in order c = 0, 1, ...
+__device__ __forceinline__ float chunk_chain(const float4 *__restrict__ r4, const float4 *__restrict__ q4) {
     float s = 0.0f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const float4 r = r4[j], v = q4[j];
+        const float4 r = __ldg(r4 + j), v = q4[j];
         s = __fmaf_rn(r.x, v.x, s);
         s = __fmaf_rn(r.y, v.y, s);
         s = __fmaf_rn(r.z, v.z, s);
@@ -331,75 +344,120 @@ __device__ __forceinline__ float chunk_chain(const float *__restrict__ row, cons
     return s;
 }
 
-__device__ __forceinline__ float warp_canonical(const float *__restrict__ row, const float *__restrict__ q, int d,
-                                                int lane) {
+__device__ float canonical_coord(const float *__restrict__ row, const float *q, int d) {
+    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+    const float4 *q4 = reinterpret_cast<const float4 *>(q);
     const int nc = d / 32;
-    const float s0 = lane < nc ? chunk_chain(row + 32 * lane, q + 32 * lane) : 0.0f;
-    const float s1 = lane + 32 < nc ? chunk_chain(row + 32 * (lane + 32), q + 32 * (lane + 32)) : 0.0f;
     float tot = 0.0f;
-    for (int c = 0; c < nc; ++c) tot = __fadd_rn(tot, __shfl_sync(0xFFFFFFFFu, c < 32 ? s0 : s1, c & 31));
+    int c = 0;
+    for (; c + 4 <= nc; c += 4) {
+        float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float4 r = __ldg(r4 + 8 * (c + t) + j), v = q4[8 * (c + t) + j];
+                s[t] = __fmaf_rn(r.x, v.x, s[t]);
+                s[t] = __fmaf_rn(r.y, v.y, s[t]);
+                s[t] = __fmaf_rn(r.z, v.z, s[t]);
+                s[t] = __fmaf_rn(r.w, v.w, s[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) tot = __fadd_rn(tot, s[t]);
+    }
+    for (; c < nc; ++c) tot = __fadd_rn(tot, chunk_chain(r4 + 8 * c, q4 + 8 * c));
     return tot;
 }
 
-constexpr int kMaxWords = 64;  // d <= 2048
+constexpr int kMaxD = 2048;
+constexpr int kQxWarps = 4;
+
+// Per-warp shared memory of the exact pass: the query, its rotated
+// coordinates, the list of coordinates to recompute and their exact flags.
+struct QxLayout {
+    size_t q, x, list, exact, warp;
+    __host__ __device__ explicit QxLayout(int d) {
+        q = 0;
+        x = q + 4 * (size_t)d;
+        list = x + 4 * (size_t)d;
+        exact = list + 2 * (size_t)d;
+        warp = (exact + 4 * (size_t)(d / 32) + 15) & ~(size_t)15;
+    }
+};
+
+// Recompute the listed coordinates, one per lane, and mark them exact.
+__device__ __forceinline__ void recompute_listed(const float *__restrict__ rot, const float *qs, float *xs,
+                                                 const uint16_t *list, uint32_t *ex, int n, int d, int lane) {
+    for (int r = lane; r < n; r += 32) {
+        const int i = list[r];
+        xs[i] = canonical_coord(rot + (size_t)i * d, qs, d);
+        atomicOr(&ex[i >> 5], 1u << (i & 31));
+    }
+    __syncwarp();
+}
 
 // One warp per query.  qa = the tensor-core q'; err_scale * ||q|| bounds
 // |qa_i - canonical_i| for every i.  Writes planes (per word w the four
 // planes b as one uint4 -- [w][b] -- or, with plane_major, [b][w]) and
 // (v_l, delta, Sq, 1/sqrt(d)) exactly as the canonical rotation would give.
-__global__ void quantize_exact_kernel(const float *__restrict__ q, const float *__restrict__ rot,
-                                      const float *__restrict__ qa, int nq, int d, float err_scale,
-                                      uint32_t *__restrict__ planes, float4 *__restrict__ scal,
-                                      uint32_t *__restrict__ recomputed, int plane_major) {
-    const int lane = threadIdx.x & 31;
-    const int qi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+__global__ void __launch_bounds__(kQxWarps * 32)
+    quantize_exact_kernel(const float *__restrict__ q, const float *__restrict__ rot, const float *__restrict__ qa,
+                          int nq, int d, float err_scale, uint32_t *__restrict__ planes, float4 *__restrict__ scal,
+                          uint32_t *__restrict__ recomputed, int plane_major) {
+    extern __shared__ __align__(16) unsigned char qxsm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int qi = blockIdx.x * kQxWarps + wib;
     if (qi >= nq) return;
+    const QxLayout L(d);
+    unsigned char *base = qxsm + wib * L.warp;
+    float *qs = reinterpret_cast<float *>(base + L.q);
+    float *xs = reinterpret_cast<float *>(base + L.x);
+    uint16_t *list = reinterpret_cast<uint16_t *>(base + L.list);
+    uint32_t *ex = reinterpret_cast<uint32_t *>(base + L.exact);
     const int nw = d / 32;
     const float *qq = q + (size_t)qi * d;
     const float *qr = qa + (size_t)qi * d;
-    float x[kMaxWords];
-    uint64_t exact = 0;  // bit w: x[w] is canonical
-    float ss = 0.0f;
+    float ss = 0.0f, lo = __int_as_float(0x7f800000), hi = -lo;
     for (int w = 0; w < nw; ++w) {
-        x[w] = qr[w * 32 + lane];
-        const float v = qq[w * 32 + lane];
+        const int i = w * 32 + lane;
+        const float v = qq[i], x = qr[i];
+        qs[i] = v;
+        xs[i] = x;
         ss = fmaf(v, v, ss);
+        lo = fminf(lo, x);
+        hi = fmaxf(hi, x);
     }
-    for (int o = 16; o >= 1; o >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
-    const float err = err_scale * sqrtf(ss) + 1e-30f;
-    int nrec = 0;
-    // candidates for the minimum and the maximum (within 2 err of the
-    // tensor-core extremes): recompute them
-    float lo = x[0], hi = x[0];
-    for (int w = 1; w < nw; ++w) {
-        lo = fminf(lo, x[w]);
-        hi = fmaxf(hi, x[w]);
-    }
+    for (int w = lane; w < nw; w += 32) ex[w] = 0u;
     for (int o = 16; o >= 1; o >>= 1) {
+        ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
         lo = fminf(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
         hi = fmaxf(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
     }
+    const float err = err_scale * sqrtf(ss) + 1e-30f;
+    // candidates for the minimum and the maximum (within 2 err of the
+    // tensor-core extremes): recompute them
+    int n = 0;
     for (int w = 0; w < nw; ++w) {
-        uint32_t m = __ballot_sync(0xFFFFFFFFu, x[w] <= lo + 2.0f * err || x[w] >= hi - 2.0f * err);
-        while (m) {
-            const int l = __ffs(m) - 1;
-            m &= m - 1;
-            const float v = warp_canonical(rot + (size_t)(w * 32 + l) * d, qq, d, lane);
-            if (lane == l) {
-                x[w] = v;
-                exact |= 1ull << w;
-                ++nrec;
-            }
+        const int i = w * 32 + lane;
+        const bool f = xs[i] <= lo + 2.0f * err || xs[i] >= hi - 2.0f * err;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, f);
+        if (f) list[n + __popc(m & ((1u << lane) - 1u))] = (uint16_t)i;
+        n += __popc(m);
+    }
+    __syncwarp();
+    recompute_listed(rot, qs, xs, list, ex, n, d, lane);
+    int nrec = n;
+    // exact v_l, v_r over the recomputed candidates: the same comparisons
+    // as the canonical quantizer
+    float vl = __int_as_float(0x7f800000), vr = -vl;
+    for (int w = 0; w < nw; ++w) {
+        const int i = w * 32 + lane;
+        if (ex[w] >> lane & 1u) {
+            vl = xs[i] < vl ? xs[i] : vl;
+            vr = xs[i] > vr ? xs[i] : vr;
         }
     }
-    // exact v_l, v_r: the same comparisons as the canonical quantizer
-    const float inf = __int_as_float(0x7f800000);
-    float vl = inf, vr = -inf;
-    for (int w = 0; w < nw; ++w)
-        if (exact >> w & 1ull) {
-            vl = x[w] < vl ? x[w] : vl;
-            vr = x[w] > vr ? x[w] : vr;
-        }
     for (int o = 16; o >= 1; o >>= 1) {
         const float a = __shfl_xor_sync(0xFFFFFFFFu, vl, o), b = __shfl_xor_sync(0xFFFFFFFFu, vr, o);
         vl = a < vl ? a : vl;
@@ -409,29 +467,27 @@ __global__ void quantize_exact_kernel(const float *__restrict__ q, const float *
     const float delta = range > 0.0f ? __fdiv_rn(range, 15.0f) : 0.0f;
     const float inv = range > 0.0f ? __fdiv_rn(15.0f, range) : 0.0f;
     const float margin = err * inv * 1.01f + 1e-4f;  // in units of the code
+    // coordinates within the margin of an integer boundary (1 .. 15)
+    n = 0;
+    if (range > 0.0f) {
+        for (int w = 0; w < nw; ++w) {
+            const int i = w * 32 + lane;
+            const float y = __fadd_rn(__fmul_rn(__fsub_rn(xs[i], vl), inv), 0.5f);
+            const float nearest = fminf(fmaxf(rintf(y), 1.0f), 15.0f);
+            const bool f = !(ex[w] >> lane & 1u) && fabsf(y - nearest) <= margin;
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, f);
+            if (f) list[n + __popc(m & ((1u << lane) - 1u))] = (uint16_t)i;
+            n += __popc(m);
+        }
+        __syncwarp();
+        recompute_listed(rot, qs, xs, list, ex, n, d, lane);
+        nrec += n;
+    }
     int sq = 0;
     for (int w = 0; w < nw; ++w) {
-        float y = 0.0f;
-        bool redo = false;
-        if (range > 0.0f) {
-            y = __fadd_rn(__fmul_rn(__fsub_rn(x[w], vl), inv), 0.5f);
-            // an integer boundary (1 .. 15) within the margin: decide exactly
-            const float nearest = fminf(fmaxf(rintf(y), 1.0f), 15.0f);
-            redo = !(exact >> w & 1ull) && fabsf(y - nearest) <= margin;
-        }
-        uint32_t m = __ballot_sync(0xFFFFFFFFu, redo);
-        while (m) {
-            const int l = __ffs(m) - 1;
-            m &= m - 1;
-            const float v = warp_canonical(rot + (size_t)(w * 32 + l) * d, qq, d, lane);
-            if (lane == l) {
-                x[w] = v;
-                ++nrec;
-                y = __fadd_rn(__fmul_rn(__fsub_rn(v, vl), inv), 0.5f);
-            }
-        }
         int t = 0;
         if (range > 0.0f) {
+            const float y = __fadd_rn(__fmul_rn(__fsub_rn(xs[w * 32 + lane], vl), inv), 0.5f);
             t = __float2int_rz(y);
             t = t > 15 ? 15 : t;
         }
@@ -451,7 +507,6 @@ __global__ void quantize_exact_kernel(const float *__restrict__ q, const float *
         }
     }
     sq = __reduce_add_sync(0xFFFFFFFFu, sq);
-    nrec = __reduce_add_sync(0xFFFFFFFFu, nrec);
     if (lane == 0) {
         scal[qi] = make_float4(vl, delta, (float)sq, __fdiv_rn(1.0f, __fsqrt_rn((float)d)));
         if (recomputed) atomicAdd(recomputed, (uint32_t)nrec);
@@ -526,18 +581,25 @@ cudaError_t launch_rotate_tc(const float *q, const float *rot_hi, const float *r
         return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(rotate_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
-    dim3 grid((d + BN - 1) / BN, (nq + BM - 1) / BM);
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    const long long tiles = (long long)((d + BN - 1) / BN) * ((nq + BM - 1) / BM);
+    const int grid = (int)(tiles < sms ? tiles : sms);  // one persistent CTA per SM
     rotate_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(qm, hm, lm, out, nq, d, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_quantize_exact(const float *q, const float *rot, const float *qa, int nq, int d, uint32_t *planes,
                                   float4 *scal, uint32_t *recomputed, bool plane_major, cudaStream_t s) {
-    if (d / 32 > kMaxWords) return cudaErrorInvalidValue;
+    if (d > kMaxD || d % 32 != 0) return cudaErrorInvalidValue;
     if (nq <= 0) return cudaSuccess;
-    const int wpb = 4;
-    quantize_exact_kernel<<<(nq + wpb - 1) / wpb, wpb * 32, 0, s>>>(q, rot, qa, nq, d, rotate_tc_err_scale(d),
-                                                                   planes, scal, recomputed, plane_major ? 1 : 0);
+    const size_t smem = kQxWarps * QxLayout(d).warp;
+    cudaError_t e = cudaFuncSetAttribute(quantize_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    quantize_exact_kernel<<<(nq + kQxWarps - 1) / kQxWarps, kQxWarps * 32, smem, s>>>(
+        q, rot, qa, nq, d, rotate_tc_err_scale(d), planes, scal, recomputed, plane_major ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -501,6 +501,18 @@ extern "C" size_t sqg_workspace_size(const sqg_index *ix, int nq, int max_k, int
     return need;
 }
 
+extern "C" size_t sqg_workspace_size_ex(const sqg_index *ix, int nq, int max_k, int max_ef,
+                                        const sqg_search_params *params) {
+    if (!ix || nq < 0 || max_k < 1 || max_k > SQG_MAX_K || max_ef < max_k || max_ef > SQG_MAX_EF) return 0;
+    sqg_search_params p = params ? *params : default_params();
+    if (params && p.stop_every == 0) p.stop_every = 1;
+    if (check_params(p) != SQG_OK) return 0;
+    DeviceGuard g(ix->device);
+    LaunchPlan pl;
+    if (make_plan(ix, nq, max_k, max_ef, p, pl) != SQG_OK) return 0;
+    return pl.ws_total;
+}
+
 static int search_impl(const sqg_index *ix, const float *queries, int nq, const int32_t *k, const int32_t *ef,
                        uint32_t *out_ids, float *out_dists, const sqg_search_params *params, void *workspace,
                        size_t ws_bytes, sqg_query_stats *stats, cudaStream_t stream, float *trace_feat,

@@ -136,3 +136,19 @@ def test_tc_search_parity(gpu_tiny, oracle_mod, ef):
 def test_tc_search_parity_other_shapes(shaped, oracle_mod):
     ix, p, x, q = shaped
     _search_equal(ix, oracle_mod.Index(p), q, 10, 40)
+
+
+def test_tc_rotation_in_cuda_graph_with_knobs(shaped, oracle_mod):
+    """The tensor-core rotation captured in a CUDA graph together with the
+    search, under tuning knobs that change the workspace size: the replay
+    gives the direct search's results."""
+    from paper_2411_12229_gb300.autotune import GraphSearch
+    ix, p, x, q = shaped
+    qd = torch.from_numpy(q).cuda()
+    knobs = dict(visited_smem_log2=5, warps_per_block=2, rotation=2)
+    gs = GraphSearch(ix, q.shape[0], 10, 40, max_k=10, max_ef=40, **knobs)
+    ids, dists = gs(qd)
+    ref_ids, ref_d = ix.search(qd, 10, 40, rotation=1)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(_np(ids).reshape(-1, 10), _np(ref_ids))
+    np.testing.assert_array_equal(_np(dists).reshape(-1, 10), _np(ref_d))
