@@ -87,7 +87,9 @@ typedef struct {
     const float *stop_mlp;   /* device, SQG_MLP_NPARAM floats, or NULL: learned stop off */
     float stop_logit;        /* stop when the MLP's logit exceeds this */
     int32_t stop_every;      /* evaluate the stop every this many expansions (>= 1) */
-    int32_t team;            /* lanes per query: 32 (default, 0) or 16 */
+    int32_t team;            /* lanes per query: 32 (default, 0), 16 or 8 -- a warp then
+                                runs 2 or 4 queries side by side; 16 and 8 need d <= 256
+                                and no stop_mlp / trace (else SQG_ERR_UNSUPPORTED) */
     int32_t warps_per_block; /* 0 = library default */
     void *timing_events[2];  /* optional cudaEvent_t pair recorded on the stream right before
                                 and right after the search kernel; NULL = none */

@@ -7,6 +7,8 @@ Knobs, all result-neutral (the search is bit-identical under each):
   visited_smem_log2  shared-memory slots of the visited set (2^9, 2^10)
   lean               1: the 64-register build (d <= 256, more resident
                      warps); 2: the 96-register build
+  team               lanes per query: 32, or 16 / 8 with 2 / 4 queries per
+                     warp (d <= 256; always the 96-register build)
 The tuner times every combination on the caller's own batch (CUDA events,
 median of `reps`) and keeps the fastest per (GPU, d, R, ef bucket) in a
 JSON cache, which ``tuned`` then returns.
@@ -26,8 +28,21 @@ import pathlib
 import numpy as np
 import torch
 
-KNOBS = {"warps_per_block": (1, 2, 4), "prefetch": (1, 2), "visited_smem_log2": (9, 10), "lean": (1, 2)}
-DEFAULT = {"warps_per_block": 4, "prefetch": 1, "visited_smem_log2": 0, "lean": 0}
+KNOBS = {"warps_per_block": (1, 2, 4), "prefetch": (1, 2), "visited_smem_log2": (9, 10), "lean": (1, 2),
+         "team": (32, 16, 8)}
+DEFAULT = {"warps_per_block": 4, "prefetch": 1, "visited_smem_log2": 0, "lean": 0, "team": 0}
+
+
+def combos(ix, knobs=None):
+    """The knob combinations that apply to this index (teams below 32 lanes
+    only for d <= 256, where the register build is fixed)."""
+    knobs = knobs or KNOBS
+    names = list(knobs)
+    for combo in itertools.product(*(knobs[n] for n in names)):
+        cfg = dict(zip(names, combo))
+        if cfg.get("team", 32) < 32 and (ix.d > 256 or cfg.get("lean", 2) == 1):
+            continue
+        yield cfg
 
 
 def cache_path() -> pathlib.Path:
@@ -58,8 +73,7 @@ def autotune(ix, queries: torch.Tensor, k, ef, *, reps: int = 5, save: bool = Tr
     names = list(knobs)
     table = []
     efmax = int(ef) if np.ndim(ef) == 0 else int(torch.as_tensor(ef).max())
-    for combo in itertools.product(*(knobs[n] for n in names)):
-        cfg = dict(zip(names, combo))
+    for cfg in combos(ix, knobs):
         ms = _time(ix, queries, k, ef, reps, **cfg)
         table.append({**cfg, "ms": round(ms, 4), "qps": round(queries.shape[0] / (ms / 1e3))})
     best = min(table, key=lambda r: r["ms"])

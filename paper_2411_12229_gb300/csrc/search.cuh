@@ -153,20 +153,56 @@ __device__ __forceinline__ void hash_insert(uint32_t *H, uint32_t bits, uint32_t
         s = (s + 1) & mask;
     }
 }
-// Warp: move every id of the shared table `S` into the cleared global table
+// ---------------------------------------------------------------- teams
+// A team of T lanes (T = 32, 16 or 8) serves one query; a warp holds 32/T
+// teams that run side by side.  Every collective below is scoped to the
+// team: ballots return the team's T bits, shuffles address lanes within it.
+template <int T>
+struct Team {
+    static_assert(T == 32 || T == 16 || T == 8, "team of 32, 16 or 8 lanes");
+    static constexpr int V = 32 / T;  // lanes of the canonical 32-lane order each lane stands for
+    uint32_t mask;  // the team's lanes in the warp
+    int tl;         // lane within the team
+    int base;       // the team's first lane
+    __device__ __forceinline__ explicit Team(int lane) {
+        tl = lane & (T - 1);
+        base = lane & ~(T - 1);
+        if constexpr (T == 32) mask = kFull;
+        else mask = ((1u << T) - 1u) << base;
+    }
+    __device__ __forceinline__ uint32_t ballot(bool p) const {
+        const uint32_t b = __ballot_sync(mask, p);
+        if constexpr (T == 32) return b;
+        else return (b >> base) & ((1u << T) - 1u);
+    }
+    template <class X>
+    __device__ __forceinline__ X shfl(X v, int src) const {
+        return __shfl_sync(mask, v, src, T);
+    }
+    template <class X>
+    __device__ __forceinline__ X shfl_xor(X v, int o) const {
+        return __shfl_xor_sync(mask, v, o, T);
+    }
+    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+    __device__ __forceinline__ int reduce_min(int v) const { return __reduce_min_sync(mask, v); }
+    __device__ __forceinline__ int reduce_add(int v) const { return __reduce_add_sync(mask, v); }
+};
+
+// Team: move every id of the shared table `S` into the cleared global table
 // `G` (concurrent inserts by compare-and-swap).
+template <int T>
 __device__ __forceinline__ void hash_migrate(const uint32_t *S, uint32_t sbits, uint32_t *G, uint32_t gbits,
-                                             int lane) {
+                                             const Team<T> &tm) {
     const uint32_t gsize = 1u << gbits, gmask = gsize - 1u;
-    for (uint32_t i = lane; i < gsize; i += 32) G[i] = kEmpty;
-    __syncwarp();
-    for (uint32_t i = lane; i < (1u << sbits); i += 32) {
+    for (uint32_t i = tm.tl; i < gsize; i += T) G[i] = kEmpty;
+    tm.sync();
+    for (uint32_t i = tm.tl; i < (1u << sbits); i += T) {
         const uint32_t id = S[i];
         if (id == kEmpty) continue;
         uint32_t s = hslot(id, gbits);
         while (atomicCAS(&G[s], kEmpty, id) != kEmpty) s = (s + 1) & gmask;
     }
-    __syncwarp();
+    tm.sync();
 }
 __device__ __forceinline__ bool hash_contains(const uint32_t *H, uint32_t bits, uint32_t id) {
     const uint32_t mask = (1u << bits) - 1u;
@@ -187,17 +223,24 @@ struct QuerySide {
     float vl, delta, inv_sqrt_d;
     int sq;
 };
-__device__ __forceinline__ QuerySide quantize_warp(const float *qr, uint32_t d, uint32_t *planes, int lane) {
+// Team T: coordinate 32w + tl + T v belongs to lane tl (v < 32/T); the
+// planes' word w is assembled from the 32/T team ballots.
+template <int T>
+__device__ __forceinline__ QuerySide quantize_team(const float *qr, uint32_t d, uint32_t *planes, const Team<T> &tm) {
+    constexpr int V = Team<T>::V;
     const uint32_t nw = d / 32;
-    float vl = qr[lane], vr = qr[lane];
-    for (uint32_t w = 1; w < nw; ++w) {
-        float x = qr[w * 32 + lane];
-        vl = x < vl ? x : vl;
-        vr = x > vr ? x : vr;
+    float vl = __int_as_float(0x7f800000), vr = -vl;
+    for (uint32_t w = 0; w < nw; ++w) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float x = qr[w * 32 + tm.tl + T * v];
+            vl = x < vl ? x : vl;
+            vr = x > vr ? x : vr;
+        }
     }
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        float a = __shfl_xor_sync(kFull, vl, o), b = __shfl_xor_sync(kFull, vr, o);
+    for (int o = T / 2; o >= 1; o >>= 1) {
+        const float a = tm.shfl_xor(vl, o), b = tm.shfl_xor(vr, o);
         vl = a < vl ? a : vl;
         vr = b > vr ? b : vr;
     }
@@ -209,48 +252,82 @@ __device__ __forceinline__ QuerySide quantize_warp(const float *qr, uint32_t d, 
     qs.inv_sqrt_d = __fdiv_rn(1.0f, __fsqrt_rn((float)d));
     int sq = 0;
     for (uint32_t w = 0; w < nw; ++w) {
-        int t = 0;
-        if (range > 0.0f) {
-            float x = __fsub_rn(qr[w * 32 + lane], vl);
-            x = __fmul_rn(x, inv);
-            x = __fadd_rn(x, 0.5f);
-            t = __float2int_rz(x);
-            t = t > 15 ? 15 : t;
+        uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            int t = 0;
+            if (range > 0.0f) {
+                float x = __fsub_rn(qr[w * 32 + tm.tl + T * v], vl);
+                x = __fmul_rn(x, inv);
+                x = __fadd_rn(x, 0.5f);
+                t = __float2int_rz(x);
+                t = t > 15 ? 15 : t;
+            }
+            sq += t;
+            b0 |= tm.ballot(t & 1) << (T * v);
+            b1 |= tm.ballot(t & 2) << (T * v);
+            b2 |= tm.ballot(t & 4) << (T * v);
+            b3 |= tm.ballot(t & 8) << (T * v);
         }
-        sq += t;
-        uint32_t b0 = __ballot_sync(kFull, t & 1), b1 = __ballot_sync(kFull, t & 2);
-        uint32_t b2 = __ballot_sync(kFull, t & 4), b3 = __ballot_sync(kFull, t & 8);
-        if (lane == 0) {
+        if (tm.tl == 0) {
             // word-major: the 4 planes of word w share one 16-byte slot
             reinterpret_cast<uint4 *>(planes)[w] = make_uint4(b0, b1, b2, b3);
         }
     }
-    qs.sq = __reduce_add_sync(kFull, sq);
+    qs.sq = tm.reduce_add(sq);
     return qs;
 }
+__device__ __forceinline__ QuerySide quantize_warp(const float *qr, uint32_t d, uint32_t *planes, int lane) {
+    return quantize_team<32>(qr, d, planes, Team<32>(lane));
+}
 
-// Exact squared distance in the canonical order: lane l sums float4 chunks
-// l, l+32, ... (x, y, z, w; fmaf(d, d, acc) from 0), then an xor butterfly.
-template <int CH>
-__device__ __forceinline__ float exact_dist(const float4 (&qv)[CH], const float *raw, uint32_t nch, int lane) {
-    float acc = 0.0f;
+// Exact squared distance in the canonical order: lane l of 32 sums float4
+// chunks l, l+32, ... (x, y, z, w; fmaf(d, d, acc) from 0), then an xor
+// butterfly adds partials l and l^16, ^8, ^4, ^2, ^1.  A team of T lanes
+// keeps the 32/T partials of lanes tl + T v in registers: butterfly steps of
+// at least T combine registers, the smaller ones shuffle, and every step
+// adds the same two partials as the 32-lane order, so the result is equal.
+template <int CH, int T>
+__device__ __forceinline__ float exact_dist_team(const float4 (&qv)[32 / T][CH], const float *raw, uint32_t nch,
+                                                 const Team<T> &tm) {
+    constexpr int V = 32 / T;
+    float acc[V];
     const float4 *r4 = reinterpret_cast<const float4 *>(raw);
 #pragma unroll
-    for (int t = 0; t < CH; ++t) {
-        uint32_t c = lane + 32 * t;
-        if (c < nch) {
-            float4 x = r4[c];
-            float dx = __fsub_rn(qv[t].x, x.x), dy = __fsub_rn(qv[t].y, x.y);
-            float dz = __fsub_rn(qv[t].z, x.z), dw = __fsub_rn(qv[t].w, x.w);
-            acc = __fmaf_rn(dx, dx, acc);
-            acc = __fmaf_rn(dy, dy, acc);
-            acc = __fmaf_rn(dz, dz, acc);
-            acc = __fmaf_rn(dw, dw, acc);
+    for (int v = 0; v < V; ++v) {
+        acc[v] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < CH; ++t) {
+            const uint32_t c = tm.tl + T * v + 32 * t;
+            if (c < nch) {
+                const float4 x = r4[c];
+                const float dx = __fsub_rn(qv[v][t].x, x.x), dy = __fsub_rn(qv[v][t].y, x.y);
+                const float dz = __fsub_rn(qv[v][t].z, x.z), dw = __fsub_rn(qv[v][t].w, x.w);
+                acc[v] = __fmaf_rn(dx, dx, acc[v]);
+                acc[v] = __fmaf_rn(dy, dy, acc[v]);
+                acc[v] = __fmaf_rn(dz, dz, acc[v]);
+                acc[v] = __fmaf_rn(dw, dw, acc[v]);
+            }
         }
     }
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(kFull, acc, o));
-    return acc;
+    for (int o = 16; o >= 1; o >>= 1) {
+        if (o >= T) {
+            float nx[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) nx[v] = __fadd_rn(acc[v], acc[v ^ (o / T)]);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = nx[v];
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = __fadd_rn(acc[v], tm.shfl_xor(acc[v], o));
+        }
+    }
+    return acc[0];
+}
+template <int CH>
+__device__ __forceinline__ float exact_dist(const float4 (&qv)[CH], const float *raw, uint32_t nch, int lane) {
+    return exact_dist_team<CH, 32>(reinterpret_cast<const float4(&)[1][CH]>(qv), raw, nch, Team<32>(lane));
 }
 
 // RaBitQ estimate of neighbour j from its block (Sec. 3.1.1):
@@ -339,11 +416,19 @@ __device__ __forceinline__ float mlp_logit_warp(const float *w, const float (&f)
 
 // ---------------------------------------------------------------- the kernel
 // LEAN: a build capped at 64 registers (8 resident blocks of 4 warps) for
-// d <= 256, trading a few spills for more warps in flight.
-template <int CH, int NB, bool LEAN = false>
+// d <= 256, trading a few spills for more warps in flight.  T: lanes per
+// query; a warp runs 32/T queries side by side, each team with its own
+// shared-memory slot, work-queue loop and visited set, so the per-query
+// serial steps (select, hash insert, merge bookkeeping) are shared by the
+// warp's queries instead of idling lanes.
+template <int CH, int NB, bool LEAN = false, int T = 32>
 __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_kernel(const SearchArgs a) {
+    constexpr int V = 32 / T;   // teams (queries) per warp
+    constexpr int NT = NB * V;  // neighbours per lane
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Team<T> tm(lane);
+    const int tl = tm.tl, team = lane / T;
     const uint32_t R = a.R, d = a.d, nch = d / 4;
     const float inv_R = __fdiv_rn(1.0f, (float)R);
 
@@ -368,7 +453,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
     }
     __syncthreads();
 
-    unsigned char *ws = smem + a.cta_bytes + (size_t)warp * a.warp_bytes;
+    unsigned char *ws = smem + a.cta_bytes + (size_t)(warp * V + team) * a.warp_bytes;
     unsigned char *buf[2] = {ws + a.o_buf0, ws + a.o_buf1};
     uint64_t *bar = reinterpret_cast<uint64_t *>(ws + a.o_bar);
     // beam and result: (key bits, id) pairs; bit 31 of a beam id marks an
@@ -376,25 +461,25 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
     uint2 *beam = reinterpret_cast<uint2 *>(ws + a.o_beam);
     uint2 *res = reinterpret_cast<uint2 *>(ws + a.o_res);
     uint32_t *planes = reinterpret_cast<uint32_t *>(ws + a.o_planes);
-    const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
-    // visited set: a shared-memory table, moved once to this warp's global
+    const uint32_t gteam = (blockIdx.x * (blockDim.x >> 5) + warp) * V + team;
+    // visited set: a shared-memory table, moved once to this team's global
     // table if a query's expansions fill half of it
     uint32_t *const Hs = reinterpret_cast<uint32_t *>(ws + a.o_hash);
-    uint32_t *const Hg = a.ghash ? a.ghash + ((size_t)gwarp << a.hash_bits) : nullptr;
+    uint32_t *const Hg = a.ghash ? a.ghash + ((size_t)gteam << a.hash_bits) : nullptr;
 
-    if (lane == 0) {
+    if (tl == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
     }
     fence_mbar_init();
-    __syncwarp();
+    tm.sync();
     uint32_t phase = 0;     // bit b: parity of the next completion of bar[b]
     bool healthy = true;    // false after an unrecovered copy timeout
 
     while (healthy) {
         int qi = 0;
-        if (lane == 0) qi = (int)atomicAdd(a.queue_head, 1u);
-        qi = __shfl_sync(kFull, qi, 0);
+        if (tl == 0) qi = (int)atomicAdd(a.queue_head, 1u);
+        qi = tm.shfl(qi, 0);
         if (qi >= a.nq) break;
 
         const int k = a.k[qi], ef = a.ef[qi];
@@ -402,11 +487,11 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
         uint32_t status = 0;
         if (!(k >= 1 && k <= a.max_k && ef >= k && ef <= a.max_ef)) {
             const int kk = k < 0 ? 0 : (k > SQG_MAX_K ? SQG_MAX_K : k);
-            for (int t = lane; t < kk; t += 32) {
+            for (int t = tl; t < kk; t += T) {
                 a.out_ids[off + t] = SQG_NO_ID;
                 a.out_dists[off + t] = __int_as_float(0x7f800000);
             }
-            if (lane == 0) {
+            if (tl == 0) {
                 if (a.stats) a.stats[qi] = sqg_query_stats{0u, SQG_STATUS_BAD_PARAM};
                 atomicOr(a.status_word, SQG_STATUS_BAD_PARAM);
                 if (a.trace_n) a.trace_n[qi] = 0;
@@ -416,39 +501,41 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
         const int hop_cap = a.hop_cap > 0 ? a.hop_cap : 4 * ef + 64;
 
         // ---- query setup: raw query in registers, quantized rotated query planes
-        float4 qv[CH];
+        float4 qv[V][CH];
         const float *q = a.queries + (size_t)qi * d;
 #pragma unroll
-        for (int t = 0; t < CH; ++t) {
-            uint32_t c = lane + 32 * t;
-            qv[t] = c < nch ? reinterpret_cast<const float4 *>(q)[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int t = 0; t < CH; ++t) {
+                const uint32_t c = tl + T * v + 32 * t;
+                qv[v][t] = c < nch ? reinterpret_cast<const float4 *>(q)[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         QuerySide qs;
         if (a.qplanes) {  // quantized by the exact pass after the tensor-core rotation
             const uint4 *src = reinterpret_cast<const uint4 *>(a.qplanes + (size_t)qi * 4 * (d / 32));
-            for (uint32_t w = lane; w < d / 32; w += 32) reinterpret_cast<uint4 *>(planes)[w] = src[w];
+            for (uint32_t w = tl; w < d / 32; w += T) reinterpret_cast<uint4 *>(planes)[w] = src[w];
             const float4 sc = a.qscal[qi];
             qs.vl = sc.x;
             qs.delta = sc.y;
             qs.sq = (int)sc.z;
             qs.inv_sqrt_d = sc.w;
         } else {
-            qs = quantize_warp(a.qrot + (size_t)qi * d, d, planes, lane);
+            qs = quantize_team<T>(a.qrot + (size_t)qi * d, d, planes, tm);
         }
         uint32_t *H = Hs;
         uint32_t hbits = a.shash_bits;
-        for (uint32_t i = lane; i < (1u << hbits); i += 32) H[i] = kEmpty;
+        for (uint32_t i = tl; i < (1u << hbits); i += T) H[i] = kEmpty;
 
         // ---- Algorithm 1, line 1: the beam and the result start from the entry
         int m = 1, cur = 0, rc = 0;
-        if (lane == 0) {
+        if (tl == 0) {
             beam[0] = make_uint2(0u, a.entry);  // key: the entry's exact distance, set at its expansion
         }
         int cb = 0;                          // buffer holding the block to expand next
         uint32_t pend = a.entry;             // id whose block is in flight into buf[cb]
         bool inflight = true;
-        __syncwarp();
-        if (lane == 0) {
+        tm.sync();
+        if (tl == 0) {
             fence_proxy_async();
             bulk_fetch(buf[0], a.blocks + (size_t)a.entry * a.block_bytes, a.block_bytes, &bar[0]);
         }
@@ -463,8 +550,8 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
             // after cur, which is the first unvisited entry) and find the next
             // unvisited entry after cur
             int nxt = m;
-            for (int base = cur; base < m; base += 32) {
-                const int i = base + lane;
+            for (int base = cur; base < m; base += T) {
+                const int i = base + tl;
                 uint32_t v = kVisited;
                 if (i < m) {
                     v = beam[i].y;
@@ -474,18 +561,18 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                     }
                 }
                 if (nxt == m) {
-                    const uint32_t b = __ballot_sync(kFull, i > cur && !(v & kVisited));
+                    const uint32_t b = tm.ballot(i > cur && !(v & kVisited));
                     if (b) nxt = base + __ffs(b) - 1;
                 }
             }
-            if (lane == 0) {
+            if (tl == 0) {
                 hash_insert(H, hbits, p);
                 if (a.path && hops < a.path_cap) a.path[(size_t)qi * a.path_cap + hops] = p;
             }
-            __syncwarp();
+            tm.sync();
             ++hops;
             if (Hg && H == Hs && (uint32_t)hops >= (1u << hbits) / 2) {
-                hash_migrate(Hs, hbits, Hg, a.hash_bits, lane);
+                hash_migrate<T>(Hs, hbits, Hg, a.hash_bits, tm);
                 H = Hg;
                 hbits = a.hash_bits;
             }
@@ -494,8 +581,8 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                     if (!mbar_wait_bounded(&bar[cb], (phase >> cb) & 1u)) { status |= SQG_STATUS_TIMEOUT; healthy = false; break; }
                     phase ^= 1u << cb;
                 }
-                __syncwarp();
-                if (lane == 0) {
+                tm.sync();
+                if (tl == 0) {
                     fence_proxy_async();
                     bulk_fetch(buf[cb], a.blocks + (size_t)p * a.block_bytes, a.block_bytes, &bar[cb]);
                 }
@@ -512,29 +599,29 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
             const unsigned char *blk = buf[cb];
 
             // ---- line 4: exact distance, implicit re-ranking
-            const float dist_c = exact_dist<CH>(qv, reinterpret_cast<const float *>(blk), nch, lane);
-            if (hops == 1 && lane == 0) beam[0].x = __float_as_uint(dist_c);
+            const float dist_c = exact_dist_team<CH, T>(qv, reinterpret_cast<const float *>(blk), nch, tm);
+            if (hops == 1 && tl == 0) beam[0].x = __float_as_uint(dist_c);
             bool improved = false;
             {
                 const bool full = rc == k;
                 if (!full || kless(dist_c, p, __uint_as_float(res[k - 1].x), res[k - 1].y)) {
                     improved = true;
                     int pos = 0;
-                    for (int base = 0; base < rc; base += 32) {
-                        int i = base + lane;
+                    for (int base = 0; base < rc; base += T) {
+                        int i = base + tl;
                         const uint2 e = i < rc ? res[i] : make_uint2(0u, 0u);
-                        pos += __popc(__ballot_sync(kFull, i < rc && kless(__uint_as_float(e.x), e.y, dist_c, p)));
+                        pos += __popc(tm.ballot(i < rc && kless(__uint_as_float(e.x), e.y, dist_c, p)));
                     }
                     const int top = full ? k - 1 : rc;  // entries [pos, top) move up one
-                    for (int base = ((top - 1) & ~31); base >= (pos & ~31) && top > pos; base -= 32) {
-                        int i = base + lane;
+                    for (int base = ((top - 1) & ~(T - 1)); base >= (pos & ~(T - 1)) && top > pos; base -= T) {
+                        int i = base + tl;
                         bool mv = i >= pos && i < top;
                         const uint2 e = mv ? res[i] : make_uint2(0u, 0u);
-                        __syncwarp();
+                        tm.sync();
                         if (mv) res[i + 1] = e;
-                        __syncwarp();
+                        tm.sync();
                     }
-                    if (lane == 0) res[pos] = make_uint2(__float_as_uint(dist_c), p);
+                    if (tl == 0) res[pos] = make_uint2(__float_as_uint(dist_c), p);
                     rc = full ? k : rc + 1;
                 }
             }
@@ -545,14 +632,14 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
             const uint2 we = beam[ef - 1 < m ? ef - 1 : 0];
             const float wk = __uint_as_float(we.x);
             const uint32_t wi = we.y & kIdMask;
-            float ck[NB];
-            uint32_t cid[NB];
-            int cpos[NB];
-            bool adm[NB];
+            float ck[NT];
+            uint32_t cid[NT];
+            int cpos[NT];
+            bool adm[NT];
             const float sqrt_dc = a.eps0 == 0.0f ? 0.0f : __fsqrt_rn(dist_c);
 #pragma unroll
-            for (int t = 0; t < NB; ++t) {
-                const uint32_t j = lane + 32 * t;
+            for (int t = 0; t < NT; ++t) {
+                const uint32_t j = tl + T * t;
                 cid[t] = ids[j];
                 const Est e = estimate(blk, a, planes, qs, j, dist_c, sqrt_dc);
                 ck[t] = e.key;
@@ -563,7 +650,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
             }
             if (!a.multi_estimate) {  // ablation w/o ME: skip ids already in the beam
 #pragma unroll
-                for (int t = 0; t < NB; ++t) {
+                for (int t = 0; t < NT; ++t) {
                     bool in = false;
                     for (int i = 0; i < m && adm[t]; ++i) in |= (beam[i].y & kIdMask) == cid[t];
                     adm[t] = adm[t] && !in;
@@ -571,7 +658,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
             }
             // position in the beam; an identical (key, id) already there is dropped
 #pragma unroll
-            for (int t = 0; t < NB; ++t) {
+            for (int t = 0; t < NT; ++t) {
                 cpos[t] = 0;
                 if (adm[t]) {
                     int lo = 0, hi = m;
@@ -588,48 +675,48 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                     }
                 }
             }
-            uint32_t am[NB];
+            uint32_t am[NT];
             int nadm = 0;
 #pragma unroll
-            for (int t = 0; t < NB; ++t) {
-                am[t] = __ballot_sync(kFull, adm[t]);
+            for (int t = 0; t < NT; ++t) {
+                am[t] = tm.ballot(adm[t]);
                 nadm += __popc(am[t]);
             }
             // rank among the admitted candidates (ids in a block are distinct)
-            int rank[NB];
+            int rank[NT];
 #pragma unroll
-            for (int t = 0; t < NB; ++t) rank[t] = 0;
+            for (int t = 0; t < NT; ++t) rank[t] = 0;
             const float kInf = __int_as_float(0x7f800000);
             float bk = kInf, b2k = kInf;  // best and second-best admitted candidates
             uint32_t bi = kEmpty, b2i = kEmpty;
 #pragma unroll
-            for (int t2 = 0; t2 < NB; ++t2) {
+            for (int t2 = 0; t2 < NT; ++t2) {
                 uint32_t mm = am[t2];
                 while (mm) {
                     const int src = __ffs(mm) - 1;
                     mm &= mm - 1;
-                    const float ok = __shfl_sync(kFull, ck[t2], src);
-                    const uint32_t oi = __shfl_sync(kFull, cid[t2], src);
+                    const float ok = tm.shfl(ck[t2], src);
+                    const uint32_t oi = tm.shfl(cid[t2], src);
 #pragma unroll
-                    for (int t = 0; t < NB; ++t) rank[t] += kless(ok, oi, ck[t], cid[t]) ? 1 : 0;
+                    for (int t = 0; t < NT; ++t) rank[t] += kless(ok, oi, ck[t], cid[t]) ? 1 : 0;
                 }
             }
             // the best admitted candidate has rank 0 (ranks are distinct), the
             // runner-up rank 1 (needed for the speculative prefetch only)
 #pragma unroll
-            for (int t = 0; t < NB; ++t) {
-                const uint32_t m0 = __ballot_sync(kFull, adm[t] && rank[t] == 0);
+            for (int t = 0; t < NT; ++t) {
+                const uint32_t m0 = tm.ballot(adm[t] && rank[t] == 0);
                 if (m0) {
                     const int s = __ffs(m0) - 1;
-                    bk = __shfl_sync(kFull, ck[t], s);
-                    bi = __shfl_sync(kFull, cid[t], s);
+                    bk = tm.shfl(ck[t], s);
+                    bi = tm.shfl(cid[t], s);
                 }
                 if (a.prefetch == 2) {
-                    const uint32_t m1 = __ballot_sync(kFull, adm[t] && rank[t] == 1);
+                    const uint32_t m1 = tm.ballot(adm[t] && rank[t] == 1);
                     if (m1) {
                         const int s = __ffs(m1) - 1;
-                        b2k = __shfl_sync(kFull, ck[t], s);
-                        b2i = __shfl_sync(kFull, cid[t], s);
+                        b2k = tm.shfl(ck[t], s);
+                        b2i = tm.shfl(cid[t], s);
                     }
                 }
             }
@@ -649,9 +736,9 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                         if (kless(b2k, b2i, rk, ri)) { rk = b2k; ri = b2i; }
                     } else {
                         int n2 = m;  // the unvisited beam entry after nxt
-                        for (int base = nxt + 1; base < m; base += 32) {
-                            const int i = base + lane;
-                            const uint32_t bb2 = __ballot_sync(kFull, i < m && !(beam[i].y & kVisited));
+                        for (int base = nxt + 1; base < m; base += T) {
+                            const int i = base + tl;
+                            const uint32_t bb2 = tm.ballot(i < m && !(beam[i].y & kVisited));
                             if (bb2) { n2 = base + __ffs(bb2) - 1; break; }
                         }
                         if (n2 < m) {
@@ -665,15 +752,15 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                     runner_id = ri;
                 }
             }
-            __syncwarp();
-            if (runner_id != kEmpty && lane == 0)
+            tm.sync();
+            if (runner_id != kEmpty && tl == 0)
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
                                  a.blocks + (size_t)runner_id * a.block_bytes),
                              "r"(a.block_bytes)
                              : "memory");
             if (next_id != kEmpty) {
                 const int nb = cb ^ 1;
-                if (lane == 0) {
+                if (tl == 0) {
                     fence_proxy_async();
                     bulk_fetch(buf[nb], a.blocks + (size_t)next_id * a.block_bytes, a.block_bytes, &bar[nb]);
                 }
@@ -689,9 +776,9 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                 // smaller key never has a larger position, so this is sorted
                 int *spos = reinterpret_cast<int *>(ws + a.o_spos);
 #pragma unroll
-                for (int t = 0; t < NB; ++t)
+                for (int t = 0; t < NT; ++t)
                     if (adm[t]) spos[rank[t]] = cpos[t];
-                __syncwarp();
+                tm.sync();
                 const int minpos = spos[0];
                 // number of admitted candidates placed at or before beam entry i
                 auto count_le = [&](int i) {
@@ -703,28 +790,28 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                     }
                     return lo;
                 };
-                for (int base = ((m - 1) & ~31); base >= (minpos & ~31); base -= 32) {
-                    const int i = base + lane;
+                for (int base = ((m - 1) & ~(T - 1)); base >= (minpos & ~(T - 1)); base -= T) {
+                    const int i = base + tl;
                     const bool valid = i >= minpos && i < m;
                     const int cnt = valid ? count_le(i) : 0;
                     const uint2 e = valid ? beam[i] : make_uint2(0u, 0u);
-                    __syncwarp();
+                    tm.sync();
                     if (valid && cnt > 0 && i + cnt < ef) beam[i + cnt] = e;
-                    __syncwarp();
+                    tm.sync();
                 }
                 const int nxt_shift = nxt < m ? count_le(nxt) : 0;
                 int newcur = m + nadm;  // "none"
 #pragma unroll
-                for (int t = 0; t < NB; ++t) {
+                for (int t = 0; t < NT; ++t) {
                     const int fp = cpos[t] + rank[t];
                     const bool keep = adm[t] && fp < ef;
                     if (keep) {
                         beam[fp] = make_uint2(__float_as_uint(ck[t]), cid[t]);
                         newcur = min(newcur, fp);
                     }
-                    inserted += __popc(__ballot_sync(kFull, keep));
+                    inserted += __popc(tm.ballot(keep));
                 }
-                newcur = __reduce_min_sync(kFull, newcur);
+                newcur = tm.reduce_min(newcur);
                 if (nxt < m && nxt >= minpos) {
                     if (nxt + nxt_shift < ef) newcur = min(newcur, nxt + nxt_shift);
                 } else if (nxt < m) {
@@ -735,10 +822,11 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
             } else {
                 cur = nxt;
             }
-            __syncwarp();
+            tm.sync();
 
             // ---- learned early stop (not in the paper) / trace
-            const bool stop_on = a.mlp || a.trace_feat;  // the state below feeds the stop only
+            // (teams of 32 lanes only: the fused network and the trace use the whole warp)
+            const bool stop_on = T == 32 && (a.mlp || a.trace_feat);  // the state below feeds the stop only
             if (stop_on) {
                 st.hops = hops;
                 st.inserted_last = inserted;
@@ -749,18 +837,18 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                 st.ema_insert = __fadd_rn(__fmul_rn(0.75f, st.ema_insert),
                                           __fmul_rn(0.25f, __fmul_rn((float)inserted, inv_R)));
             }
-            if (stop_on && a.stop_every > 0 && hops % a.stop_every == 0 && rc == k) {
+            if constexpr (T == 32) if (stop_on && a.stop_every > 0 && hops % a.stop_every == 0 && rc == k) {
                 const float rk = __uint_as_float(res[k - 1].x);
                 const float rk2 = __fmul_rn(1.25f, rk);
                 int u = 0, near1 = 0, near2 = 0;  // unvisited; of them with key <= rk, <= 1.25 rk
-                for (int base = 0; base < m; base += 32) {
-                    const int i = base + lane;
+                for (int base = 0; base < m; base += T) {
+                    const int i = base + tl;
                     const uint2 e = i < m ? beam[i] : make_uint2(0u, kVisited);
                     const bool un = !(e.y & kVisited);
                     const float kk = un ? __uint_as_float(e.x) : 0.0f;
-                    u += __popc(__ballot_sync(kFull, un));
-                    near1 += __popc(__ballot_sync(kFull, un && kk <= rk));
-                    near2 += __popc(__ballot_sync(kFull, un && kk <= rk2));
+                    u += __popc(tm.ballot(un));
+                    near1 += __popc(tm.ballot(un && kk <= rk));
+                    near2 += __popc(tm.ballot(un && kk <= rk2));
                 }
                 const float den = rk > 1e-20f ? rk : 1e-20f;
                 const float fef = (float)ef;
@@ -799,13 +887,13 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                     if (a.gt) {
                         int hit = 0;
                         const uint32_t *g = a.gt + (size_t)qi * a.gt_k;
-                        for (int i = lane; i < rc; i += 32) {
+                        for (int i = tl; i < rc; i += 32) {
                             const uint32_t x = res[i].y;
                             for (int b = 0; b < k; ++b) hit += g[b] == x ? 1 : 0;
                         }
 #pragma unroll
-                        for (int o = 16; o >= 1; o >>= 1) hit += __shfl_xor_sync(kFull, hit, o);
-                        if (lane == 0) a.trace_hit[(size_t)qi * a.trace_cap + tn] = hit;
+                        for (int o = 16; o >= 1; o >>= 1) hit += tm.shfl_xor(hit, o);
+                        if (tl == 0) a.trace_hit[(size_t)qi * a.trace_cap + tn] = hit;
                     }
                     ++tn;
                 }
@@ -824,21 +912,21 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                 healthy = false;
             }
         }
-        __syncwarp();
+        tm.sync();
         // ---- line 8: the k nearest expanded vertices by exact distance
         const bool ok = !(status & SQG_STATUS_TIMEOUT);
-        for (int t = lane; t < k; t += 32) {
+        for (int t = tl; t < k; t += T) {
             const bool have = ok && t < rc;
             const uint2 e = have ? res[t] : make_uint2(0x7f800000u, SQG_NO_ID);
             a.out_ids[off + t] = e.y;
             a.out_dists[off + t] = __uint_as_float(e.x);
         }
-        if (lane == 0) {
+        if (tl == 0) {
             if (a.stats) a.stats[qi] = sqg_query_stats{(uint32_t)hops, status};
             if (status) atomicOr(a.status_word, status);
             if (a.trace_n) a.trace_n[qi] = tn;
         }
-        __syncwarp();
+        tm.sync();
     }
 }
 
@@ -853,6 +941,10 @@ cudaError_t launch_quantize_exact(const float *q, const float *rot, const float 
 cudaError_t launch_search_nb1(int ch, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const SearchArgs &a);
 cudaError_t launch_search_nb2(int ch, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const SearchArgs &a);
 cudaError_t search_occupancy_nb1(int ch, int block, size_t smem, int *blocks_per_sm);
+// teams of 16 or 8 lanes (search_team.cu): ch 1 or 2, nb 1 or 2
+cudaError_t launch_search_team(int ch, int nb, int team, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                               const SearchArgs &a);
+cudaError_t search_occupancy_team(int ch, int nb, int team, int block, size_t smem, int *blocks_per_sm);
 cudaError_t search_occupancy_nb2(int ch, int block, size_t smem, int *blocks_per_sm);
 
 }  // namespace sqg

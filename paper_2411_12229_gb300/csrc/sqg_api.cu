@@ -240,7 +240,7 @@ int pick_ch(uint32_t d) {
 }
 
 struct LaunchPlan {
-    int ch, nb, warps, grid;
+    int ch, nb, team, warps, grid;
     size_t smem;
     SearchArgs a;  // layout fields filled in
     bool ghash;
@@ -253,9 +253,16 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     pl.ch = pick_ch(d);
     pl.nb = (int)(R / 32);
     if (pl.ch < 0 || (pl.nb != 1 && pl.nb != 2)) return SQG_ERR_UNSUPPORTED;
-    // the 64-register build for d <= 256 unless asked for the full one
-    // (measured faster at d = 128: more resident warps hide more latency)
-    if (p.lean != 2 && pl.ch <= 2) pl.ch = -pl.ch;
+    pl.team = p.team == 0 ? 32 : p.team;
+    const int V = 32 / pl.team;  // queries per warp
+    if (pl.team < 32) {
+        // smaller teams: d <= 256, the 96-register build, no fused stop network
+        if (pl.ch > 2 || p.stop_mlp) return SQG_ERR_UNSUPPORTED;
+    } else if (p.lean != 2 && pl.ch <= 2) {
+        // the 64-register build for d <= 256 unless asked for the full one
+        // (measured faster at d = 128: more resident warps hide more latency)
+        pl.ch = -pl.ch;
+    }
     const long long cap = p.hop_cap > 0 ? p.hop_cap : 4LL * max_ef + 64;
     uint32_t bits = 5;
     while ((1ull << bits) < 2ull * (unsigned long long)cap + 1) ++bits;
@@ -274,7 +281,7 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     a.o_spos = (uint32_t)o; o = align_up(o + 4 * (size_t)R, 16);
     // visited set: up to 2^10 slots in shared memory; a longer search moves
     // to its warp's full-size table in the workspace
-    const uint32_t smem_bits_default = pl.ch < 0 ? 9u : 10u;
+    const uint32_t smem_bits_default = (pl.ch < 0 || pl.team < 32) ? 9u : 10u;
     a.shash_bits =
         std::min<uint32_t>(bits, p.visited_smem_log2 > 0 ? (uint32_t)p.visited_smem_log2 : smem_bits_default);
     pl.ghash = a.shash_bits < bits;
@@ -283,18 +290,20 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     const size_t cta = p.stop_mlp ? align_up(sizeof(float) * SQG_MLP_NPARAM, 128) : 0;
     int warps = p.warps_per_block > 0 ? p.warps_per_block : 4;
     warps = std::min(warps, 4);
-    while (warps > 1 && cta + warps * warp_bytes > ix->smem_optin) --warps;
-    if (cta + warps * warp_bytes > ix->smem_optin) return SQG_ERR_CAPACITY;
+    // one slot of warp_bytes per query in flight: V per warp
+    while (warps > 1 && cta + warps * V * warp_bytes > ix->smem_optin) --warps;
+    if (cta + warps * V * warp_bytes > ix->smem_optin) return SQG_ERR_CAPACITY;
     a.warp_bytes = (uint32_t)warp_bytes;
     a.cta_bytes = (uint32_t)cta;
     pl.warps = warps;
-    pl.smem = cta + warps * warp_bytes;
+    pl.smem = cta + warps * V * warp_bytes;
     int per_sm = 0;
-    cudaError_t e = pl.nb == 1 ? search_occupancy_nb1(pl.ch, warps * 32, pl.smem, &per_sm)
-                               : search_occupancy_nb2(pl.ch, warps * 32, pl.smem, &per_sm);
+    cudaError_t e = pl.team < 32 ? search_occupancy_team(pl.ch, pl.nb, pl.team, warps * 32, pl.smem, &per_sm)
+                    : pl.nb == 1 ? search_occupancy_nb1(pl.ch, warps * 32, pl.smem, &per_sm)
+                                 : search_occupancy_nb2(pl.ch, warps * 32, pl.smem, &per_sm);
     if (e != cudaSuccess) return SQG_ERR_CUDA;
     if (per_sm < 1) return SQG_ERR_CAPACITY;
-    const long long want = ((long long)nq + warps - 1) / warps;
+    const long long want = ((long long)nq + warps * V - 1) / (warps * V);
     pl.grid = (int)std::max(1LL, std::min<long long>((long long)per_sm * ix->num_sms, want));
     // workspace
     size_t w = 0;
@@ -304,7 +313,7 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     pl.ws_maxes = w; w = align_up(w + 8, 256);
     pl.ws_stats = w; w = align_up(w + sizeof(sqg_query_stats) * (size_t)std::max(nq, 1), 256);
     pl.ws_ghash = w;
-    if (pl.ghash) w = align_up(w + hash_bytes * (size_t)pl.grid * warps, 256);
+    if (pl.ghash) w = align_up(w + hash_bytes * (size_t)pl.grid * warps * V, 256);
     // the exactly quantized query after a tensor-core rotation
     pl.ws_planes = w; w = align_up(w + 16 * (size_t)(d / 32) * (size_t)std::max(nq, 1), 256);
     pl.ws_scal = w; w = align_up(w + 16 * (size_t)std::max(nq, 1), 256);
@@ -332,7 +341,8 @@ sqg_search_params default_params() {
 int check_params(const sqg_search_params &p) {
     if (p.hop_cap < 0 || p.max_k < 0 || p.max_ef < 0 || p.max_k > SQG_MAX_K || p.max_ef > SQG_MAX_EF ||
         (p.max_k > 0 && p.max_ef > 0 && p.max_ef < p.max_k) || p.stop_every < 0 ||
-        (p.team != 0 && p.team != 32) || p.warps_per_block < 0 || !std::isfinite(p.eps0) ||
+        (p.team != 0 && p.team != 8 && p.team != 16 && p.team != 32) || p.warps_per_block < 0 ||
+        !std::isfinite(p.eps0) ||
         (p.visited_smem_log2 != 0 && (p.visited_smem_log2 < 5 || p.visited_smem_log2 > 12)) ||
         p.prefetch < 0 || p.prefetch > 2 || p.lean < 0 || p.lean > 2 || p.rotation < 0 || p.rotation > 2 ||
         (p.stop_mlp && p.stop_every < 1))
@@ -524,6 +534,7 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     sqg_search_params p = params ? *params : default_params();
     if (params && p.stop_every == 0) p.stop_every = 1;
     if (check_params(p) != SQG_OK) return SQG_ERR_INVALID_ARG;
+    if (trace_feat && p.team != 0 && p.team != 32) return SQG_ERR_UNSUPPORTED;  // the trace uses whole warps
     DeviceGuard g(ix->device);
     cudaError_t e;
     int max_k = p.max_k, max_ef = p.max_ef;
@@ -614,8 +625,10 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     if (e == cudaSuccess && p.timing_events[0])
         e = cudaEventRecord(reinterpret_cast<cudaEvent_t>(p.timing_events[0]), stream);
     if (e == cudaSuccess) {
-        e = pl.nb == 1 ? launch_search_nb1(pl.ch, dim3(pl.grid), dim3(pl.warps * 32), pl.smem, stream, a)
-                       : launch_search_nb2(pl.ch, dim3(pl.grid), dim3(pl.warps * 32), pl.smem, stream, a);
+        e = pl.team < 32 ? launch_search_team(pl.ch, pl.nb, pl.team, dim3(pl.grid), dim3(pl.warps * 32), pl.smem,
+                                              stream, a)
+            : pl.nb == 1 ? launch_search_nb1(pl.ch, dim3(pl.grid), dim3(pl.warps * 32), pl.smem, stream, a)
+                         : launch_search_nb2(pl.ch, dim3(pl.grid), dim3(pl.warps * 32), pl.smem, stream, a);
     }
     if (e == cudaSuccess && p.timing_events[1])
         e = cudaEventRecord(reinterpret_cast<cudaEvent_t>(p.timing_events[1]), stream);

@@ -16,13 +16,13 @@ def test_every_tuning_knob_gives_identical_results(tiny_index, tmp_path, monkeyp
     ix = Index(p, 0)
     qd = torch.from_numpy(q).cuda()
     ref = ix.search(qd, 10, 64)
-    import itertools
-    names = list(autotune.KNOBS)
-    for combo in itertools.product(*(autotune.KNOBS[n] for n in names)):
-        got = ix.search(qd, 10, 64, **dict(zip(names, combo)))
-        assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]), dict(zip(names, combo))
+    cfgs = list(autotune.combos(ix))
+    assert len(cfgs) == 24 + 2 * 12  # teams of 16 and 8 lanes only with the 96-register build
+    for cfg in cfgs:
+        got = ix.search(qd, 10, 64, **cfg)
+        assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]), cfg
     res = autotune.autotune(ix, qd, 10, 64, reps=2)
-    assert len(res["table"]) == 24
+    assert len(res["table"]) == len(cfgs)
     assert autotune.tuned(ix, 64) == res["best"]
     assert autotune.tuned(ix, 1000) == autotune.DEFAULT
 
