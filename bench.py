@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-stop", action="store_true", help="skip the learned-stop comparison")
     ap.add_argument("--stop-train", type=int, default=20000, help="training queries for the learned stop")
+    ap.add_argument("--prep", action="store_true",
+                    help="time query preparation alone (rotation + 4-bit quantization), CUDA vs tensor cores")
     return ap.parse_args()
 
 
@@ -173,14 +175,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_record(workload_name):
+def traffic_record(workload_name, ef):
     """DRAM bytes per launch of the search kernel from a committed ncu
-    summary, used only while the kernel source is unchanged since."""
+    summary of the same launch (workload and ef), used only while the kernel
+    source is unchanged since."""
     p = ROOT / "profiles" / "search_kernel_traffic.json"
     if not p.exists():
         return None
     z = json.loads(p.read_text())
-    if z.get("kernel_digest") != kernel_digest() or z.get("workload") != workload_name:
+    if z.get("kernel_digest") != kernel_digest() or z.get("workload") != workload_name or z.get("ef") != ef:
         return None
     return z
 
@@ -366,6 +369,61 @@ def bench_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_prep(args):
+    """Query preparation alone: q' = P^-1 q and its exact 4-bit
+    quantization, on the CUDA cores and on the tensor cores (plus the exact
+    pass), for the workload's dimension and query count.  The index is a
+    small one (--n, default 1000 vertices, exact kNN graph built on the
+    host): the rotation does not depend on n."""
+    import torch
+
+    from paper_2411_12229_gb300 import index_builder as ib
+    from paper_2411_12229_gb300.api import Index
+    w = synth.WORKLOADS[args.workload]
+    n, nq, d = args.n or 1000, args.nq or w.n_queries, w.d
+    ws = synth.small(w, n, 64)
+    x = synth.base(ws)
+    path = pathlib.Path(args.cache) / f"prep-{w.name}-n{n}.sqg"
+    path.parent.mkdir(parents=True, exist_ok=True)
+    if not path.exists():
+        ib.build_index(path, x, w.degree)
+    ix = Index(path, 0)
+    q = torch.from_numpy(synth.queries(w.with_(n_queries=nq))).cuda()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    res = {}
+    for name, fn in (("cuda_cores", lambda: ix.prepare_queries(q)), ("tensor_cores", lambda: ix.prepare_queries_tc(q))):
+        for _ in range(max(3, args.warmup)):
+            out = fn()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = fn()
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        res[name] = (float(np.median(ms)), out)
+    same = bool(torch.equal(res["cuda_cores"][1][1], res["tensor_cores"][1][1]) and
+                torch.equal(res["cuda_cores"][1][2], res["tensor_cores"][1][2]))
+    rec = int(res["tensor_cores"][1][3].item())
+    flop = 2.0 * nq * d * d
+    peak = json.loads((ROOT / "MEASURED_PEAKS.json").read_text())["bf16_tflops"] * (1.1 / 2.25) \
+        if (ROOT / "MEASURED_PEAKS.json").exists() else 1900.0 * (1.1 / 2.25)
+    t_tc = res["tensor_cores"][0]
+    line = {"metric": "query preparation time (rotation + 4-bit quantization)", "unit": "ms", "workload": w.name,
+            "d": d, "queries": nq, "cuda_core_ms": round(res["cuda_cores"][0], 4), "tensor_core_ms": round(t_tc, 4),
+            "speedup": round(res["cuda_cores"][0] / t_tc, 3), "planes_identical": same,
+            "recomputed_fraction": round(rec / (nq * d), 5),
+            "roofline": {"bound": "tensor", "achieved": round(3 * flop / (t_tc / 1e3) / 1e12, 1),
+                         "peak": round(peak, 1), "unit": "TFLOP/s",
+                         "frac": round(3 * flop / (t_tc / 1e3) / 1e12 / peak, 4),
+                         "note": "3xTF32 FLOP over the tensor-core rotation and the exact pass together; "
+                                 "peak = measured bf16 x nominal tf32/bf16 ratio (1.1/2.25)"},
+            "l2": "flushed (512 MiB write) before each call"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -374,6 +432,8 @@ def main():
 
     from paper_2411_12229_gb300 import build as build_mod
     build_mod.build()
+    if args.prep:
+        return bench_prep(args)
     from paper_2411_12229_gb300 import eval as E
     from paper_2411_12229_gb300.api import Index
 
@@ -499,7 +559,7 @@ def main():
     kern_mean = float(np.mean(kern_ms))
     achieved = alg_bytes / (kern_mean / 1e3) / 1e9
     peak, peak_src = measured_peaks()
-    tr = traffic_record(w.name)
+    tr = traffic_record(w.name, ef_sel)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_src,
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,

@@ -63,7 +63,7 @@ class Workload:
         return dataclasses.replace(self, **kw)
 
 
-EF_SWEEP = (16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512)
+EF_SWEEP = (16, 24, 32, 36, 40, 44, 48, 56, 64, 80, 96, 112, 128, 160, 192, 256, 320, 384, 512)
 
 # The five workloads, named by what they are.
 TINY_10K_D128 = Workload("tiny-10k-d128", 10_000, 128, 64, 200, 32, ef=(32, 64, 128))
