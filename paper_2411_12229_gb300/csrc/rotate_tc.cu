@@ -15,8 +15,10 @@
 //               swizzle) into a 3-stage ring;
 //   warp 1      MMA issuer: 12 MMAs per chunk into one of two TMEM buffers;
 //   warps 2-5   split the query tile into hi (in place) and lo;
-//   warps 6-9   drain each chunk's 128 x 128 result from TMEM (tcgen05.ld)
-//               and add it to fp32 registers, one tile row per thread.
+//   warps 6-21  drain each chunk's 128 x 128 result from TMEM (tcgen05.ld)
+//               and add it to fp32 registers: 4 warps per 32-lane quarter
+//               of TMEM, 32 columns of one tile row per thread, so one
+//               load round-trip per chunk.
 // Draining per chunk keeps the tensor cores' accumulation short (96 products
 // per accumulator), which is what makes the error bound below tight.
 //
@@ -24,9 +26,9 @@
 // v_l and Delta being exactly those of the canonical rotation.  The
 // tensor-core q' differs from it by at most err = c(d) * ||q||, so every
 // coordinate whose code or whose role as min/max could change within err is
-// recomputed in the canonical order (one lane per coordinate); the rest are
-// decided from q'.  The result is bit-identical to quantizing the canonical
-// rotation.
+// recomputed in the canonical order (one warp per coordinate, its row staged
+// through shared memory, one chunk per lane); the rest are decided from q'.
+// The result is bit-identical to quantizing the canonical rotation.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -42,8 +44,9 @@ constexpr int BM = 128, BN = 128, BK = 32;  // BK fp32 = one 128-byte swizzled r
 constexpr int kStages = 3;
 constexpr int kTile = BM * BK * 4;          // 16 KB
 constexpr int kStageBytes = 4 * kTile;      // query raw->hi, query lo, P hi, P lo
-constexpr int kWarps = 10, kThreads = kWarps * 32;
-constexpr int kConvWarp0 = 2, kConvWarps = 4, kDrainWarp0 = 6;
+constexpr int kConvWarp0 = 2, kConvWarps = 4, kDrainWarp0 = 6, kDrainWarps = 16;
+constexpr int kWarps = kDrainWarp0 + kDrainWarps, kThreads = kWarps * 32;
+constexpr int kDrainCols = BN / (kDrainWarps / 4);  // accumulator columns per drain thread
 constexpr uint32_t kTmemCols = 2 * BN;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
 constexpr unsigned long long kWaitNs = 1000000000ull;
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int t = 0; t < 2; ++t) {
             bar_init(saddr(&tfull_bar[t]), 1);
-            bar_init(saddr(&tempty_bar[t]), 4);
+            bar_init(saddr(&tempty_bar[t]), kDrainWarps);
         }
         bar_init(saddr(&done_bar), 1);
         abort_flag = 0;
@@ -275,36 +278,35 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31 = tile rows
-        float acc[BN];
+        const int col0 = ((warp - kDrainWarp0) >> 2) * kDrainCols;
+        float acc[kDrainCols];
         for (int g = 0; g < total; ++g) {
             const int t = g & 1, m = g >> 1, k = g % nchunk;
             if (k == 0) {
 #pragma unroll
-                for (int j = 0; j < BN; ++j) acc[j] = 0.0f;
+                for (int j = 0; j < kDrainCols; ++j) acc[j] = 0.0f;
             }
             if (!bar_wait(saddr(&tfull_bar[t]), (uint32_t)(m & 1), abort_v)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-            for (int cc = 0; cc < BN / 32; ++cc) {
+            for (int cc = 0; cc < kDrainCols; cc += 32) {
                 uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * BN + cc * 32), v);
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * BN + col0 + cc), v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) acc[cc * 32 + j] = __fadd_rn(acc[cc * 32 + j], __uint_as_float(v[j]));
+                for (int j = 0; j < 32; ++j) acc[cc + j] = __fadd_rn(acc[cc + j], __uint_as_float(v[j]));
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) bar_arrive(saddr(&tempty_bar[t]));
-            if (k == nchunk - 1) {  // the tile is complete: write its rows
+            if (k == nchunk - 1) {  // the tile is complete: write this thread's part of its row
                 int r0, c0;
                 tile_of(g, r0, c0);
                 const int row = r0 + quarter * 32 + lane;
-                if (row < nq) {
-                    float4 *o = reinterpret_cast<float4 *>(out + (size_t)row * d + c0);
-                    const int ncol = d - c0 < BN ? d - c0 : BN;  // a multiple of 32
+                if (row < nq && c0 + col0 < d) {  // d - c0 is a multiple of 32
+                    float4 *o = reinterpret_cast<float4 *>(out + (size_t)row * d + c0 + col0);
 #pragma unroll
-                    for (int j = 0; j < BN / 4; ++j)
-                        if (4 * j < ncol)
-                            o[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+                    for (int j = 0; j < kDrainCols / 4; ++j)
+                        o[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
                 }
             }
         }
@@ -328,14 +330,36 @@ __global__ void split_tf32_kernel(const float *__restrict__ x, float *__restrict
     }
 }
 
-// The canonical rotated coordinate of one row, by one thread: chunk chains
-// s_c (32 fmaf from 0) four at a time for instruction-level parallelism,
-// their sums added to the total in order c = 0, 1, ...
-__device__ __forceinline__ float chunk_chain(const float4 *__restrict__ r4, const float4 *__restrict__ q4) {
+constexpr int kMaxD = 2048;
+constexpr int kQxWarps = 4;
+constexpr int kPadChunk = 36;  // floats per 32-float chunk in shared memory: 144 B, conflict-free float4 reads
+
+// Per-warp shared memory of the exact pass: the query and one row of P^-1,
+// chunk c at [c * kPadChunk, +32).
+struct QxLayout {
+    size_t q, row, warp;
+    __host__ __device__ explicit QxLayout(int d) {
+        const size_t chunks = (size_t)(d / 32) * kPadChunk * 4;
+        q = 0;
+        row = chunks;
+        warp = 2 * chunks;
+    }
+};
+
+// d floats from global (16-byte aligned) into the padded chunk layout.
+__device__ __forceinline__ void stage_padded(float *dst, const float *__restrict__ src, int d, int lane) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    for (int i = lane; i < d / 4; i += 32)
+        *reinterpret_cast<float4 *>(dst + (i >> 3) * kPadChunk + (i & 7) * 4) = __ldg(s4 + i);
+}
+
+// s_c = fmaf chain over the 32 columns of chunk c, from 0.
+__device__ __forceinline__ float chunk_chain(const float *row, const float *q) {
     float s = 0.0f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const float4 r = __ldg(r4 + j), v = q4[j];
+        const float4 r = *reinterpret_cast<const float4 *>(row + 4 * j);
+        const float4 v = *reinterpret_cast<const float4 *>(q + 4 * j);
         s = __fmaf_rn(r.x, v.x, s);
         s = __fmaf_rn(r.y, v.y, s);
         s = __fmaf_rn(r.z, v.z, s);
@@ -344,58 +368,25 @@ __device__ __forceinline__ float chunk_chain(const float4 *__restrict__ r4, cons
     return s;
 }
 
-__device__ float canonical_coord(const float *__restrict__ row, const float *q, int d) {
-    const float4 *r4 = reinterpret_cast<const float4 *>(row);
-    const float4 *q4 = reinterpret_cast<const float4 *>(q);
+// The canonical rotated coordinate i, by the whole warp: the row is staged
+// (coalesced), lane c runs chunk c (and c + 32), and every lane adds the
+// chunk sums to the total in order c = 0, 1, ...; all lanes return it.
+__device__ float warp_canonical(const float *__restrict__ rot, int i, const float *qpad, float *rowpad, int d,
+                                int lane) {
     const int nc = d / 32;
+    __syncwarp();  // the previous call's reads of rowpad are done
+    stage_padded(rowpad, rot + (size_t)i * d, d, lane);
+    __syncwarp();
+    const float s0 = lane < nc ? chunk_chain(rowpad + lane * kPadChunk, qpad + lane * kPadChunk) : 0.0f;
+    const float s1 =
+        lane + 32 < nc ? chunk_chain(rowpad + (lane + 32) * kPadChunk, qpad + (lane + 32) * kPadChunk) : 0.0f;
     float tot = 0.0f;
-    int c = 0;
-    for (; c + 4 <= nc; c += 4) {
-        float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const float4 r = __ldg(r4 + 8 * (c + t) + j), v = q4[8 * (c + t) + j];
-                s[t] = __fmaf_rn(r.x, v.x, s[t]);
-                s[t] = __fmaf_rn(r.y, v.y, s[t]);
-                s[t] = __fmaf_rn(r.z, v.z, s[t]);
-                s[t] = __fmaf_rn(r.w, v.w, s[t]);
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) tot = __fadd_rn(tot, s[t]);
-    }
-    for (; c < nc; ++c) tot = __fadd_rn(tot, chunk_chain(r4 + 8 * c, q4 + 8 * c));
+#pragma unroll 8
+    for (int c = 0; c < nc; ++c) tot = __fadd_rn(tot, __shfl_sync(0xFFFFFFFFu, c < 32 ? s0 : s1, c & 31));
     return tot;
 }
 
-constexpr int kMaxD = 2048;
-constexpr int kQxWarps = 4;
-
-// Per-warp shared memory of the exact pass: the query, its rotated
-// coordinates, the list of coordinates to recompute and their exact flags.
-struct QxLayout {
-    size_t q, x, list, exact, warp;
-    __host__ __device__ explicit QxLayout(int d) {
-        q = 0;
-        x = q + 4 * (size_t)d;
-        list = x + 4 * (size_t)d;
-        exact = list + 2 * (size_t)d;
-        warp = (exact + 4 * (size_t)(d / 32) + 15) & ~(size_t)15;
-    }
-};
-
-// Recompute the listed coordinates, one per lane, and mark them exact.
-__device__ __forceinline__ void recompute_listed(const float *__restrict__ rot, const float *qs, float *xs,
-                                                 const uint16_t *list, uint32_t *ex, int n, int d, int lane) {
-    for (int r = lane; r < n; r += 32) {
-        const int i = list[r];
-        xs[i] = canonical_coord(rot + (size_t)i * d, qs, d);
-        atomicOr(&ex[i >> 5], 1u << (i & 31));
-    }
-    __syncwarp();
-}
+constexpr int kMaxWords = kMaxD / 32;
 
 // One warp per query.  qa = the tensor-core q'; err_scale * ||q|| bounds
 // |qa_i - canonical_i| for every i.  Writes planes (per word w the four
@@ -410,54 +401,52 @@ __global__ void __launch_bounds__(kQxWarps * 32)
     const int qi = blockIdx.x * kQxWarps + wib;
     if (qi >= nq) return;
     const QxLayout L(d);
-    unsigned char *base = qxsm + wib * L.warp;
-    float *qs = reinterpret_cast<float *>(base + L.q);
-    float *xs = reinterpret_cast<float *>(base + L.x);
-    uint16_t *list = reinterpret_cast<uint16_t *>(base + L.list);
-    uint32_t *ex = reinterpret_cast<uint32_t *>(base + L.exact);
+    float *qpad = reinterpret_cast<float *>(qxsm + wib * L.warp + L.q);
+    float *rowpad = reinterpret_cast<float *>(qxsm + wib * L.warp + L.row);
     const int nw = d / 32;
     const float *qq = q + (size_t)qi * d;
     const float *qr = qa + (size_t)qi * d;
+    stage_padded(qpad, qq, d, lane);
+    float x[kMaxWords];
+    uint64_t exact = 0;  // bit w: x[w] is canonical
     float ss = 0.0f, lo = __int_as_float(0x7f800000), hi = -lo;
     for (int w = 0; w < nw; ++w) {
-        const int i = w * 32 + lane;
-        const float v = qq[i], x = qr[i];
-        qs[i] = v;
-        xs[i] = x;
+        const float v = qq[w * 32 + lane];
+        x[w] = qr[w * 32 + lane];
         ss = fmaf(v, v, ss);
-        lo = fminf(lo, x);
-        hi = fmaxf(hi, x);
+        lo = fminf(lo, x[w]);
+        hi = fmaxf(hi, x[w]);
     }
-    for (int w = lane; w < nw; w += 32) ex[w] = 0u;
     for (int o = 16; o >= 1; o >>= 1) {
         ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
         lo = fminf(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
         hi = fmaxf(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
     }
     const float err = err_scale * sqrtf(ss) + 1e-30f;
+    int nrec = 0;
     // candidates for the minimum and the maximum (within 2 err of the
     // tensor-core extremes): recompute them
-    int n = 0;
     for (int w = 0; w < nw; ++w) {
-        const int i = w * 32 + lane;
-        const bool f = xs[i] <= lo + 2.0f * err || xs[i] >= hi - 2.0f * err;
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, f);
-        if (f) list[n + __popc(m & ((1u << lane) - 1u))] = (uint16_t)i;
-        n += __popc(m);
+        uint32_t m = __ballot_sync(0xFFFFFFFFu, x[w] <= lo + 2.0f * err || x[w] >= hi - 2.0f * err);
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            const float v = warp_canonical(rot, w * 32 + l, qpad, rowpad, d, lane);
+            if (lane == l) {
+                x[w] = v;
+                exact |= 1ull << w;
+            }
+            ++nrec;
+        }
     }
-    __syncwarp();
-    recompute_listed(rot, qs, xs, list, ex, n, d, lane);
-    int nrec = n;
     // exact v_l, v_r over the recomputed candidates: the same comparisons
     // as the canonical quantizer
     float vl = __int_as_float(0x7f800000), vr = -vl;
-    for (int w = 0; w < nw; ++w) {
-        const int i = w * 32 + lane;
-        if (ex[w] >> lane & 1u) {
-            vl = xs[i] < vl ? xs[i] : vl;
-            vr = xs[i] > vr ? xs[i] : vr;
+    for (int w = 0; w < nw; ++w)
+        if (exact >> w & 1ull) {
+            vl = x[w] < vl ? x[w] : vl;
+            vr = x[w] > vr ? x[w] : vr;
         }
-    }
     for (int o = 16; o >= 1; o >>= 1) {
         const float a = __shfl_xor_sync(0xFFFFFFFFu, vl, o), b = __shfl_xor_sync(0xFFFFFFFFu, vr, o);
         vl = a < vl ? a : vl;
@@ -467,27 +456,26 @@ __global__ void __launch_bounds__(kQxWarps * 32)
     const float delta = range > 0.0f ? __fdiv_rn(range, 15.0f) : 0.0f;
     const float inv = range > 0.0f ? __fdiv_rn(15.0f, range) : 0.0f;
     const float margin = err * inv * 1.01f + 1e-4f;  // in units of the code
-    // coordinates within the margin of an integer boundary (1 .. 15)
-    n = 0;
-    if (range > 0.0f) {
-        for (int w = 0; w < nw; ++w) {
-            const int i = w * 32 + lane;
-            const float y = __fadd_rn(__fmul_rn(__fsub_rn(xs[i], vl), inv), 0.5f);
-            const float nearest = fminf(fmaxf(rintf(y), 1.0f), 15.0f);
-            const bool f = !(ex[w] >> lane & 1u) && fabsf(y - nearest) <= margin;
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, f);
-            if (f) list[n + __popc(m & ((1u << lane) - 1u))] = (uint16_t)i;
-            n += __popc(m);
-        }
-        __syncwarp();
-        recompute_listed(rot, qs, xs, list, ex, n, d, lane);
-        nrec += n;
-    }
     int sq = 0;
     for (int w = 0; w < nw; ++w) {
+        float y = 0.0f;
+        bool redo = false;
+        if (range > 0.0f) {
+            y = __fadd_rn(__fmul_rn(__fsub_rn(x[w], vl), inv), 0.5f);
+            // an integer boundary (1 .. 15) within the margin: decide exactly
+            const float nearest = fminf(fmaxf(rintf(y), 1.0f), 15.0f);
+            redo = !(exact >> w & 1ull) && fabsf(y - nearest) <= margin;
+        }
+        uint32_t m = __ballot_sync(0xFFFFFFFFu, redo);
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            const float v = warp_canonical(rot, w * 32 + l, qpad, rowpad, d, lane);
+            if (lane == l) y = __fadd_rn(__fmul_rn(__fsub_rn(v, vl), inv), 0.5f);
+            ++nrec;
+        }
         int t = 0;
         if (range > 0.0f) {
-            const float y = __fadd_rn(__fmul_rn(__fsub_rn(xs[w * 32 + lane], vl), inv), 0.5f);
             t = __float2int_rz(y);
             t = t > 15 ? 15 : t;
         }
