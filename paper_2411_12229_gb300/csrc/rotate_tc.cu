@@ -305,8 +305,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (row < nq && c0 + col0 < d) {  // d - c0 is a multiple of 32
                     float4 *o = reinterpret_cast<float4 *>(out + (size_t)row * d + c0 + col0);
 #pragma unroll
-                    for (int j = 0; j < kDrainCols / 4; ++j)
-                        o[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+                    for (int j = 0; j < kDrainCols / 4; ++j)  // streaming stores: read once by the exact pass
+                        __stcs(o + j, make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]));
                 }
             }
         }
@@ -346,11 +346,22 @@ struct QxLayout {
     }
 };
 
-// d floats from global (16-byte aligned) into the padded chunk layout.
+// d floats from global (16-byte aligned) into the padded chunk layout; the
+// loads of a batch are all issued before its stores.
 __device__ __forceinline__ void stage_padded(float *dst, const float *__restrict__ src, int d, int lane) {
     const float4 *s4 = reinterpret_cast<const float4 *>(src);
-    for (int i = lane; i < d / 4; i += 32)
-        *reinterpret_cast<float4 *>(dst + (i >> 3) * kPadChunk + (i & 7) * 4) = __ldg(s4 + i);
+    const int n4 = d / 4;
+    for (int i0 = lane; i0 < n4; i0 += 32 * 8) {
+        float4 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (i0 + 32 * j < n4) v[j] = __ldg(s4 + i0 + 32 * j);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int i = i0 + 32 * j;
+            if (i < n4) *reinterpret_cast<float4 *>(dst + (i >> 3) * kPadChunk + (i & 7) * 4) = v[j];
+        }
+    }
 }
 
 // s_c = fmaf chain over the 32 columns of chunk c, from 0.
@@ -407,15 +418,24 @@ __global__ void __launch_bounds__(kQxWarps * 32)
     const float *qq = q + (size_t)qi * d;
     const float *qr = qa + (size_t)qi * d;
     stage_padded(qpad, qq, d, lane);
-    float x[kMaxWords];
-    uint64_t exact = 0;  // bit w: x[w] is canonical
+    float x[kMaxWords];  // coordinate 32w + lane
     float ss = 0.0f, lo = __int_as_float(0x7f800000), hi = -lo;
-    for (int w = 0; w < nw; ++w) {
-        const float v = qq[w * 32 + lane];
-        x[w] = qr[w * 32 + lane];
-        ss = fmaf(v, v, ss);
-        lo = fminf(lo, x[w]);
-        hi = fmaxf(hi, x[w]);
+    for (int w0 = 0; w0 < nw; w0 += 8) {  // batches of loads in flight together
+        float vq[8], vx[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (w0 + j < nw) {
+                vq[j] = __ldcs(qq + (w0 + j) * 32 + lane);  // streamed once: keep P^-1 in L2
+                vx[j] = __ldcs(qr + (w0 + j) * 32 + lane);
+            }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (w0 + j < nw) {
+                x[w0 + j] = vx[j];
+                ss = fmaf(vq[j], vq[j], ss);
+                lo = fminf(lo, vx[j]);
+                hi = fmaxf(hi, vx[j]);
+            }
     }
     for (int o = 16; o >= 1; o >>= 1) {
         ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
@@ -423,34 +443,25 @@ __global__ void __launch_bounds__(kQxWarps * 32)
         hi = fmaxf(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
     }
     const float err = err_scale * sqrtf(ss) + 1e-30f;
-    int nrec = 0;
     // candidates for the minimum and the maximum (within 2 err of the
-    // tensor-core extremes): recompute them
-    for (int w = 0; w < nw; ++w) {
-        uint32_t m = __ballot_sync(0xFFFFFFFFu, x[w] <= lo + 2.0f * err || x[w] >= hi - 2.0f * err);
-        while (m) {
-            const int l = __ffs(m) - 1;
-            m &= m - 1;
+    // tensor-core extremes), one bit per word in each lane
+    uint64_t exact = 0;
+    for (int w = 0; w < nw; ++w)
+        if (x[w] <= lo + 2.0f * err || x[w] >= hi - 2.0f * err) exact |= 1ull << w;
+    // recompute them (the extremes are among them); every lane sees each
+    // recomputed value, so v_l and v_r come out warp-uniform
+    float vl = __int_as_float(0x7f800000), vr = -vl;
+    int nrec = 0;
+    for (uint32_t owners = __ballot_sync(0xFFFFFFFFu, exact != 0); owners; owners &= owners - 1) {
+        const int l = __ffs(owners) - 1;
+        for (uint64_t cm = __shfl_sync(0xFFFFFFFFu, exact, l); cm; cm &= cm - 1) {
+            const int w = __ffsll((long long)cm) - 1;
             const float v = warp_canonical(rot, w * 32 + l, qpad, rowpad, d, lane);
-            if (lane == l) {
-                x[w] = v;
-                exact |= 1ull << w;
-            }
+            if (lane == l) x[w] = v;
+            vl = v < vl ? v : vl;
+            vr = v > vr ? v : vr;
             ++nrec;
         }
-    }
-    // exact v_l, v_r over the recomputed candidates: the same comparisons
-    // as the canonical quantizer
-    float vl = __int_as_float(0x7f800000), vr = -vl;
-    for (int w = 0; w < nw; ++w)
-        if (exact >> w & 1ull) {
-            vl = x[w] < vl ? x[w] : vl;
-            vr = x[w] > vr ? x[w] : vr;
-        }
-    for (int o = 16; o >= 1; o >>= 1) {
-        const float a = __shfl_xor_sync(0xFFFFFFFFu, vl, o), b = __shfl_xor_sync(0xFFFFFFFFu, vr, o);
-        vl = a < vl ? a : vl;
-        vr = b > vr ? b : vr;
     }
     const float range = __fsub_rn(vr, vl);
     const float delta = range > 0.0f ? __fdiv_rn(range, 15.0f) : 0.0f;
@@ -466,10 +477,8 @@ __global__ void __launch_bounds__(kQxWarps * 32)
             const float nearest = fminf(fmaxf(rintf(y), 1.0f), 15.0f);
             redo = !(exact >> w & 1ull) && fabsf(y - nearest) <= margin;
         }
-        uint32_t m = __ballot_sync(0xFFFFFFFFu, redo);
-        while (m) {
+        for (uint32_t m = __ballot_sync(0xFFFFFFFFu, redo); m; m &= m - 1) {
             const int l = __ffs(m) - 1;
-            m &= m - 1;
             const float v = warp_canonical(rot, w * 32 + l, qpad, rowpad, d, lane);
             if (lane == l) y = __fadd_rn(__fmul_rn(__fsub_rn(v, vl), inv), 0.5f);
             ++nrec;
