@@ -189,6 +189,10 @@ class Index:
         torch.cuda.current_stream().synchronize()
         return ih.numpy(), dh.numpy()
 
+    def host_pipeline(self, nq: int, k: int, ef: int, depth: int = 2, **kw) -> "HostPipeline":
+        """A pipelined end-to-end search over host batches of nq queries."""
+        return HostPipeline(self, nq, k, ef, depth=depth, **kw)
+
     # ------------------------------------------------------------------ test hooks
     def prepare_queries(self, queries: torch.Tensor, stream=None):
         nq = queries.shape[0]
@@ -233,3 +237,79 @@ class Index:
         s = C.c_uint32()
         B.check(B.lib().sqg_get_status(self._h, _stream_ptr(stream), C.byref(s)), "sqg_get_status")
         return int(s.value)
+
+
+class HostPipeline:
+    """End-to-end search over a sequence of host batches of one shape: batch
+    i is copied in from pinned host memory, searched and its (ids, dists)
+    copied back on stream i % depth, so one batch's copies overlap another's
+    search.  Each slot owns its device buffers, workspace and pinned result
+    buffers; nothing allocates or waits on the device inside submit() except
+    for the slot being reused.
+
+        pipe = ix.host_pipeline(nq, k, ef)
+        for qh in pinned_batches:        # (nq, d) float32, pinned
+            done = pipe.submit(qh)       # results of an earlier batch, or None
+        rest = pipe.drain()              # the remaining results, in order
+    """
+
+    class _Slot:
+        pass
+
+    def __init__(self, ix: Index, nq: int, k: int, ef: int, depth: int = 2, **kw):
+        if depth < 1:
+            raise ValueError("depth must be >= 1")
+        self.ix, self.nq, self.k, self.ef, self.kw = ix, int(nq), int(k), int(ef), dict(kw)
+        dev = torch.device("cuda", ix.device)
+        ws_bytes = ix.workspace_size(nq, k, ef, **kw)
+        self.slots, self.order, self.count = [], [], 0
+        for _ in range(depth):
+            sl = HostPipeline._Slot()
+            sl.stream = torch.cuda.Stream(device=dev)
+            sl.qd = torch.empty((nq, ix.d), dtype=torch.float32, device=dev)
+            sl.kt = torch.full((nq,), self.k, dtype=torch.int32, device=dev)
+            sl.et = torch.full((nq,), self.ef, dtype=torch.int32, device=dev)
+            sl.ids = torch.empty(nq * self.k, dtype=torch.int32, device=dev)
+            sl.dists = torch.empty(nq * self.k, dtype=torch.float32, device=dev)
+            sl.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+            sl.ih = torch.empty((nq, self.k), dtype=torch.int32).pin_memory()
+            sl.dh = torch.empty((nq, self.k), dtype=torch.float32).pin_memory()
+            sl.event = torch.cuda.Event()
+            sl.busy = False
+            self.slots.append(sl)
+        torch.cuda.synchronize(dev)
+
+    def _collect(self, sl):
+        sl.event.synchronize()
+        sl.busy = False
+        return sl.ih.numpy().copy(), sl.dh.numpy().copy()
+
+    def submit(self, qh: torch.Tensor):
+        """Start one batch (a pinned (nq, d) float32 host tensor, left
+        untouched until its results come back); returns the (ids, dists) of
+        the batch submitted `depth` calls earlier, or None."""
+        if qh.shape != (self.nq, self.ix.d) or qh.dtype != torch.float32 or qh.is_cuda:
+            raise ValueError(f"expected a host float32 tensor of shape ({self.nq}, {self.ix.d})")
+        sl = self.slots[self.count % len(self.slots)]
+        done = self._collect(sl) if sl.busy else None
+        with torch.cuda.stream(sl.stream):
+            sl.qd.copy_(qh, non_blocking=True)
+            self.ix.search(sl.qd, sl.kt, sl.et, out=(sl.ids, sl.dists), workspace=sl.ws, stream=sl.stream,
+                           max_k=self.k, max_ef=self.ef, **self.kw)
+            sl.ih.copy_(sl.ids.view(self.nq, self.k), non_blocking=True)
+            sl.dh.copy_(sl.dists.view(self.nq, self.k), non_blocking=True)
+            sl.event.record(sl.stream)
+        sl.busy = True
+        self.count += 1
+        return done
+
+    def drain(self) -> list:
+        """The results of every batch still in flight, oldest first."""
+        out = []
+        n = len(self.slots)
+        for j in range(n):
+            sl = self.slots[(self.count + j) % n]
+            if sl.busy:
+                out.append(self._collect(sl))
+        return out
+

@@ -45,3 +45,22 @@ def test_graph_captured_batch_replays_the_search(tiny_index, oracle_mod):
         ids = ids.cpu().numpy().view(np.uint32)
         for i in range(nq):
             np.testing.assert_array_equal(ids[off[i]:off[i + 1]], O.search(q[a + i], int(k[i]), int(ef[i]))[0])
+
+
+def test_host_pipeline_returns_each_batch_in_order(tiny_index, oracle_mod):
+    """The pipelined host-to-host API: batches come back in submission
+    order, each equal to the direct search of its queries."""
+    from paper_2411_12229_gb300.api import Index
+    p, x, q = tiny_index
+    ix = Index(p, 0)
+    nq = 16
+    batches = [torch.from_numpy(np.ascontiguousarray(q[i * nq:(i + 1) * nq])).pin_memory() for i in range(4)]
+    pipe = ix.host_pipeline(nq, 10, 48, depth=2)
+    got = [r for r in (pipe.submit(b) for b in batches) if r is not None]
+    got += pipe.drain()
+    assert len(got) == len(batches)
+    for b, (ids, dists) in zip(batches, got):
+        ref_ids, ref_d = ix.search(b.cuda(), 10, 48)
+        np.testing.assert_array_equal(ids, ref_ids.cpu().numpy())
+        np.testing.assert_array_equal(dists, ref_d.cpu().numpy())
+    assert pipe.drain() == []
