@@ -56,7 +56,7 @@ struct SearchArgs {
     uint32_t *ghash;      // per-warp full tables in global memory when shash_bits < hash_bits
     float eps0;
     int multi_estimate;
-    const float *mlp;
+    const float *mlp;       // the stop network with W1, W2 transposed to [in][out], or null
     float stop_logit;
     int stop_every;
     int prefetch;       // 1: next block only; 2: also L2-prefetch the runner-up
@@ -379,8 +379,9 @@ struct StopState {
 };
 __device__ __forceinline__ float clamp8(float x) { return x < -8.0f ? -8.0f : (x > 8.0f ? 8.0f : x); }
 
-// MLP 16 -> 64 -> 64 -> 1 on one warp; weights in shared memory, layer
-// matrices stored transposed ([in][out]) for conflict-free reads.  Hidden
+// MLP 16 -> 64 -> 64 -> 1 on one warp; weights in global memory (the same
+// 21 KB for every warp, so they stay in L1), layer matrices stored
+// transposed ([in][out]) so each input's weights are one coalesced row.  Hidden
 // neuron o is an fmaf chain over its inputs in order starting from its bias;
 // the output adds p_l = fmaf(W3[l+32], h[l+32], W3[l] h[l]) by xor butterfly,
 // then b3.
@@ -391,27 +392,27 @@ __device__ __forceinline__ float mlp_logit_warp(const float *w, const float (&f)
     const float *b2 = W2t + 64 * 64;              // [64]
     const float *W3 = b2 + 64;                    // [64]
     const float *b3 = W3 + 64;                    // [1]
-    float ha = b1[lane], hb = b1[lane + 32];
+    float ha = __ldg(b1 + lane), hb = __ldg(b1 + lane + 32);
 #pragma unroll
     for (int i = 0; i < SQG_MLP_IN; ++i) {
-        ha = __fmaf_rn(W1t[i * 64 + lane], f[i], ha);
-        hb = __fmaf_rn(W1t[i * 64 + lane + 32], f[i], hb);
+        ha = __fmaf_rn(__ldg(W1t + i * 64 + lane), f[i], ha);
+        hb = __fmaf_rn(__ldg(W1t + i * 64 + lane + 32), f[i], hb);
     }
     ha = ha > 0.0f ? ha : 0.0f;
     hb = hb > 0.0f ? hb : 0.0f;
-    float ga = b2[lane], gb = b2[lane + 32];
+    float ga = __ldg(b2 + lane), gb = __ldg(b2 + lane + 32);
 #pragma unroll 8
     for (int i = 0; i < 64; ++i) {
         float hi = __shfl_sync(kFull, i < 32 ? ha : hb, i & 31);
-        ga = __fmaf_rn(W2t[i * 64 + lane], hi, ga);
-        gb = __fmaf_rn(W2t[i * 64 + lane + 32], hi, gb);
+        ga = __fmaf_rn(__ldg(W2t + i * 64 + lane), hi, ga);
+        gb = __fmaf_rn(__ldg(W2t + i * 64 + lane + 32), hi, gb);
     }
     ga = ga > 0.0f ? ga : 0.0f;
     gb = gb > 0.0f ? gb : 0.0f;
-    float p = __fmaf_rn(W3[lane + 32], gb, __fmul_rn(W3[lane], ga));
+    float p = __fmaf_rn(__ldg(W3 + lane + 32), gb, __fmul_rn(__ldg(W3 + lane), ga));
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) p = __fadd_rn(p, __shfl_xor_sync(kFull, p, o));
-    return __fadd_rn(p, b3[0]);
+    return __fadd_rn(p, __ldg(b3 + 0));
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -432,26 +433,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
     const uint32_t R = a.R, d = a.d, nch = d / 4;
     const float inv_R = __fdiv_rn(1.0f, (float)R);
 
-    float *wts = reinterpret_cast<float *>(smem);
-    if (a.mlp) {  // transpose W1, W2 into [in][out]
-        const float *W1 = a.mlp, *b1 = W1 + 64 * SQG_MLP_IN, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64;
-        for (int i = threadIdx.x; i < 64 * SQG_MLP_IN; i += blockDim.x) {
-            int o = i / SQG_MLP_IN, c = i % SQG_MLP_IN;
-            wts[c * 64 + o] = W1[i];
-        }
-        float *q = wts + 64 * SQG_MLP_IN;
-        for (int i = threadIdx.x; i < 64; i += blockDim.x) q[i] = b1[i];
-        q += 64;
-        for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
-            int o = i / 64, c = i % 64;
-            q[c * 64 + o] = W2[i];
-        }
-        q += 64 * 64;
-        for (int i = threadIdx.x; i < 64; i += blockDim.x) q[i] = b2[i];
-        q += 64;
-        for (int i = threadIdx.x; i < 65; i += blockDim.x) q[i] = W3[i];  // W3 and b3
-    }
-    __syncthreads();
+    const float *wts = a.mlp;  // the stop network, W1 and W2 transposed (global, L1-cached)
 
     unsigned char *ws = smem + a.cta_bytes + (size_t)(warp * V + team) * a.warp_bytes;
     unsigned char *buf[2] = {ws + a.o_buf0, ws + a.o_buf1};

@@ -103,6 +103,23 @@ __global__ void plan_kernel(const int32_t *k, const int32_t *ef, int nq, long lo
     }
 }
 
+// The stop network's parameters (W1 [64][16], b1, W2 [64][64], b2, W3, b3)
+// with W1 and W2 transposed to [in][out], so a warp reads a layer's weights
+// for one input as one coalesced row.
+__global__ void mlp_transpose_kernel(const float *__restrict__ src, float *__restrict__ dst) {
+    const float *W1 = src, *b1 = W1 + 64 * SQG_MLP_IN, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64;
+    float *t = dst;
+    for (int i = threadIdx.x; i < 64 * SQG_MLP_IN; i += blockDim.x) t[(i % SQG_MLP_IN) * 64 + i / SQG_MLP_IN] = W1[i];
+    t += 64 * SQG_MLP_IN;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) t[i] = b1[i];
+    t += 64;
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) t[(i % 64) * 64 + i / 64] = W2[i];
+    t += 64 * 64;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) t[i] = b2[i];
+    t += 64;
+    for (int i = threadIdx.x; i < 65; i += blockDim.x) t[i] = W3[i];  // W3 and b3
+}
+
 // q' = P^-1 q for a batch (Eq. (4)) in the canonical chunked order:
 // out[r][i] = (((0 + s_0) + s_1) + ...) over the d/32 chunks, s_c the fmaf
 // chain of rot[i][j] * q[r][j] over j = 32c .. 32c+31 from 0.  64 x 64 output
@@ -245,7 +262,7 @@ struct LaunchPlan {
     SearchArgs a;  // layout fields filled in
     bool ghash;
     // workspace layout
-    size_t ws_offsets, ws_qrot, ws_queue, ws_maxes, ws_stats, ws_ghash, ws_planes, ws_scal, ws_total;
+    size_t ws_offsets, ws_qrot, ws_queue, ws_maxes, ws_stats, ws_ghash, ws_planes, ws_scal, ws_mlp, ws_total;
 };
 
 int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_search_params &p, LaunchPlan &pl) {
@@ -287,7 +304,7 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     pl.ghash = a.shash_bits < bits;
     a.o_hash = (uint32_t)o;
     const size_t warp_bytes = align_up(o + ((size_t)4 << a.shash_bits), 128);
-    const size_t cta = p.stop_mlp ? align_up(sizeof(float) * SQG_MLP_NPARAM, 128) : 0;
+    const size_t cta = 0;  // the stop network's weights are read from the workspace (L1-cached)
     int warps = p.warps_per_block > 0 ? p.warps_per_block : 4;
     warps = std::min(warps, 4);
     // one slot of warp_bytes per query in flight: V per warp
@@ -317,6 +334,9 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     // the exactly quantized query after a tensor-core rotation
     pl.ws_planes = w; w = align_up(w + 16 * (size_t)(d / 32) * (size_t)std::max(nq, 1), 256);
     pl.ws_scal = w; w = align_up(w + 16 * (size_t)std::max(nq, 1), 256);
+    // the stop network, its two weight matrices transposed to [in][out]
+    pl.ws_mlp = w;
+    if (p.stop_mlp) w = align_up(w + sizeof(float) * SQG_MLP_NPARAM, 256);
     pl.ws_total = w;
     return SQG_OK;
 }
@@ -589,7 +609,12 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     a.ghash = pl.ghash ? reinterpret_cast<uint32_t *>(ws + pl.ws_ghash) : nullptr;
     a.eps0 = p.eps0;
     a.multi_estimate = p.multi_estimate;
-    a.mlp = p.stop_mlp;
+    a.mlp = nullptr;
+    if (p.stop_mlp) {
+        float *t = reinterpret_cast<float *>(ws + pl.ws_mlp);
+        mlp_transpose_kernel<<<1, 256, 0, stream>>>(p.stop_mlp, t);
+        a.mlp = t;
+    }
     a.stop_logit = p.stop_logit;
     a.stop_every = p.stop_every;
     a.prefetch = p.prefetch == 0 ? 1 : p.prefetch;

@@ -36,8 +36,11 @@ def _sp(stream=None) -> int:
     return int((stream or torch.cuda.current_stream()).cuda_stream)
 
 
-def collect(ix, queries: np.ndarray, gt: np.ndarray, k: int, ef_cap: int, every: int, chunk: int = 8192):
-    """Features and labels from traces of the plain search at ef_cap."""
+def collect(ix, queries: np.ndarray, gt: np.ndarray, k: int, ef_cap: int, every: int, chunk: int = 8192,
+            target_hits: np.ndarray | None = None):
+    """Features and labels from traces of the plain search at ef_cap.  A row
+    is positive once the result holds as many true top-k ids as
+    `target_hits` (per query; default: what the traced search ends with)."""
     cap = max(1, (4 * ef_cap + 64) // every + 1)
     feats, labels, qidx = [], [], []
     gt_d = torch.from_numpy(np.ascontiguousarray(gt[:, :k], dtype=np.int32)).cuda()
@@ -49,6 +52,8 @@ def collect(ix, queries: np.ndarray, gt: np.ndarray, k: int, ef_cap: int, every:
         f, h, n = f.cpu().numpy(), h.cpu().numpy(), n.cpu().numpy()
         for i in range(b - a):
             final = len(np.intersect1d(ids[i], gt[a + i, :k]))
+            if target_hits is not None:
+                final = min(final, int(target_hits[a + i]))
             m = n[i]
             if m == 0:
                 continue
@@ -133,14 +138,28 @@ def evaluate(ix, queries: torch.Tensor, gt: np.ndarray, k: int, ef: int, model: 
     return recall(ids.cpu().numpy(), gt, k), qps, float(st[:, 0].float().mean())
 
 
+def hits_of(ids: np.ndarray, gt: np.ndarray, k: int) -> np.ndarray:
+    return np.array([len(np.intersect1d(ids[i], gt[i, :k])) for i in range(ids.shape[0])], dtype=np.int32)
+
+
 def fit(ix, train_q: np.ndarray, train_gt: np.ndarray, k: int, ef_cap: int, target: float, *, every: int = 2,
-        val_frac: float = 0.2, steps: int = 3000, seed: int = 0, log=None) -> StopModel:
+        ef_ref: int | None = None, val_frac: float = 0.2, steps: int = 3000, seed: int = 0, log=None) -> StopModel:
     """Trace, train, then pick the stop threshold on held-out queries: the
-    most aggressive logit whose recall still reaches `target`."""
+    most aggressive logit whose recall still reaches `target`.  With ef_ref,
+    a row is positive once the traced search (at ef_cap) holds as many true
+    top-k ids as the plain search at ef_ref ends with for that query, so the
+    stop learns to match the smaller beam's result early and keeps the
+    larger beam for the queries that need it."""
     nv = max(1, int(train_q.shape[0] * val_frac))
     tq, tg = train_q[nv:], train_gt[nv:]
     vq, vg = train_q[:nv], train_gt[:nv]
-    f, y, _ = collect(ix, tq, tg, k, ef_cap, every)
+    th = None
+    if ef_ref is not None:
+        th = np.empty(tq.shape[0], dtype=np.int32)
+        for a in range(0, tq.shape[0], 8192):
+            ids, _ = ix.search(torch.from_numpy(np.ascontiguousarray(tq[a:a + 8192])).cuda(), k, ef_ref)
+            th[a:a + 8192] = hits_of(ids.cpu().numpy(), tg[a:a + 8192], k)
+    f, y, _ = collect(ix, tq, tg, k, ef_cap, every, target_hits=th)
     P = train(f, y, steps=steps, seed=seed, log=log)
     model = StopModel(P, 0.0, every, ef_cap, dict(rows=int(f.shape[0]), positive=float(y.mean())))
     vqd = torch.from_numpy(np.ascontiguousarray(vq)).cuda()
