@@ -248,20 +248,21 @@ def learned_stop_comparison(args, w, ix, qd, gt_ids, sweep, ef_sel, device):
     t0 = time.time()
     tq = synth.train_queries(w, args.stop_train)
     tg, _ = E.ground_truth(synth.base(w), tq, 10, device=device)
-    cap = 2 * ef_sel
     rows, models = [], {}
-    for every in (4, 8):  # evaluation period: the network's cost against how early it can stop
+    # (evaluation period, beam cap): the network's cost against how early it
+    # can stop; a cap above the plain ef lets hard queries search further
+    for every, cap in ((8, ef_sel), (4, 2 * ef_sel), (8, 2 * ef_sel)):
         model = L.fit(ix, tq, tg, 10, cap, args.target, every=every, ef_ref=ef_sel, steps=3000)
-        models[every] = model.logit
+        models[f"every{every}_cap{cap}"] = model.logit
         for thr in sorted({model.logit, model.logit - 0.5, model.logit + 0.5, model.logit + 1.0}):
             r, qps, hops = L.evaluate(ix, qd, gt_ids, 10, cap, model, logit=thr, reps=5)
-            rows.append({"every": every, "logit": thr, "recall": round(r, 4), "qps": round(qps),
+            rows.append({"every": every, "ef_cap": cap, "logit": thr, "recall": round(r, 4), "qps": round(qps),
                          "hops": round(hops, 2)})
     ok = [x for x in rows if x["recall"] >= args.target]
     best = max(ok, key=lambda x: x["qps"]) if ok else None
     plain = next((s for s in sweep if s["recall"] >= args.target), None)
     log(f"learned stop in {time.time() - t0:.1f}s: {rows}")
-    return {"ef_cap": cap, "every": [4, 8], "label": f"hits of the plain search at ef {ef_sel}",
+    return {"variants": list(models), "label": f"hits of the plain search at ef {ef_sel}",
             "train_queries": int(args.stop_train), "calibrated_logit": models,
             "points": rows, "best_at_target": best,
             "plain_at_target": {k: plain[k] for k in ("ef", "recall", "qps", "hops")} if plain else None,
