@@ -288,10 +288,9 @@ __device__ __forceinline__ QuerySide quantize_warp(const float *qr, uint32_t d, 
 // at least T combine registers, the smaller ones shuffle, and every step
 // adds the same two partials as the 32-lane order, so the result is equal.
 template <int CH, int T>
-__device__ __forceinline__ float exact_dist_team(const float4 (&qv)[32 / T][CH], const float *raw, uint32_t nch,
-                                                 const Team<T> &tm) {
+__device__ __forceinline__ void exact_partial(const float4 (&qv)[32 / T][CH], const float *raw, uint32_t nch,
+                                              const Team<T> &tm, float (&acc)[32 / T]) {
     constexpr int V = 32 / T;
-    float acc[V];
     const float4 *r4 = reinterpret_cast<const float4 *>(raw);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -310,6 +309,10 @@ __device__ __forceinline__ float exact_dist_team(const float4 (&qv)[32 / T][CH],
             }
         }
     }
+}
+template <int T>
+__device__ __forceinline__ float exact_reduce(float (&acc)[32 / T], const Team<T> &tm) {
+    constexpr int V = 32 / T;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
         if (o >= T) {
@@ -325,6 +328,13 @@ __device__ __forceinline__ float exact_dist_team(const float4 (&qv)[32 / T][CH],
     }
     return acc[0];
 }
+template <int CH, int T>
+__device__ __forceinline__ float exact_dist_team(const float4 (&qv)[32 / T][CH], const float *raw, uint32_t nch,
+                                                 const Team<T> &tm) {
+    float acc[32 / T];
+    exact_partial<CH, T>(qv, raw, nch, tm, acc);
+    return exact_reduce<T>(acc, tm);
+}
 template <int CH>
 __device__ __forceinline__ float exact_dist(const float4 (&qv)[CH], const float *raw, uint32_t nch, int lane) {
     return exact_dist_team<CH, 32>(reinterpret_cast<const float4(&)[1][CH]>(qv), raw, nch, Team<32>(lane));
@@ -337,22 +347,45 @@ struct Est {
     int S;
     float est, key;
 };
-// sqrt_dc = sqrtf(dist_c), computed once per expansion (used only when eps0 != 0).
-__device__ __forceinline__ Est estimate(const unsigned char *blk, const SearchArgs &a, const uint32_t *planes,
-                                        const QuerySide &qs, uint32_t j, float dist_c, float sqrt_dc) {
+// S of neighbour j: integer, independent of dist_c, so a caller can overlap
+// it with the exact distance's butterfly.  Up to d = 256 the word loop is
+// unrolled and predicated (one basic block).
+template <int CH>
+__device__ __forceinline__ int estimate_S(const unsigned char *blk, const SearchArgs &a, const uint32_t *planes,
+                                          uint32_t j) {
     const uint32_t nw = a.d / 32, R = a.R;
     const uint32_t *codes = reinterpret_cast<const uint32_t *>(blk + a.off_codes) + j;
     int s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    if constexpr (CH <= 2) {
+#pragma unroll
+        for (uint32_t w = 0; w < 4 * CH; ++w) {
+            if (w < nw) {
+                const uint32_t c = codes[w * R];
+                const uint4 pl = reinterpret_cast<const uint4 *>(planes)[w];
+                s0 += __popc(c & pl.x);
+                s1 += __popc(c & pl.y);
+                s2 += __popc(c & pl.z);
+                s3 += __popc(c & pl.w);
+            }
+        }
+    } else {
 #pragma unroll 4
-    for (uint32_t w = 0; w < nw; ++w) {
-        uint32_t c = codes[w * R];
-        const uint4 pl = reinterpret_cast<const uint4 *>(planes)[w];
-        s0 += __popc(c & pl.x);
-        s1 += __popc(c & pl.y);
-        s2 += __popc(c & pl.z);
-        s3 += __popc(c & pl.w);
+        for (uint32_t w = 0; w < nw; ++w) {
+            const uint32_t c = codes[w * R];
+            const uint4 pl = reinterpret_cast<const uint4 *>(planes)[w];
+            s0 += __popc(c & pl.x);
+            s1 += __popc(c & pl.y);
+            s2 += __popc(c & pl.z);
+            s3 += __popc(c & pl.w);
+        }
     }
-    const int S = s0 + 2 * s1 + 4 * s2 + 8 * s3;
+    return s0 + 2 * s1 + 4 * s2 + 8 * s3;
+}
+// The estimate and key of neighbour j from its S.
+// sqrt_dc = sqrtf(dist_c), computed once per expansion (used only when eps0 != 0).
+__device__ __forceinline__ Est estimate_from_S(const unsigned char *blk, const SearchArgs &a, const QuerySide &qs,
+                                               uint32_t j, int S, float dist_c, float sqrt_dc) {
+    const uint32_t R = a.R;
     const float *fac = reinterpret_cast<const float *>(blk + a.off_factors);
     const float f_add = fac[j], f_rescale = fac[R + j];
     const int pc = (int)reinterpret_cast<const uint32_t *>(fac)[3 * R + j];
@@ -369,6 +402,10 @@ __device__ __forceinline__ Est estimate(const unsigned char *blk, const SearchAr
         e.key = __fsub_rn(e.est, __fmul_rn(a.eps0, bound));
     }
     return e;
+}
+__device__ __forceinline__ Est estimate(const unsigned char *blk, const SearchArgs &a, const uint32_t *planes,
+                                        const QuerySide &qs, uint32_t j, float dist_c, float sqrt_dc) {
+    return estimate_from_S(blk, a, qs, j, estimate_S<16>(blk, a, planes, j), dist_c, sqrt_dc);
 }
 
 // ---------------------------------------------------------------- learned stop
@@ -581,7 +618,20 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
             const unsigned char *blk = buf[cb];
 
             // ---- line 4: exact distance, implicit re-ranking
-            const float dist_c = exact_dist_team<CH, T>(qv, reinterpret_cast<const float *>(blk), nch, tm);
+            // exact distance partials, then the neighbours' integer sums S while
+            // the partials' butterfly is in flight, then the butterfly
+            float dacc[V];
+            exact_partial<CH, T>(qv, reinterpret_cast<const float *>(blk), nch, tm, dacc);
+            const uint32_t *ids = reinterpret_cast<const uint32_t *>(blk + a.off_ids);
+            int Sv[NT];
+            uint32_t cid[NT];
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                const uint32_t j = tl + T * t;
+                cid[t] = ids[j];
+                Sv[t] = estimate_S<CH>(blk, a, planes, j);
+            }
+            const float dist_c = exact_reduce<T>(dacc, tm);
             if (hops == 1 && tl == 0) beam[0].x = __float_as_uint(dist_c);
             bool improved = false;
             {
@@ -609,21 +659,18 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
             }
 
             // ---- line 5: estimates for all R neighbours from the same block
-            const uint32_t *ids = reinterpret_cast<const uint32_t *>(blk + a.off_ids);
             const bool full = m == ef;
             const uint2 we = beam[ef - 1 < m ? ef - 1 : 0];
             const float wk = __uint_as_float(we.x);
             const uint32_t wi = we.y & kIdMask;
             float ck[NT];
-            uint32_t cid[NT];
             int cpos[NT];
             bool adm[NT];
             const float sqrt_dc = a.eps0 == 0.0f ? 0.0f : __fsqrt_rn(dist_c);
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
                 const uint32_t j = tl + T * t;
-                cid[t] = ids[j];
-                const Est e = estimate(blk, a, planes, qs, j, dist_c, sqrt_dc);
+                const Est e = estimate_from_S(blk, a, qs, j, Sv[t], dist_c, sqrt_dc);
                 ck[t] = e.key;
                 // line 6: only unvisited neighbours enter; an entry that the cut
                 // to ef would drop at once is skipped early
