@@ -102,8 +102,19 @@ def ensure_index(args, w, device, rank):
         info = ib.build_index(str(idx) + ".part", base, w.degree, device=device, init="random",
                               iterations=args.build_iters, ef_build=args.ef_build, cand_k=2 * w.degree, log=log)
         os.replace(str(idx) + ".part", idx)
-        log(f"built in {time.time() - t:.1f}s {info['iterations'][-1]}")
+        secs = time.time() - t
+        log(f"built in {secs:.1f}s {info['iterations'][-1]}")
+        pathlib.Path(str(idx) + ".build.json").write_text(json.dumps(
+            {"seconds": round(secs, 1), "iterations": args.build_iters, "ef_build": args.ef_build,
+             "last_iteration": {k: (float(v) if isinstance(v, (int, float, np.floating, np.integer)) else str(v))
+                                for k, v in info["iterations"][-1].items()}}))
     return idx, gtp
+
+
+def build_record(idx):
+    """The index build's wall time, if this cache built it."""
+    p = pathlib.Path(str(idx) + ".build.json")
+    return json.loads(p.read_text()) if p.exists() else None
 
 
 def ground_truth(args, w, gtp, queries, device, world):
@@ -620,6 +631,10 @@ def main():
                "sample": f"first {done} of the {nq} queries at ef={ef_sel}, {el:.1f}s on {threads} threads"}
         same = sum(np.array_equal(ids_o[i], out[0].view(nq, k)[i].cpu().numpy().view(np.uint32)) for i in ids_o)
         cpu["ids_identical_to_gpu"] = f"{same}/{len(ids_o)}"
+        # one thread, the paper's own search protocol (a few seconds)
+        d1, e1, _ = run_oracle(idx, q, k, ef_sel, 3.0, 1, nq)
+        cpu["single_thread_value"] = round(d1 / e1, 2)
+        cpu["single_thread_sample"] = f"first {d1} queries, {e1:.1f}s on 1 thread"
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -643,6 +658,7 @@ def main():
                           for t in (0.90, 0.95, 0.99)},
         "ef_at_recall": {str(t): pick(t) for t in (0.90, 0.95, 0.99)},
         "hops_mean": round(float(hops.mean()), 2),
+        "index_build": build_record(idx),
         "learned_stop": stop_cmp,
         "sweep": sweep,
     }

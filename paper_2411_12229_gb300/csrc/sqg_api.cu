@@ -50,7 +50,9 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // ---------------------------------------------------------------- kernels
 
 // Output offsets (exclusive prefix sum of each query's slot count) and the
-// largest valid k / ef of the batch.  One block; nq is looped in tiles.
+// largest valid k / ef of the batch.  One block; each thread scans
+// kPlanItems consecutive queries of a tile, so a 10k batch takes two tiles.
+constexpr int kPlanItems = 8;
 __global__ void plan_kernel(const int32_t *k, const int32_t *ef, int nq, long long *offsets, int *maxes) {
     __shared__ long long warp_sums[kPlanThreads / 32];
     __shared__ long long carry;
@@ -59,21 +61,28 @@ __global__ void plan_kernel(const int32_t *k, const int32_t *ef, int nq, long lo
     if (tid == 0) { carry = 0; smax_k = 0; smax_ef = 0; }
     __syncthreads();
     int mk = 0, me = 0;
-    for (int base = 0; base < nq; base += kPlanThreads) {
-        const int i = base + tid;
-        long long c = 0;
-        if (i < nq) {
-            const int kk = k[i], ee = ef[i];
-            c = kk < 0 ? 0 : (kk > SQG_MAX_K ? SQG_MAX_K : kk);
-            if (kk >= 1 && kk <= SQG_MAX_K && ee >= kk && ee <= SQG_MAX_EF) {
-                mk = max(mk, kk);
-                me = max(me, ee);
+    for (int base = 0; base < nq; base += kPlanThreads * kPlanItems) {
+        const int i0 = base + tid * kPlanItems;
+        int c[kPlanItems];
+        long long tsum = 0;
+#pragma unroll
+        for (int j = 0; j < kPlanItems; ++j) {
+            const int i = i0 + j;
+            c[j] = 0;
+            if (i < nq) {
+                const int kk = k[i], ee = ef[i];
+                c[j] = kk < 0 ? 0 : (kk > SQG_MAX_K ? SQG_MAX_K : kk);
+                if (kk >= 1 && kk <= SQG_MAX_K && ee >= kk && ee <= SQG_MAX_EF) {
+                    mk = max(mk, kk);
+                    me = max(me, ee);
+                }
             }
+            tsum += c[j];
         }
-        long long x = c;  // inclusive scan within the warp
+        long long x = tsum;  // inclusive scan of the threads' sums within the warp
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            const long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) warp_sums[w] = x;
@@ -82,16 +91,20 @@ __global__ void plan_kernel(const int32_t *k, const int32_t *ef, int nq, long lo
             long long s = lane < kPlanThreads / 32 ? warp_sums[lane] : 0;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                long long y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+                const long long y = __shfl_up_sync(0xFFFFFFFFu, s, o);
                 if (lane >= o) s += y;
             }
             warp_sums[lane] = s;  // inclusive over warps
         }
         __syncthreads();
-        const long long before = carry + (w > 0 ? warp_sums[w - 1] : 0) + x - c;
-        if (i < nq) offsets[i] = before;
+        long long run = carry + (w > 0 ? warp_sums[w - 1] : 0) + x - tsum;
+#pragma unroll
+        for (int j = 0; j < kPlanItems; ++j) {
+            if (i0 + j < nq) offsets[i0 + j] = run;
+            run += c[j];
+        }
         __syncthreads();
-        if (tid == kPlanThreads - 1) carry = before + c;
+        if (tid == kPlanThreads - 1) carry = run;
         __syncthreads();
     }
     atomicMax(&smax_k, mk);
