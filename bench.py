@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-stop", action="store_true", help="skip the learned-stop comparison")
     ap.add_argument("--stop-train", type=int, default=20000, help="training queries for the learned stop")
+    ap.add_argument("--rotation", default="dense", choices=["dense", "fjlt"],
+                    help="index rotation: dense P^-1, or the fast JLT (Sec. 3.1.4; data padded to a power of 2)")
     ap.add_argument("--prep", action="store_true",
                     help="time query preparation alone (rotation + 4-bit quantization), CUDA vs tensor cores")
     return ap.parse_args()
@@ -86,7 +88,10 @@ def cache_paths(args, w):
     c = pathlib.Path(args.cache)
     c.mkdir(parents=True, exist_ok=True)
     tag = f"{w.name}-n{w.n}-R{w.degree}-it{args.build_iters}-ef{args.ef_build}"
-    return c / f"{tag}.sqg", c / f"{tag}-gt-q{w.n_queries}"
+    gt = c / f"{tag}-gt-q{w.n_queries}"  # the ground truth does not depend on the rotation
+    if args.rotation != "dense":
+        tag += f"-{args.rotation}"
+    return c / f"{tag}.sqg", gt
 
 
 def ensure_index(args, w, device, rank):
@@ -100,7 +105,8 @@ def ensure_index(args, w, device, rank):
         base = synth.base(w)
         log(f"building {idx.name}: n={w.n} d={w.d} R={w.degree}")
         info = ib.build_index(str(idx) + ".part", base, w.degree, device=device, init="random",
-                              iterations=args.build_iters, ef_build=args.ef_build, cand_k=2 * w.degree, log=log)
+                              iterations=args.build_iters, ef_build=args.ef_build, cand_k=2 * w.degree,
+                              rotation=args.rotation, log=log)
         os.replace(str(idx) + ".part", idx)
         secs = time.time() - t
         log(f"built in {secs:.1f}s {info['iterations'][-1]}")
@@ -361,7 +367,7 @@ def bench_mixed(args, w, ix, qd, q, gt_ids, rank, world, dist, local):
         got = np.stack([ids[off[i]:off[i + 1]] for i in sel])
         rec[str(kk)] = round(E.recall(got, gt_ids[sel], kk), 4)
     hops = st[:, 0].double().cpu().numpy()
-    alg = float(hops.sum() * ix.block_bytes + nq * 4 * w.d + 8 * total)
+    alg = float(hops.sum() * ix.block_bytes + nq * 4 * ix.d + 8 * total)
     peak, src = measured_peaks()
     line = {"metric": "queries/sec, mixed k and ef in one launch", "value": round(nq / (ms / 1e3), 1),
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -439,12 +445,36 @@ def bench_prep(args):
     n, nq, d = args.n or 1000, args.nq or w.n_queries, w.d
     ws = synth.small(w, n, 64)
     x = synth.base(ws)
-    path = pathlib.Path(args.cache) / f"prep-{w.name}-n{n}.sqg"
+    path = pathlib.Path(args.cache) / f"prep-{w.name}-n{n}-{args.rotation}.sqg"
     path.parent.mkdir(parents=True, exist_ok=True)
     if not path.exists():
-        ib.build_index(path, x, w.degree)
+        ib.build_index(path, x, w.degree, rotation=args.rotation)
     ix = Index(path, 0)
-    q = torch.from_numpy(synth.queries(w.with_(n_queries=nq))).cuda()
+    q = ix.fit_queries(torch.from_numpy(synth.queries(w.with_(n_queries=nq))).cuda())
+    if ix.fjlt:  # the fast transform (no dense contraction, no tensor-core path)
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+        for _ in range(max(3, args.warmup)):
+            ix.prepare_queries(q)
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ix.prepare_queries(q)
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = float(np.median(ms))
+        traffic = 2.0 * 4 * nq * ix.d  # read q, write q' (the planes are small)
+        peak_hbm = json.loads((ROOT / "MEASURED_PEAKS.json").read_text())["hbm_gbs"] \
+            if (ROOT / "MEASURED_PEAKS.json").exists() else 6800.0
+        print(json.dumps({"metric": "query preparation time (fast JLT + 4-bit quantization)", "unit": "ms",
+                          "workload": w.name, "d": w.d, "d_padded": ix.d, "queries": nq, "fjlt_ms": round(t, 4),
+                          "roofline": {"bound": "hbm", "achieved": round(traffic / (t / 1e3) / 1e9, 1),
+                                       "peak": peak_hbm, "unit": "GB/s",
+                                       "frac": round(traffic / (t / 1e3) / 1e9 / peak_hbm, 4)},
+                          "l2": "flushed (512 MiB write) before each call"}), flush=True)
+        return
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     res = {}
     for name, fn in (("cuda_cores", lambda: ix.prepare_queries(q)), ("tensor_cores", lambda: ix.prepare_queries_tc(q))):
@@ -508,6 +538,8 @@ def main():
     q = replica_queries(w, rank, world)
     gt_ids, gt_d = ground_truth(args, w, f"{gtp}-r{rank}", q, local, world)
     ix = Index(idx, local)
+    if ix.d != q.shape[1]:  # a fast-JLT index: data and queries zero-padded to a power of 2
+        q = np.ascontiguousarray(np.pad(q, ((0, 0), (0, ix.d - q.shape[1]))))
     qd = torch.from_numpy(q).cuda()
     if w.mixed_k:
         return bench_mixed(args, w, ix, qd, q, gt_ids, rank, world, dist, local)
@@ -612,7 +644,7 @@ def main():
 
     # ---- roofline of the search kernel: algorithmic bytes / its event time
     bb = ix.block_bytes
-    alg_bytes = float(hops.sum() * bb + nq * (4 * w.d + 8 * k))
+    alg_bytes = float(hops.sum() * bb + nq * (4 * ix.d + 8 * k))
     kern_mean = float(np.mean(kern_ms))
     achieved = alg_bytes / (kern_mean / 1e3) / 1e9
     peak, peak_src = measured_peaks()
@@ -640,13 +672,14 @@ def main():
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_max, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "d": w.d, "degree": w.degree, "k": k, "ef": ef_sel,
+        "config": {"workload": w.name, "n": w.n, "d": w.d, "degree": w.degree, "rotation": args.rotation,
+                   "k": k, "ef": ef_sel,
                    "queries_per_step": nq, "recall@10": round(rec_sel, 4), "parallelism": f"replicas{world}",
                    "l2": f"index ({ix.n * ix.block_bytes / 1e9:.2f} GB) larger than L2, no flush between job "
                          "steps; isolated steps flushed (512 MiB write)",
                    "launch": "one CUDA graph per step, steps alternating over 2 streams",
                    "step_isolated_ms": round(iso_ms, 4)},
-        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(nq * w.d * 4),
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(nq * ix.d * 4),
                 "d2h_bytes_per_step": int(nq * k * 8),
                 "recall@10": round(rec_e2e, 4) if rec_e2e is not None else None,
                 "api": "Index.host_pipeline (2 streams), host wall clock"},

@@ -130,7 +130,8 @@ const char *sqg_error_string(int code);
  * n(32D + 32R + DR) bits plus factors (Sec. 3.3).
  *
  * File v1, little-endian: 256-byte header
- *   0 "SQG1" | 4 version=1 u32 | 8 n u64 | 16 d u32 | 20 R u32 |
+ *   0 "SQG1" | 4 version u32 (1: dense rotation; 2: the fast JLT, see
+ *   sqg_write_index2) | 8 n u64 | 16 d u32 | 20 R u32 |
  *   24 block_bytes u32 | 28 entry u32 | 32 metric u32 (0 = squared L2) |
  *   36 off_codes | 40 off_factors | 44 off_ids (u32) | 48 rot_offset u64 |
  *   56 blocks_offset u64 | 64 file_bytes u64 | 72 seed_rotation u64 |
@@ -320,6 +321,16 @@ uint32_t sqg_medoid(const float *data, uint64_t n, uint32_t d, int threads);
 int sqg_write_index(const char *path, const float *data, uint64_t n, uint32_t d, const uint32_t *adj,
                     uint32_t R, const float *rot, uint32_t entry, uint64_t seed_rotation, uint64_t seed_graph,
                     int threads);
+
+/* sqg_write_index with the rotation's kind: 0 = the dense P^-1 (version 1);
+ * 1 = the fast JLT of Sec. 3.1.4 (version 2, d a power of 2): three rounds
+ * of a sign flip s_r and the Walsh-Hadamard transform scaled by 1/sqrt(d),
+ * s_r[i] = -1 when bit 63 of splitmix64(seed_rotation ^ (r << 32 | i)) is
+ * set.  `rot` must then hold that transform as a dense matrix (the edges'
+ * codes are built with it); queries are rotated by the fast transform. */
+int sqg_write_index2(const char *path, const float *data, uint64_t n, uint32_t d, const uint32_t *adj,
+                     uint32_t R, const float *rot, uint32_t entry, uint64_t seed_rotation, uint64_t seed_graph,
+                     int threads, uint32_t rotation_kind);
 
 #ifdef __cplusplus
 }

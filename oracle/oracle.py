@@ -57,6 +57,11 @@ def lib():
                 "orc_vertex": (None, [P, U32, P, P, P, P, P, P]),
                 "orc_rotate_f64": (None, [P, U32, P, P]),
                 "orc_rotate_f32": (None, [P, U32, P, P]),
+                "orc_splitmix64": (U64, [U64]),
+                "orc_fjlt_signs": (None, [U64, U32, P]),
+                "orc_fjlt_f64": (None, [P, U32, P, P]),
+                "orc_fjlt_f32": (None, [P, U32, P, P]),
+                "orc_fjlt_index_signs": (P, [P]),
                 "orc_sqdist_f64": (F64, [P, P, U32]),
                 "orc_quantize_edge": (None, [P, U32, P, P, P, P]),
                 "orc_estimate_unquantized_f64": (None, [P, U32, P, P, P, P]),
@@ -114,6 +119,13 @@ class Index:
     def rotation(self) -> np.ndarray:
         p = lib().orc_rotation(self._h)
         return np.ctypeslib.as_array(C.cast(p, C.POINTER(C.c_float)), shape=(self.d, self.d)).copy()
+
+    def fjlt_signs(self) -> np.ndarray | None:
+        """The fast JLT's 3 x d signs of a version-2 index, else None."""
+        p = lib().orc_fjlt_index_signs(self._h)
+        if not p:
+            return None
+        return np.ctypeslib.as_array(C.cast(p, C.POINTER(C.c_float)), shape=(3, self.d)).copy()
 
     def raw(self, v: int) -> np.ndarray:
         p = lib().orc_raw(self._h, int(v))
@@ -198,6 +210,30 @@ def rotate_f32(rot, q) -> np.ndarray:
     rot, q = _f32(rot), _f32(q)
     out = np.empty(rot.shape[0], np.float32)
     lib().orc_rotate_f32(_p(rot), rot.shape[0], _p(q), _p(out))
+    return out
+
+
+def splitmix64(x: int) -> int:
+    return int(lib().orc_splitmix64(C.c_uint64(x & 0xFFFFFFFFFFFFFFFF)))
+
+
+def fjlt_signs(seed: int, d: int) -> np.ndarray:
+    out = np.empty(3 * d, np.float32)
+    lib().orc_fjlt_signs(C.c_uint64(seed), d, _p(out))
+    return out.reshape(3, d)
+
+
+def fjlt_f64(signs, q) -> np.ndarray:
+    signs, q = _f32(signs), _f32(q)
+    out = np.empty(q.shape[0], np.float64)
+    lib().orc_fjlt_f64(_p(signs), q.shape[0], _p(q), _p(out))
+    return out
+
+
+def fjlt_f32(signs, q) -> np.ndarray:
+    signs, q = _f32(signs), _f32(q)
+    out = np.empty(q.shape[0], np.float32)
+    lib().orc_fjlt_f32(_p(signs), q.shape[0], _p(q), _p(out))
     return out
 
 

@@ -73,6 +73,12 @@
 /*     72 seed_rotation u64 | 80 seed_graph u64 | 88 payload_hash u64   */
 /*     96 header_hash u64 (over bytes 0..95) | rest zero                */
 /*   rotation P^-1: d*d float32 row-major at rot_offset                 */
+/*   version 2: the rotation is the fast JLT of Sec. 3.1.4 (d a power   */
+/*     of 2): three rounds of a sign flip s_r followed by the Walsh-    */
+/*     Hadamard transform scaled by 1/sqrt(d); s_r[i] = -1 when bit 63  */
+/*     of splitmix64(seed_rotation ^ (r << 32 | i)) is set, else +1.    */
+/*     The d*d region then holds the same transform as a dense matrix   */
+/*     (what the index's codes were built with).                        */
 /*   n vertex blocks of block_bytes each at blocks_offset; a block is   */
 /*     raw vector  d float32                          @ 0               */
 /*     codes       d*R bits: u32 word w of neighbour j at index w*R+j;  */
@@ -92,6 +98,8 @@ typedef struct {
     unsigned char *file; /* whole file */
     const float *rot;    /* d*d */
     const unsigned char *blocks;
+    int fjlt;            /* version 2: the query side uses the fast JLT */
+    float *signs;        /* 3*d, +1 / -1 (version 2) */
 } orc_index;
 
 static uint32_t rd32(const unsigned char *p) {
@@ -111,7 +119,24 @@ static uint64_t fnv_words(const unsigned char *p, uint64_t nbytes) {
 void orc_index_free(orc_index *ix) {
     if (!ix) return;
     free(ix->file);
+    free(ix->signs);
     free(ix);
+}
+
+/* splitmix64 (Steele, Lea, Flood 2014): the output for state x, i.e. the
+ * first value the generator returns after being seeded with x. */
+uint64_t orc_splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* The fast JLT's three sign vectors (3*d values, +1 / -1). */
+void orc_fjlt_signs(uint64_t seed, uint32_t d, float *signs) {
+    for (uint32_t r = 0; r < 3; ++r)
+        for (uint32_t i = 0; i < d; ++i)
+            signs[r * d + i] = (orc_splitmix64(seed ^ (((uint64_t)r << 32) | i)) >> 63) ? -1.0f : 1.0f;
 }
 
 int orc_index_load(const char *path, orc_index **out) {
@@ -127,7 +152,8 @@ int orc_index_load(const char *path, orc_index **out) {
     if (!buf) { fclose(f); return ORC_ERR_OOM; }
     if (fread(buf, 1, (size_t)sz, f) != (size_t)sz) { free(buf); fclose(f); return ORC_ERR_IO; }
     fclose(f);
-    if (memcmp(buf, "SQG1", 4) != 0 || rd32(buf + 4) != 1u) { free(buf); return ORC_ERR_FORMAT; }
+    const uint32_t version = rd32(buf + 4);
+    if (memcmp(buf, "SQG1", 4) != 0 || (version != 1u && version != 2u)) { free(buf); return ORC_ERR_FORMAT; }
     if (fnv_words(buf, 96) != rd64(buf + 96)) { free(buf); return ORC_ERR_FORMAT; }
     orc_index *ix = (orc_index *)calloc(1, sizeof(orc_index));
     if (!ix) { free(buf); return ORC_ERR_OOM; }
@@ -157,6 +183,13 @@ int orc_index_load(const char *path, orc_index **out) {
     }
     ix->rot = (const float *)(buf + ix->rot_offset);
     ix->blocks = buf + ix->blocks_offset;
+    if (version == 2u) {
+        if (d & (d - 1)) { orc_index_free(ix); return ORC_ERR_FORMAT; }  /* a power of 2 */
+        ix->fjlt = 1;
+        ix->signs = (float *)malloc(sizeof(float) * 3 * d);
+        if (!ix->signs) { orc_index_free(ix); return ORC_ERR_OOM; }
+        orc_fjlt_signs(rd64(buf + 72), (uint32_t)d, ix->signs);
+    }
     *out = ix;
     return ORC_OK;
 }
@@ -167,6 +200,9 @@ void orc_index_shape(const orc_index *ix, uint64_t *n, uint32_t *d, uint32_t *R,
 }
 
 const float *orc_rotation(const orc_index *ix) { return ix->rot; }
+
+/* The fast JLT's signs (3*d) of a version-2 index, else NULL. */
+const float *orc_fjlt_index_signs(const orc_index *ix) { return ix->fjlt ? ix->signs : NULL; }
 
 static const unsigned char *blk(const orc_index *ix, uint32_t v) {
     return ix->blocks + (uint64_t)v * ix->block_bytes;
@@ -215,6 +251,25 @@ void orc_rotate_f64(const float *rot, uint32_t d, const float *x, double *y) {
         double s = 0.0;
         for (uint32_t j = 0; j < d; ++j) s += (double)rot[(uint64_t)i * d + j] * (double)x[j];
         y[i] = s;
+    }
+}
+
+/* y = P^-1 x for the fast JLT in fp64 (Sec. 3.1.4): for r = 0, 1, 2 the
+ * signs s_r, the Walsh-Hadamard transform H (entries +1/-1, H_ij =
+ * (-1)^popcount(i & j)) and the scale 1/sqrt(d).  d a power of 2. */
+void orc_fjlt_f64(const float *signs, uint32_t d, const float *x, double *y) {
+    const double c = 1.0 / sqrt((double)d);
+    for (uint32_t i = 0; i < d; ++i) y[i] = (double)x[i];
+    for (uint32_t r = 0; r < 3; ++r) {
+        for (uint32_t i = 0; i < d; ++i) y[i] *= (double)signs[r * d + i];
+        for (uint32_t h = 1; h < d; h <<= 1)
+            for (uint32_t i = 0; i < d; i += 2 * h)
+                for (uint32_t j = i; j < i + h; ++j) {
+                    const double a = y[j], b = y[j + h];
+                    y[j] = a + b;
+                    y[j + h] = a - b;
+                }
+        for (uint32_t i = 0; i < d; ++i) y[i] *= c;
     }
 }
 
@@ -347,6 +402,31 @@ void orc_rotate_f32(const float *rot, uint32_t d, const float *q, float *y) {
     }
 }
 
+/* The fast JLT in fp32, the order both sides take: per round the sign
+ * flip (exact), the transform's stages h = 1, 2, 4, ... each replacing
+ * (y_j, y_j+h) by (y_j + y_j+h, y_j - y_j+h), then y_i * fl(1/sqrt(d)). */
+void orc_fjlt_f32(const float *signs, uint32_t d, const float *x, float *y) {
+    const float c = 1.0f / sqrtf((float)d);
+    for (uint32_t i = 0; i < d; ++i) y[i] = x[i];
+    for (uint32_t r = 0; r < 3; ++r) {
+        for (uint32_t i = 0; i < d; ++i) y[i] = y[i] * signs[r * d + i];
+        for (uint32_t h = 1; h < d; h <<= 1)
+            for (uint32_t i = 0; i < d; i += 2 * h)
+                for (uint32_t j = i; j < i + h; ++j) {
+                    const float a = y[j], b = y[j + h];
+                    y[j] = a + b;
+                    y[j + h] = a - b;
+                }
+        for (uint32_t i = 0; i < d; ++i) y[i] = y[i] * c;
+    }
+}
+
+/* q' of the query side: the fast JLT for a version-2 index, else P^-1 q. */
+static void rotate_query(const orc_index *ix, const float *q, float *qrot) {
+    if (ix->fjlt) orc_fjlt_f32(ix->signs, ix->d, q, qrot);
+    else orc_rotate_f32(ix->rot, ix->d, q, qrot);
+}
+
 /* R1: v_l = min q', v_r = max q', delta = (v_r - v_l)/15,
  * qbar_i = min(15, trunc((q'_i - v_l) * (15/(v_r - v_l)) + 0.5)).  */
 void orc_quantize_query(const float *qr, uint32_t d, unsigned char *qbar, float *vl_out, float *delta_out,
@@ -427,7 +507,7 @@ static void estimate(const orc_index *ix, const orc_query *qq, uint32_t v, uint3
 }
 
 static void prepare_query(const orc_index *ix, const float *q, orc_query *qq, float *qrot) {
-    orc_rotate_f32(ix->rot, ix->d, q, qrot);
+    rotate_query(ix, q, qrot);
     qq->q = q;
     orc_quantize_query(qrot, ix->d, qq->qbar, &qq->vl, &qq->delta, &qq->sq);
     qq->inv_sqrt_d = 1.0f / sqrtf((float)ix->d);
@@ -452,7 +532,7 @@ int orc_estimate_block(const orc_index *ix, const float *q, uint32_t v, float ep
 /* Test hook: the prepared query (q', qbar, v_l, delta, Sq). */
 void orc_prepare_query(const orc_index *ix, const float *q, float *qrot, unsigned char *qbar, float *vl,
                        float *delta, int32_t *sq) {
-    orc_rotate_f32(ix->rot, ix->d, q, qrot);
+    rotate_query(ix, q, qrot);
     orc_quantize_query(qrot, ix->d, qbar, vl, delta, sq);
 }
 

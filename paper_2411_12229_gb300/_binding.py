@@ -68,6 +68,7 @@ _SIGS = {
     "sqg_build_graph": (I32, [P, U64, U32, P, U32, U32, U32, U64, P, P, I32]),
     "sqg_medoid": (U32, [P, U64, U32, I32]),
     "sqg_write_index": (I32, [C.c_char_p, P, U64, U32, P, U32, P, U32, U64, U64, I32]),
+    "sqg_write_index2": (I32, [C.c_char_p, P, U64, U32, P, U32, P, U32, U64, U64, I32, U32]),
     "sqg_search_noalloc": (I32, [P, P, I32, P, P, I32, I32, P, P, P]),
     "sqg_noalloc_scratch_bytes": (SZ, []),
     "sqg_mlp_grad": (I32, [P, P, P, P, I32, P, P, P, P]),

@@ -44,6 +44,15 @@ class Index:
         self.n, self.d, self.degree = int(info.n), int(info.d), int(info.degree)
         self.block_bytes, self.entry = int(info.block_bytes), int(info.entry)
         self.device_bytes = int(info.device_bytes)
+        with open(path, "rb") as f:  # header version 2: the fast JLT (data zero-padded to d)
+            self.fjlt = int.from_bytes(f.read(8)[4:8], "little") == 2
+
+    def fit_queries(self, queries: torch.Tensor) -> torch.Tensor:
+        """Queries of a fast-JLT index may have fewer columns than d (the data
+        were zero-padded to a power of 2): pad them the same way."""
+        if queries.dim() == 2 and queries.shape[1] < self.d and self.fjlt:
+            return torch.nn.functional.pad(queries, (0, self.d - queries.shape[1]))
+        return queries
 
     def close(self) -> None:
         if getattr(self, "_h", None):
@@ -96,6 +105,7 @@ class Index:
         else flat ragged arrays (query i at offset sum_{j<i} k[j]).  Padding
         is id -1 with distance +inf.  With stats=True also returns an
         (nq, 2) int32 tensor of (hops, status bits)."""
+        queries = self.fit_queries(queries)
         if queries.dtype != torch.float32 or not queries.is_cuda or queries.dim() != 2 or queries.shape[1] != self.d:
             raise ValueError(f"queries must be a CUDA float32 tensor of shape (nq, {self.d})")
         queries = queries.contiguous()
@@ -137,6 +147,7 @@ class Index:
         gt) at every evaluation point, and/or the expansion order.  Returns
         ids, dists, stats, feats (nq, cap, 16), hits (nq, cap), counts (nq,)
         and, with path_cap > 0, path (nq, path_cap; -1 past the last hop)."""
+        queries = self.fit_queries(queries)
         nq, dev = queries.shape[0], queries.device
         kt, et = _i32(k, nq, dev), _i32(ef, nq, dev)
         ids = torch.empty(nq * k, dtype=torch.int32, device=dev)
@@ -195,6 +206,7 @@ class Index:
 
     # ------------------------------------------------------------------ test hooks
     def prepare_queries(self, queries: torch.Tensor, stream=None):
+        queries = self.fit_queries(queries)
         nq = queries.shape[0]
         dev = queries.device
         qrot = torch.empty((nq, self.d), dtype=torch.float32, device=dev)
@@ -222,6 +234,7 @@ class Index:
         return qrot, planes, scal, rec
 
     def estimate_block(self, queries: torch.Tensor, v: torch.Tensor, eps0: float = 0.0, stream=None):
+        queries = self.fit_queries(queries)
         nq, dev, R = queries.shape[0], queries.device, self.degree
         S = torch.empty((nq, R), dtype=torch.int32, device=dev)
         est = torch.empty((nq, R), dtype=torch.float32, device=dev)

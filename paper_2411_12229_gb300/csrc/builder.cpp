@@ -312,10 +312,11 @@ extern "C" int sqg_build_graph(const float *data, uint64_t n, uint32_t d, const 
     return SQG_OK;
 }
 
-extern "C" int sqg_write_index(const char *path, const float *data, uint64_t n, uint32_t d, const uint32_t *adj,
-                               uint32_t R, const float *rot, uint32_t entry, uint64_t seed_rotation,
-                               uint64_t seed_graph, int threads) {
-    if (!path || !data || !adj || !rot || n == 0 || d == 0 || d % 32 != 0 || R == 0 || R % 32 != 0 || entry >= n)
+extern "C" int sqg_write_index2(const char *path, const float *data, uint64_t n, uint32_t d, const uint32_t *adj,
+                                uint32_t R, const float *rot, uint32_t entry, uint64_t seed_rotation,
+                                uint64_t seed_graph, int threads, uint32_t rotation_kind) {
+    if (!path || !data || !adj || !rot || n == 0 || d == 0 || d % 32 != 0 || R == 0 || R % 32 != 0 || entry >= n ||
+        rotation_kind > 1 || (rotation_kind == 1 && (d & (d - 1)) != 0))
         return SQG_ERR_INVALID_ARG;
     for (uint64_t i = 0; i < n * R; ++i)
         if (adj[i] >= n) return SQG_ERR_INVALID_ARG;
@@ -415,8 +416,15 @@ extern "C" int sqg_write_index(const char *path, const float *data, uint64_t n, 
         }, 64);
         ok = put(buf.data(), buf.size());
     }
-    sqg_fmt::fill_header(header.data(), lay, entry, seed_rotation, seed_graph, h);
+    sqg_fmt::fill_header(header.data(), lay, entry, seed_rotation, seed_graph, h,
+                         rotation_kind == 1 ? sqg_fmt::kVersionFjlt : sqg_fmt::kVersion);
     ok = ok && std::fseek(f, 0, SEEK_SET) == 0 && std::fwrite(header.data(), 1, header.size(), f) == header.size();
     ok = (std::fclose(f) == 0) && ok;
     return ok ? SQG_OK : SQG_ERR_IO;
+}
+
+extern "C" int sqg_write_index(const char *path, const float *data, uint64_t n, uint32_t d, const uint32_t *adj,
+                               uint32_t R, const float *rot, uint32_t entry, uint64_t seed_rotation,
+                               uint64_t seed_graph, int threads) {
+    return sqg_write_index2(path, data, n, d, adj, R, rot, entry, seed_rotation, seed_graph, threads, 0);
 }

@@ -8,7 +8,8 @@
 
 namespace sqg_fmt {
 
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 1;      // the rotation is the stored dense P^-1
+constexpr uint32_t kVersionFjlt = 2;  // the query side applies the fast JLT (d a power of 2)
 constexpr uint64_t kHeaderBytes = 256;
 constexpr uint64_t kFnvBasis = 0xcbf29ce484222325ull;
 constexpr uint64_t kFnvPrime = 0x100000001b3ull;
@@ -62,10 +63,10 @@ inline uint64_t fnv_words(uint64_t h, const unsigned char *p, uint64_t nbytes) {
 }
 
 inline void fill_header(unsigned char *h, const Layout &l, uint32_t entry, uint64_t seed_rot, uint64_t seed_graph,
-                        uint64_t payload_hash) {
+                        uint64_t payload_hash, uint32_t version = kVersion) {
     std::memset(h, 0, kHeaderBytes);
     std::memcpy(h, "SQG1", 4);
-    store_u32(h + 4, kVersion);
+    store_u32(h + 4, version);
     store_u64(h + 8, l.n);
     store_u32(h + 16, l.d);
     store_u32(h + 20, l.R);
@@ -86,13 +87,28 @@ inline void fill_header(unsigned char *h, const Layout &l, uint32_t entry, uint6
 
 struct Header {
     Layout l;
-    uint32_t entry, metric;
-    uint64_t payload_hash;
+    uint32_t entry, metric, version;
+    uint64_t payload_hash, seed_rot;
 };
+
+// splitmix64 (Steele, Lea, Flood 2014): the generator's output for state x.
+inline uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// The fast JLT's sign of round r (0..2) at coordinate i: -1 when bit 63 of
+// splitmix64(seed ^ (r << 32 | i)) is set.
+inline float fjlt_sign(uint64_t seed, uint32_t r, uint32_t i) {
+    return (splitmix64(seed ^ (((uint64_t)r << 32) | i)) >> 63) ? -1.0f : 1.0f;
+}
 
 // Parse and check a header against the layout it implies and the file size.
 inline bool parse_header(const unsigned char *h, uint64_t file_size, Header &out) {
-    if (std::memcmp(h, "SQG1", 4) != 0 || load_u32(h + 4) != kVersion) return false;
+    const uint32_t version = load_u32(h + 4);
+    if (std::memcmp(h, "SQG1", 4) != 0 || (version != kVersion && version != kVersionFjlt)) return false;
     if (fnv_words(kFnvBasis, h, 96) != load_u64(h + 96)) return false;
     uint64_t n = load_u64(h + 8);
     uint32_t d = load_u32(h + 16), R = load_u32(h + 20);
@@ -102,10 +118,13 @@ inline bool parse_header(const unsigned char *h, uint64_t file_size, Header &out
         load_u32(h + 40) != l.off_factors || load_u32(h + 44) != l.off_ids || load_u64(h + 48) != l.rot_offset ||
         load_u64(h + 56) != l.blocks_offset || load_u64(h + 64) != l.file_bytes || l.file_bytes != file_size)
         return false;
+    if (version == kVersionFjlt && (d & (d - 1)) != 0) return false;
     out.l = l;
     out.entry = load_u32(h + 28);
     out.metric = load_u32(h + 32);
+    out.version = version;
     out.payload_hash = load_u64(h + 88);
+    out.seed_rot = load_u64(h + 72);
     return out.entry < n && out.metric == 0;
 }
 

@@ -963,6 +963,8 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
 // Tensor-core rotation and the exact quantization after it (rotate_tc.cu).
 float rotate_tc_err_scale(int d);
 cudaError_t launch_split_tf32(const float *x, float *hi, float *lo, size_t n, cudaStream_t s);
+// The fast JLT on the query side (fjlt.cu); d a power of 2 in 32..2048.
+cudaError_t launch_fjlt(const float *q, const float *signs, float *out, int nq, int d, cudaStream_t s);
 cudaError_t launch_rotate_tc(const float *q, const float *rot_hi, const float *rot_lo, float *out, int nq, int d,
                              uint32_t *status, cudaStream_t s);
 cudaError_t launch_quantize_exact(const float *q, const float *rot, const float *qa, int nq, int d, uint32_t *planes,

@@ -25,6 +25,8 @@ struct sqg_index {
     unsigned char *d_blocks;
     float *d_rot;
     float *d_rot_hi, *d_rot_lo;  // tf32 split of the rotation for the tensor-core path
+    bool fjlt;                   // version 2: queries are rotated by the fast JLT
+    float *d_signs;              // its 3 x d signs
     uint32_t *d_status;
     int num_sms;
     size_t smem_optin;
@@ -354,11 +356,21 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     return SQG_OK;
 }
 
+// q' on the CUDA cores: the fast JLT for a version-2 index, else the dense
+// P^-1 q in the canonical chunked order.
+cudaError_t rotate_simt(const sqg_index *ix, const float *queries, float *out, int nq, cudaStream_t stream) {
+    const int d = (int)ix->lay.d;
+    if (ix->fjlt) return launch_fjlt(queries, ix->d_signs, out, nq, d, stream);
+    dim3 rg((d + kRotT - 1) / kRotT, (nq + kRotT - 1) / kRotT);
+    rotate_kernel<<<rg, 256, 0, stream>>>(queries, ix->d_rot, out, nq, d);
+    return cudaGetLastError();
+}
+
 // Rotation path: 1 = the CUDA-core kernel in the canonical order, 2 = tensor
 // cores plus the exact quantization pass (same codes bit for bit); 0 = tensor
 // cores from d = 512 up (2.5x faster there; at d = 128 the two tie).
 bool use_tc_rotation(const sqg_index *ix, const sqg_search_params &p) {
-    if (p.rotation == 1) return false;
+    if (ix->fjlt || p.rotation == 1) return false;  // the fast JLT needs no contraction
     if (p.rotation == 2) return true;
     return ix->lay.d >= 512;
 }
@@ -435,6 +447,7 @@ extern "C" int sqg_index_load(const char *path, int device, sqg_index **out) {
     ix->device = device;
     ix->lay = L;
     ix->entry = h.entry;
+    ix->fjlt = h.version == sqg_fmt::kVersionFjlt;
     cudaDeviceGetAttribute(&ix->num_sms, cudaDevAttrMultiProcessorCount, device);
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -451,6 +464,18 @@ extern "C" int sqg_index_load(const char *path, int device, sqg_index **out) {
         return SQG_ERR_OOM;
     }
     cudaMemset(ix->d_status, 0, sizeof(uint32_t));
+    if (ix->fjlt) {  // the fast JLT's signs, from the rotation seed
+        std::vector<float> sg(3 * (size_t)L.d);
+        for (uint32_t r = 0; r < 3; ++r)
+            for (uint32_t i = 0; i < L.d; ++i) sg[(size_t)r * L.d + i] = sqg_fmt::fjlt_sign(h.seed_rot, r, i);
+        if (L.d > 2048 || cudaMalloc(&ix->d_signs, sizeof(float) * sg.size()) != cudaSuccess ||
+            cudaMemcpy(ix->d_signs, sg.data(), sizeof(float) * sg.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            std::fclose(f);
+            sqg_index_free(ix);
+            cudaGetLastError();
+            return SQG_ERR_UNSUPPORTED;
+        }
+    }
     // stream the payload through a pinned buffer, hashing and checking ids
     const size_t chunk = (size_t)64 << 20;
     unsigned char *stage = nullptr;
@@ -512,6 +537,7 @@ extern "C" void sqg_index_free(sqg_index *ix) {
     if (ix->d_rot) cudaFree(ix->d_rot);
     if (ix->d_rot_hi) cudaFree(ix->d_rot_hi);
     if (ix->d_rot_lo) cudaFree(ix->d_rot_lo);
+    if (ix->d_signs) cudaFree(ix->d_signs);
     if (ix->d_status) cudaFree(ix->d_status);
     delete ix;
 }
@@ -655,9 +681,9 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
             if (own_ws) cudaFreeAsync(workspace, stream);
             return SQG_ERR_CUDA;
         }
-    } else {
-        dim3 rg((ix->lay.d + kRotT - 1) / kRotT, (nq + kRotT - 1) / kRotT);
-        rotate_kernel<<<rg, 256, 0, stream>>>(queries, ix->d_rot, const_cast<float *>(a.qrot), nq, (int)ix->lay.d);
+    } else if (rotate_simt(ix, queries, const_cast<float *>(a.qrot), nq, stream) != cudaSuccess) {
+        if (own_ws) cudaFreeAsync(workspace, stream);
+        return SQG_ERR_CUDA;
     }
     e = cudaMemsetAsync(a.queue_head, 0, sizeof(unsigned int), stream);
     if (e == cudaSuccess && p.timing_events[0])
@@ -711,8 +737,7 @@ extern "C" int sqg_prepare_queries(const sqg_index *ix, const float *queries, in
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     DeviceGuard g(ix->device);
     const int d = (int)ix->lay.d;
-    dim3 rg((d + kRotT - 1) / kRotT, (nq + kRotT - 1) / kRotT);
-    rotate_kernel<<<rg, 256, 0, stream>>>(queries, ix->d_rot, out_qrot, nq, d);
+    if (rotate_simt(ix, queries, out_qrot, nq, stream) != cudaSuccess) return SQG_ERR_CUDA;
     const int wpb = 4;
     quantize_kernel<<<(nq + wpb - 1) / wpb, wpb * 32, sizeof(uint32_t) * wpb * 4 * (d / 32), stream>>>(
         out_qrot, nq, d, out_planes, out_scal);
@@ -725,6 +750,7 @@ extern "C" int sqg_prepare_queries_tc(const sqg_index *ix, const float *queries,
     if (!ix || nq < 0) return SQG_ERR_INVALID_ARG;
     if (nq == 0) return SQG_OK;
     if (!queries || !out_qrot || !out_planes || !out_scal || !recomputed) return SQG_ERR_INVALID_ARG;
+    if (ix->fjlt) return SQG_ERR_UNSUPPORTED;  // the fast JLT has no dense contraction to put on tensor cores
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     DeviceGuard g(ix->device);
     const int d = (int)ix->lay.d;
@@ -746,8 +772,10 @@ extern "C" int sqg_estimate_block(const sqg_index *ix, const float *queries, int
     const int d = (int)ix->lay.d;
     float *qrot = nullptr;
     if (cudaMallocAsync(&qrot, sizeof(float) * (size_t)nq * d, stream) != cudaSuccess) return SQG_ERR_OOM;
-    dim3 rg((d + kRotT - 1) / kRotT, (nq + kRotT - 1) / kRotT);
-    rotate_kernel<<<rg, 256, 0, stream>>>(queries, ix->d_rot, qrot, nq, d);
+    if (rotate_simt(ix, queries, qrot, nq, stream) != cudaSuccess) {
+        cudaFreeAsync(qrot, stream);
+        return SQG_ERR_CUDA;
+    }
     SearchArgs a;
     std::memset(&a, 0, sizeof(a));
     a.blocks = ix->d_blocks;

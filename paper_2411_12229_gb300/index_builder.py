@@ -45,6 +45,40 @@ def random_rotation(d: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(q.T, dtype=np.float32)
 
 
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """splitmix64 (Steele, Lea, Flood 2014): the output for each state x (uint64)."""
+    with np.errstate(over="ignore"):
+        z = x.astype(np.uint64) + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def fjlt_signs(d: int, seed: int) -> np.ndarray:
+    """3 x d signs of the fast JLT: -1 where bit 63 of
+    splitmix64(seed ^ (r << 32 | i)) is set."""
+    r = np.arange(3, dtype=np.uint64)[:, None]
+    i = np.arange(d, dtype=np.uint64)[None, :]
+    x = np.uint64(seed) ^ ((r << np.uint64(32)) | i)
+    return np.where(splitmix64(x) >> np.uint64(63), -1.0, 1.0)
+
+
+def fjlt_matrix(d: int, seed: int) -> np.ndarray:
+    """The fast JLT (Sec. 3.1.4) as a dense matrix, fp64 -> float32: rows of
+    c H S_3 c H S_2 c H S_1 with H the Walsh-Hadamard matrix (Sylvester
+    order) and c = 1/sqrt(d); d a power of 2."""
+    if d & (d - 1):
+        raise ValueError("the fast JLT needs d a power of 2")
+    h = np.ones((1, 1))
+    while h.shape[0] < d:
+        h = np.block([[h, h], [h, -h]])
+    s = fjlt_signs(d, seed)
+    m = np.eye(d)
+    for r in range(3):
+        m = (h @ (s[r][:, None] * m)) / np.sqrt(d)
+    return np.ascontiguousarray(m, dtype=np.float32)
+
+
 def knn_host(data: np.ndarray, k: int, threads: int = 0) -> np.ndarray:
     data = np.ascontiguousarray(data, dtype=np.float32)
     out = np.empty((data.shape[0], k), dtype=np.uint32)
@@ -71,13 +105,13 @@ def build_graph(data: np.ndarray, cand: np.ndarray, R: int, entry: int, seed: in
 
 
 def write_index(path, data: np.ndarray, adj: np.ndarray, rot: np.ndarray, entry: int, seed_rotation: int,
-                seed_graph: int, threads: int = 0) -> None:
+                seed_graph: int, threads: int = 0, rotation_kind: int = 0) -> None:
     data = np.ascontiguousarray(data, dtype=np.float32)
     adj = np.ascontiguousarray(adj, dtype=np.uint32)
     rot = np.ascontiguousarray(rot, dtype=np.float32)
-    B.check(B.lib().sqg_write_index(str(path).encode(), _p(data), data.shape[0], data.shape[1], _p(adj),
-                                    adj.shape[1], _p(rot), entry, seed_rotation, seed_graph, threads),
-            f"sqg_write_index({path})")
+    B.check(B.lib().sqg_write_index2(str(path).encode(), _p(data), data.shape[0], data.shape[1], _p(adj),
+                                     adj.shape[1], _p(rot), entry, seed_rotation, seed_graph, threads, rotation_kind),
+            f"sqg_write_index2({path})")
 
 
 def random_graph(n: int, R: int, seed: int) -> np.ndarray:
@@ -102,7 +136,8 @@ def random_graph(n: int, R: int, seed: int) -> np.ndarray:
 
 def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None, ef_build: int = 128,
                 cand_k: int | None = None, path_cand: int | None = None, rot_seed: int = 2, graph_seed: int = 3,
-                device: int | None = None, init: str = "auto", threads: int = 0, log=None) -> dict:
+                device: int | None = None, init: str = "auto", threads: int = 0, rotation: str = "dense",
+                log=None) -> dict:
     """Build an index file at `path` from base vectors `data` (n x d).
 
     device=None: host-only build from an exact kNN (small n).
@@ -110,12 +145,23 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
     of every vertex: the cand_k nearest vertices the search expanded plus
     the first path_cand vertices on its path from the entry point (as NSG
     takes the visited set, so that long edges between regions survive the
-    pruning); init "random" (the paper) or "knn" (host brute force)."""
+    pruning); init "random" (the paper) or "knn" (host brute force).
+
+    rotation "dense": a Haar-random P^-1 (stored, applied as a d x d
+    product); "fjlt": the fast JLT of Sec. 3.1.4, the data zero-padded to
+    the next power of 2 (queries are padded the same way by the API)."""
     t0 = time.time()
     data = np.ascontiguousarray(data, dtype=np.float32)
+    if rotation == "fjlt":
+        dp = 1 << max(5, int(np.ceil(np.log2(data.shape[1]))))
+        if dp != data.shape[1]:
+            data = np.ascontiguousarray(np.pad(data, ((0, 0), (0, dp - data.shape[1]))))
+    elif rotation != "dense":
+        raise ValueError("rotation is 'dense' or 'fjlt'")
+    kind = 1 if rotation == "fjlt" else 0
     n, d = data.shape
     cand_k = cand_k or 2 * R
-    rot = random_rotation(d, rot_seed)
+    rot = fjlt_matrix(d, rot_seed) if kind else random_rotation(d, rot_seed)
     entry = medoid(data, threads)
     info = dict(n=n, d=d, R=R, entry=entry, iterations=[])
     tmp = pathlib.Path(str(path) + ".tmp")
@@ -129,7 +175,7 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
         adj = random_graph(n, R, graph_seed)
     if iterations is None:
         iterations = 0 if device is None else (3 if init == "random" else 1)
-    write_index(tmp if iterations else path, data, adj, rot, entry, rot_seed, graph_seed, threads)
+    write_index(tmp if iterations else path, data, adj, rot, entry, rot_seed, graph_seed, threads, kind)
     if iterations:
         import torch
 
@@ -155,7 +201,7 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
             ix.close()
             adj, st = build_graph(data, cand, R, entry, graph_seed + it + 1, threads)
             final = it == iterations - 1
-            write_index(path if final else tmp, data, adj, rot, entry, rot_seed, graph_seed, threads)
+            write_index(path if final else tmp, data, adj, rot, entry, rot_seed, graph_seed, threads, kind)
             info["iterations"].append(dict(source="gpu-search", seconds=time.time() - t1, **st))
             if log:
                 log(f"build iteration {it + 1}/{iterations}: {time.time() - t1:.1f}s {st}")

@@ -193,3 +193,18 @@ def test_workload_recipes():
     assert set(np.unique(k)) == {1, 10, 100} and np.all(ef >= k) and np.all(ef <= 8 * k)
     arr = synth.poisson_arrivals(1000.0, 5000)
     assert np.all(np.diff(arr) > 0) and abs(5000 / arr[-1] - 1000) < 100
+
+
+def test_fjlt_builder_agrees_with_the_oracle(oracle_mod, lib_built):
+    """Two implementations of the same definitions: the builder's signs and
+    dense fast-JLT matrix against the oracle's generator and transform."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    for d in (32, 128, 256):
+        s = ib.fjlt_signs(d, 11)
+        np.testing.assert_array_equal(s, oracle_mod.fjlt_signs(11, d))
+        M = ib.fjlt_matrix(d, 11).astype(np.float64)
+        rng = np.random.default_rng(d)
+        x = rng.standard_normal(d).astype(np.float32)
+        np.testing.assert_allclose(M @ x.astype(np.float64), oracle_mod.fjlt_f64(s, x), rtol=0, atol=1e-5)
+    with pytest.raises(ValueError):
+        ib.fjlt_matrix(96, 1)

@@ -397,3 +397,78 @@ def test_adam_first_step_closed_form(oracle_mod):
     g = rng.standard_normal(n)
     oracle_mod.adam_step_f64(p, m, v, g, 1, 0.01)
     np.testing.assert_allclose(p, p0 - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+# --------------------------------------------------------------- fast JLT (Sec. 3.1.4)
+
+def test_splitmix64_matches_its_published_outputs(oracle_mod):
+    """The sign generator is splitmix64: seeded with 0, the reference
+    generator (Java's SplittableRandom(0)) returns 0xE220A8397B1DCDAF and
+    then 0x6E789E6AA1B965F4 (its state advances by the golden gamma)."""
+    assert oracle_mod.splitmix64(0) == 0xE220A8397B1DCDAF
+    assert oracle_mod.splitmix64(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
+
+
+@pytest.mark.parametrize("d", [32, 64, 128])
+def test_fjlt_f64_is_the_hadamard_product(oracle_mod, d):
+    """The fp64 fast transform equals the explicit product
+    c H S3 c H S2 c H S1 with H the Sylvester Hadamard matrix."""
+    from scipy.linalg import hadamard
+    signs = oracle_mod.fjlt_signs(7, d)
+    H = hadamard(d).astype(np.float64)
+    M = np.eye(d)
+    for r in range(3):
+        M = H @ (signs[r].astype(np.float64)[:, None] * M) / np.sqrt(d)
+    rng = np.random.default_rng(d)
+    for _ in range(4):
+        x = rng.standard_normal(d).astype(np.float32)
+        np.testing.assert_allclose(oracle_mod.fjlt_f64(signs, x), M @ x.astype(np.float64), rtol=0,
+                                   atol=1e-12 * np.abs(x).sum())
+    assert np.max(np.abs(M @ M.T - np.eye(d))) < 1e-12  # orthogonal
+    assert 0.3 < float((signs < 0).mean()) < 0.7
+
+
+@pytest.mark.parametrize("d", [64, 1024])
+def test_fjlt_f32_within_its_bound(oracle_mod, d):
+    """The fp32 order: per round log2(d) pairwise additions and one scaling;
+    the transform is orthogonal, so ||err||_2 <= 3 (sqrt(d) log2(d) + 1) u ||x||."""
+    signs = oracle_mod.fjlt_signs(3, d)
+    rng = np.random.default_rng(1)
+    u = 2.0 ** -24
+    for _ in range(4):
+        x = (rng.standard_normal(d) * 5).astype(np.float32)
+        a = oracle_mod.fjlt_f32(signs, x).astype(np.float64)
+        b = oracle_mod.fjlt_f64(signs, x)
+        bound = 3 * (np.sqrt(d) * np.log2(d) + 1) * u * np.linalg.norm(x.astype(np.float64))
+        assert np.linalg.norm(a - b) <= bound
+        np.testing.assert_allclose(np.linalg.norm(b), np.linalg.norm(x.astype(np.float64)), rtol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def small_fjlt_graph(tmp_path_factory, lib_built, oracle_mod):
+    """200 vertices of d = 96, zero-padded to 128 by the fast-JLT build."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    from paper_2411_12229_gb300 import synth
+    w = synth.small(synth.TINY_10K_D128.with_(d=96), 200, 20, n_components=4)
+    x = synth.base(w)
+    p = tmp_path_factory.mktemp("gf") / "g200f.sqg"
+    ib.build_index(p, x, 32, rotation="fjlt")
+    return oracle_mod.Index(p), x, synth.queries(w)
+
+
+def test_fjlt_index_full_beam_returns_exact_knn(small_fjlt_graph, oracle_mod):
+    """A version-2 index: the oracle rotates queries with the fast JLT of
+    its own generator's signs; a full beam still returns the exact kNN of
+    the unpadded data (zero padding changes no distance)."""
+    O, x, qs = small_fjlt_graph
+    assert O.d == 128 and O.fjlt_signs() is not None
+    ef = O.n * (O.R + 1)
+    for i in range(5):
+        q = np.pad(qs[i], (0, 32))
+        ids, dists, hops, st = O.search(q, 10, ef, hop_cap=10 * ef)
+        gt, gd = oracle_mod.bruteforce(x, qs[i], 10)
+        assert hops == O.n and st == 0
+        np.testing.assert_array_equal(ids, gt)
+        np.testing.assert_allclose(dists, gd, rtol=1e-5)
+        r = O.prepare_query(q)
+        np.testing.assert_array_equal(r["qrot"], oracle_mod.fjlt_f32(O.fjlt_signs(), q))
