@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--cache", default=os.environ.get("SQG_CACHE", "/tmp/sqg_cache"))
     ap.add_argument("--target", type=float, default=0.95)
     ap.add_argument("--build-iters", type=int, default=3)
-    ap.add_argument("--ef-build", type=int, default=64)
+    ap.add_argument("--ef-build", type=int, default=400, help="index build: candidate-search beam (the paper's EF)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--ef", type=int, default=0, help="fixed ef: skip the sweep (profiling runs)")

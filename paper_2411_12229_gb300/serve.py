@@ -194,10 +194,10 @@ def main():
         w = synth.small(w, args.n, w.n_queries)
     cache = pathlib.Path(args.cache)
     cache.mkdir(parents=True, exist_ok=True)
-    path = cache / f"{w.name}-n{w.n}-R{w.degree}-it3-ef64.sqg"
+    path = cache / f"{w.name}-n{w.n}-R{w.degree}-it3-ef400.sqg"
     if not path.exists():
         base = synth.base(w)
-        ib.build_index(str(path) + ".part", base, w.degree, device=0, init="random", iterations=3, ef_build=64)
+        ib.build_index(str(path) + ".part", base, w.degree, device=0, init="random", iterations=3, ef_build=400)
         os.replace(str(path) + ".part", path)
     else:
         base = None
