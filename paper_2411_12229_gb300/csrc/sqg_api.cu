@@ -304,8 +304,13 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     a.hash_bits = bits;
     const size_t hash_bytes = (size_t)4 << bits;
     size_t o = 0;
+    // one block buffer: every read of a block (raw vector, codes, factors,
+    // ids) is done before the next block's copy is issued into it, and at
+    // most one copy is in flight, so the two mbarrier phases of the kernel's
+    // double-buffer protocol can share it -- half the shared memory, twice
+    // the resident warps at d = 960 / 1536
     a.o_buf0 = (uint32_t)o; o += bb;
-    a.o_buf1 = (uint32_t)o; o += bb;
+    a.o_buf1 = a.o_buf0;
     a.o_bar = (uint32_t)o; o += 16;
     a.o_planes = (uint32_t)o; o = align_up(o + 16 * (d / 32), 16);
     a.o_beam = (uint32_t)o; o = align_up(o + 8 * (size_t)max_ef, 16);
