@@ -318,28 +318,44 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     a.o_spos = (uint32_t)o; o = align_up(o + 4 * (size_t)R, 16);
     // visited set: up to 2^10 slots in shared memory; a longer search moves
     // to its warp's full-size table in the workspace
-    const uint32_t smem_bits_default = (pl.ch < 0 || pl.team < 32) ? 9u : 10u;
+    const uint32_t smem_bits_default = 9u;  // 2^10 measured slower at large beams (less residency)
     a.shash_bits =
         std::min<uint32_t>(bits, p.visited_smem_log2 > 0 ? (uint32_t)p.visited_smem_log2 : smem_bits_default);
     pl.ghash = a.shash_bits < bits;
     a.o_hash = (uint32_t)o;
     const size_t warp_bytes = align_up(o + ((size_t)4 << a.shash_bits), 128);
     const size_t cta = 0;  // the stop network's weights are read from the workspace (L1-cached)
-    int warps = p.warps_per_block > 0 ? p.warps_per_block : 4;
-    warps = std::min(warps, 4);
     // one slot of warp_bytes per query in flight: V per warp
-    while (warps > 1 && cta + warps * V * warp_bytes > ix->smem_optin) --warps;
-    if (cta + warps * V * warp_bytes > ix->smem_optin) return SQG_ERR_CAPACITY;
+    auto occupancy = [&](int w, int *blocks) -> cudaError_t {
+        const size_t sm = cta + (size_t)w * V * warp_bytes;
+        *blocks = 0;
+        if (sm > ix->smem_optin) return cudaSuccess;
+        return pl.team < 32 ? search_occupancy_team(pl.ch, pl.nb, pl.team, w * 32, sm, blocks)
+             : pl.nb == 1   ? search_occupancy_nb1(pl.ch, w * 32, sm, blocks)
+                            : search_occupancy_nb2(pl.ch, w * 32, sm, blocks);
+    };
+    int warps = 0, per_sm = 0;
+    if (p.warps_per_block > 0) {
+        warps = std::min(p.warps_per_block, 4);
+        while (warps > 1 && cta + warps * V * warp_bytes > ix->smem_optin) --warps;
+        if (occupancy(warps, &per_sm) != cudaSuccess) return SQG_ERR_CUDA;
+    } else {
+        // the block size with the most resident warps per SM (shared memory
+        // limits large d, registers small d); larger blocks on a tie
+        for (int w : {4, 2, 1}) {
+            int b = 0;
+            if (occupancy(w, &b) != cudaSuccess) return SQG_ERR_CUDA;
+            if (b * w > per_sm * warps) {
+                warps = w;
+                per_sm = b;
+            }
+        }
+    }
+    if (warps < 1 || per_sm < 1) return SQG_ERR_CAPACITY;
     a.warp_bytes = (uint32_t)warp_bytes;
     a.cta_bytes = (uint32_t)cta;
     pl.warps = warps;
     pl.smem = cta + warps * V * warp_bytes;
-    int per_sm = 0;
-    cudaError_t e = pl.team < 32 ? search_occupancy_team(pl.ch, pl.nb, pl.team, warps * 32, pl.smem, &per_sm)
-                    : pl.nb == 1 ? search_occupancy_nb1(pl.ch, warps * 32, pl.smem, &per_sm)
-                                 : search_occupancy_nb2(pl.ch, warps * 32, pl.smem, &per_sm);
-    if (e != cudaSuccess) return SQG_ERR_CUDA;
-    if (per_sm < 1) return SQG_ERR_CAPACITY;
     const long long want = ((long long)nq + warps * V - 1) / (warps * V);
     pl.grid = (int)std::max(1LL, std::min<long long>((long long)per_sm * ix->num_sms, want));
     // workspace
