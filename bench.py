@@ -182,8 +182,10 @@ class Clocks:
 
 
 def kernel_digest() -> str:
+    """Digest of the search kernel's sources and of its launch planning."""
     h = hashlib.sha256()
-    for p in sorted((ROOT / "paper_2411_12229_gb300" / "csrc").glob("search*")):
+    csrc = ROOT / "paper_2411_12229_gb300" / "csrc"
+    for p in sorted(list(csrc.glob("search*")) + [csrc / "sqg_api.cu"]):
         h.update(p.read_bytes())
     return h.hexdigest()[:16]
 
