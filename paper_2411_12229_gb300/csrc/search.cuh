@@ -10,7 +10,9 @@
 //            neighbour ids (Sec. 3.1.3) -- by one 1-D bulk copy
 //            (cp.async.bulk) into shared memory; the NEXT vertex's block is
 //            copied while the current one is merged (memory prefetching,
-//            Sec. 3.1.4), into the other of two buffers;
+//            Sec. 3.1.4); the kernel alternates two buffer slots with their
+//            own mbarriers, which the launch plan may point at one buffer
+//            (every read of a block precedes the next copy);
 //   exact    the squared distance from the raw vector updates the result
 //            set (implicit re-ranking);
 //   estimate every neighbour's distance: S = sum_i b_i qbar_i by AND +
