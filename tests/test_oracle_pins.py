@@ -306,6 +306,19 @@ def test_without_multiple_estimates_is_a_valid_search(tiny_index, oracle_mod):
         np.testing.assert_allclose(dists, ex, rtol=1e-5)
 
 
+def test_without_multiple_estimates_full_beam_returns_exact_knn(small_graph, oracle_mod):
+    """The w/o ME ablation with a beam that never truncates still expands
+    every reachable vertex, so it returns the exact kNN like Algorithm 1."""
+    O, x, qs = small_graph
+    ef = O.n * (O.R + 1)
+    for i in range(5):
+        ids, dists, hops, st = O.search(qs[i], 10, ef, multi_estimate=False, hop_cap=10 * ef)
+        gt, gd = oracle_mod.bruteforce(x, qs[i], 10)
+        assert hops == O.n and st == 0
+        np.testing.assert_array_equal(ids, gt)
+        np.testing.assert_allclose(dists, gd, rtol=1e-5)
+
+
 def test_learned_stop_constant_networks(tiny_index, oracle_mod):
     """A network whose logit is a constant +100 stops at the first
     evaluation; -100 never stops and equals the plain search."""
