@@ -362,6 +362,34 @@ def test_stop_features_partial_pins(tiny_index, oracle_mod):
         assert np.all(np.diff(hits) >= 0) and hits[-1] <= len(set(ids.tolist()) & set(gt.tolist()))
 
 
+def test_stop_features_invariants(tiny_index, oracle_mod):
+    """What the definitions imply for every trace row: counts over ef, k and
+    R are whole numbers; f1 = (hops since the last improvement)/ef <= f0;
+    f4 = best/k-th result distance lies in [0, 1] and is 1 for k = 1;
+    f14 says whether dist_c <= r_k, i.e. f6 = dist_c/r_k <= 1; the inserted
+    fraction f7 and the averages f9, f10 of values in [0, 1] stay in [0, 1];
+    f13 = since/(hops + 1) lies in [0, 1)."""
+    p, x, qs = tiny_index
+    O = oracle_mod.Index(p)
+    ef, every, R = 48, 2, O.R
+    for k in (1, 10):
+        for i in range(4):
+            F = O.search(qs[i], k, ef, stop_every=every, trace_cap=1000)[4]
+            assert len(F) > 0
+            for col, scale in ((2, ef), (3, ef), (11, k), (12, k), (7, R)):
+                v = F[:, col] * scale
+                np.testing.assert_allclose(v, np.rint(v), atol=1e-3)
+            assert np.all(F[:, 1] <= F[:, 0] + 1e-6) and np.all(F[:, 1] >= 0)
+            assert np.all((F[:, 4] >= 0) & (F[:, 4] <= 1 + 1e-6))
+            if k == 1:
+                np.testing.assert_allclose(F[:, 4], 1.0, rtol=1e-6)
+            far = np.abs(F[:, 6] - 1) > 1e-5
+            assert np.all((F[far, 14] == 1) == (F[far, 6] < 1))
+            for col in (7, 9, 10):
+                assert np.all((F[:, col] >= 0) & (F[:, col] <= 1 + 1e-6))
+            assert np.all((F[:, 13] >= 0) & (F[:, 13] < 1))
+
+
 # --------------------------------------------------------------- MLP training math
 
 def test_mlp_gradient_matches_finite_differences(oracle_mod):
