@@ -208,3 +208,27 @@ def test_fjlt_builder_agrees_with_the_oracle(oracle_mod, lib_built):
         np.testing.assert_allclose(M @ x.astype(np.float64), oracle_mod.fjlt_f64(s, x), rtol=0, atol=1e-5)
     with pytest.raises(ValueError):
         ib.fjlt_matrix(96, 1)
+
+
+def test_fjlt_index_header_and_writer_checks(lib_built, oracle_mod, tmp_path):
+    """The fast-JLT writer refuses a d that is not a power of 2 or an
+    unknown rotation kind; a written index carries format version 2 and
+    loads in the oracle with the generator's signs."""
+    from paper_2411_12229_gb300 import _binding as B
+    from paper_2411_12229_gb300 import index_builder as ib
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((100, 96)).astype(np.float32)
+    adj = ib.random_graph(100, 32, 1)
+    rot = np.eye(96, dtype=np.float32)
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    for kind in (1, 2):
+        rc = B.lib().sqg_write_index2(str(tmp_path / "bad.sqg").encode(), ptr(x), 100, 96, ptr(adj), 32, ptr(rot),
+                                      0, 5, 3, 1, kind)
+        assert rc == -1  # SQG_ERR_INVALID_ARG
+    p = tmp_path / "ok.sqg"
+    ib.build_index(p, x, 32, rotation="fjlt")
+    with open(p, "rb") as f:
+        assert int.from_bytes(f.read(8)[4:8], "little") == 2
+    O = oracle_mod.Index(p)
+    assert O.d == 128
+    np.testing.assert_array_equal(O.fjlt_signs(), ib.fjlt_signs(128, 2))
