@@ -90,15 +90,14 @@ typedef struct {
     int32_t team;            /* lanes per query: 32 (default, 0), 16 or 8 -- a warp then
                                 runs 2 or 4 queries side by side; 16 and 8 need d <= 256
                                 and no stop_mlp / trace (else SQG_ERR_UNSUPPORTED) */
-    int32_t warps_per_block; /* 0 = library default */
+    int32_t warps_per_block; /* 1, 2 or 4; 0 = the one with the most resident warps per SM */
     void *timing_events[2];  /* optional cudaEvent_t pair recorded on the stream right before
                                 and right after the search kernel; NULL = none */
     int32_t visited_smem_log2; /* log2 of the visited set's shared-memory slots (5..12;
-                                  0 = 9 with the lean build, else 10); a search past
-                                  half of them continues in a full-size table in the
-                                  workspace */
-    int32_t prefetch;        /* 1 (default, 0): next block copied into a second shared
-                                buffer during the merge; 2: also L2-prefetch the
+                                  0 = 9); a search past half of them continues in a
+                                  full-size table in the workspace */
+    int32_t prefetch;        /* 1 (default, 0): the next block is copied into shared
+                                memory during the merge; 2: also L2-prefetch the
                                 runner-up candidate's block */
     int32_t lean;            /* d <= 256 only: 0 or 1 = the kernel build capped at 64
                                 registers (more resident warps, a few spills; the
@@ -109,7 +108,8 @@ typedef struct {
                                 the canonical order every coordinate whose 4-bit code or
                                 min/max role the tensor-core error could change, so the
                                 quantized query is identical to 1; 0 = 2 for d >= 512,
-                                else 1 */
+                                else 1.  Ignored for a fast-JLT index (format version 2),
+                                whose queries always take the fast transform */
 } sqg_search_params;
 
 typedef struct {
