@@ -53,6 +53,8 @@ def lib():
                 "orc_index_free": (None, [P]),
                 "orc_index_shape": (None, [P, P, P, P, P, P]),
                 "orc_rotation": (P, [P]),
+                "orc_metric": (U32, [P]),
+                "orc_normalize_f32": (None, [P, U32, P]),
                 "orc_raw": (P, [P, U32]),
                 "orc_vertex": (None, [P, U32, P, P, P, P, P, P]),
                 "orc_rotate_f64": (None, [P, U32, P, P]),
@@ -104,6 +106,7 @@ class Index:
         n, d, R, e, bb = C.c_uint64(), C.c_uint32(), C.c_uint32(), C.c_uint32(), C.c_uint32()
         lib().orc_index_shape(h, C.byref(n), C.byref(d), C.byref(R), C.byref(e), C.byref(bb))
         self.n, self.d, self.R, self.entry, self.block_bytes = n.value, d.value, R.value, e.value, bb.value
+        self.metric = int(lib().orc_metric(h))  # 0 squared Euclidean, 1 cosine (R16)
 
     def close(self):
         if self._h:
@@ -234,6 +237,14 @@ def fjlt_f32(signs, q) -> np.ndarray:
     signs, q = _f32(signs), _f32(q)
     out = np.empty(q.shape[0], np.float32)
     lib().orc_fjlt_f32(_p(signs), q.shape[0], _p(q), _p(out))
+    return out
+
+
+def normalize_f32(q) -> np.ndarray:
+    """q / ||q|| in fp32 in the order of R16 (a zero query is returned as is)."""
+    q = _f32(q)
+    out = np.empty(q.shape[0], np.float32)
+    lib().orc_normalize_f32(_p(q), q.shape[0], _p(out))
     return out
 
 

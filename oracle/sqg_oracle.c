@@ -31,7 +31,12 @@
  *   R6 a hop cap stops a search after hop_cap expansions with a status flag;
  *   R7 admission key = estimate - eps0 * bound, bound = f_err*||q_r-c||
  *      (RaBitQ's bound form); eps0 = 0 is Algorithm 1 exactly;
- *   R8 the initial beam entry carries the entry point's exact distance.
+ *   R8 the initial beam entry carries the entry point's exact distance;
+ *   R16 cosine similarity (Sec. 3: RaBitQ serves Euclidean distance and
+ *      cosine similarity) is served as Euclidean search between unit
+ *      vectors: an index of metric 1 stores unit-norm vectors, and every
+ *      query is scaled to unit norm before anything else (orc_normalize_f32);
+ *      the distances returned are ||q/|q| - x||^2 = 2 - 2 cos(q, x).
  *
  * Floating point.  Fp64 functions give the plain definitions (used by the
  * pins).  The search takes its decisions (which vertex to expand, what
@@ -67,7 +72,8 @@
 /* Index file (version 1).  Little-endian.                             */
 /*   header, 256 bytes:                                                */
 /*     0 magic "SQG1" | 4 version u32 | 8 n u64 | 16 d u32 | 20 R u32   */
-/*     24 block_bytes u32 | 28 entry u32 | 32 metric u32                */
+/*     24 block_bytes u32 | 28 entry u32 | 32 metric u32 (0 squared    */
+/*     Euclidean, 1 cosine: unit-norm vectors, queries normalized, R16) */
 /*     36 off_codes u32 | 40 off_factors u32 | 44 off_ids u32           */
 /*     48 rot_offset u64 | 56 blocks_offset u64 | 64 file_bytes u64     */
 /*     72 seed_rotation u64 | 80 seed_graph u64 | 88 payload_hash u64   */
@@ -163,6 +169,7 @@ int orc_index_load(const char *path, orc_index **out) {
     ix->block_bytes = rd32(buf + 24);
     ix->entry = rd32(buf + 28);
     ix->metric = rd32(buf + 32);
+    if (ix->metric > 1u) { free(buf); free(ix); return ORC_ERR_FORMAT; }
     ix->off_codes = rd32(buf + 36);
     ix->off_factors = rd32(buf + 40);
     ix->off_ids = rd32(buf + 44);
@@ -200,6 +207,7 @@ void orc_index_shape(const orc_index *ix, uint64_t *n, uint32_t *d, uint32_t *R,
 }
 
 const float *orc_rotation(const orc_index *ix) { return ix->rot; }
+uint32_t orc_metric(const orc_index *ix) { return ix->metric; }
 
 /* The fast JLT's signs (3*d) of a version-2 index, else NULL. */
 const float *orc_fjlt_index_signs(const orc_index *ix) { return ix->fjlt ? ix->signs : NULL; }
@@ -481,6 +489,44 @@ float orc_exact_dist_f32(const float *q, const float *x, uint32_t d) {
     return part[0];
 }
 
+/* R16: q / ||q|| in fp32.  s = ||q||^2 in the exact distance's order (32
+ * partial sums over float4 chunks l, l+32, ..., fmaf(x, x, acc), then the
+ * pairwise tree over partials l and l^16, ^8, ^4, ^2, ^1); each coordinate is
+ * then divided by fl(sqrt(s)).  A query with s = 0 (or s not finite) is
+ * left as it is. */
+void orc_normalize_f32(const float *q, uint32_t d, float *out) {
+    float part[32];
+    uint32_t chunks = d / 4u;
+    for (uint32_t l = 0; l < 32; ++l) {
+        float acc = 0.0f;
+        for (uint32_t c = l; c < chunks; c += 32)
+            for (uint32_t t = 0; t < 4; ++t) acc = fmaf(q[4 * c + t], q[4 * c + t], acc);
+        part[l] = acc;
+    }
+    for (uint32_t off = 16; off >= 1; off >>= 1) {
+        float nxt[32];
+        for (uint32_t l = 0; l < 32; ++l) nxt[l] = part[l] + part[l ^ off];
+        memcpy(part, nxt, sizeof(part));
+    }
+    const float s = part[0];
+    if (s > 0.0f && s <= 3.40282347e38f) {
+        const float r = sqrtf(s);
+        for (uint32_t i = 0; i < d; ++i) out[i] = q[i] / r;
+    } else {
+        for (uint32_t i = 0; i < d; ++i) out[i] = q[i];
+    }
+}
+
+/* The query every search step sees: normalized on a cosine index (R16),
+ * else the caller's vector.  Returns a buffer to free, or NULL. */
+static float *query_for(const orc_index *ix, const float **q) {
+    if (ix->metric != 1u) return NULL;
+    float *qn = (float *)malloc(sizeof(float) * ix->d);
+    orc_normalize_f32(*q, ix->d, qn);
+    *q = qn;
+    return qn;
+}
+
 typedef struct {
     const float *q;        /* raw query, d */
     unsigned char *qbar;   /* quantized rotated query, d */
@@ -517,6 +563,7 @@ static void prepare_query(const orc_index *ix, const float *q, orc_query *qq, fl
 int orc_estimate_block(const orc_index *ix, const float *q, uint32_t v, float eps0, int32_t *S, float *est,
                        float *key, float *dist_c_out) {
     if (v >= ix->n) return ORC_ERR_ARG;
+    float *qn = query_for(ix, &q);
     orc_query qq;
     float *qrot = (float *)malloc(sizeof(float) * ix->d);
     qq.qbar = (unsigned char *)malloc(ix->d);
@@ -526,14 +573,17 @@ int orc_estimate_block(const orc_index *ix, const float *q, uint32_t v, float ep
     *dist_c_out = dist_c;
     free(qrot);
     free(qq.qbar);
+    free(qn);
     return ORC_OK;
 }
 
 /* Test hook: the prepared query (q', qbar, v_l, delta, Sq). */
 void orc_prepare_query(const orc_index *ix, const float *q, float *qrot, unsigned char *qbar, float *vl,
                        float *delta, int32_t *sq) {
+    float *qn = query_for(ix, &q);
     rotate_query(ix, q, qrot);
     orc_quantize_query(qrot, ix->d, qbar, vl, delta, sq);
+    free(qn);
 }
 
 /* ------------------------------------------------------------------ */
@@ -731,6 +781,7 @@ int orc_search(const orc_index *ix, const float *q, uint32_t k, uint32_t ef, flo
                int32_t trace_cap, int32_t *trace_n, uint32_t *path, uint32_t path_cap) {
     if (!ix || !q || k == 0 || ef < k || !ids || !dists || !stats) return ORC_ERR_ARG;
     const uint32_t d = ix->d, R = ix->R;
+    float *qn = query_for(ix, &q);
     orc_query qq;
     float *qrot = (float *)malloc(sizeof(float) * d);
     qq.qbar = (unsigned char *)malloc(d);
@@ -848,5 +899,6 @@ int orc_search(const orc_index *ix, const float *q, uint32_t k, uint32_t ef, flo
     stats[1] = status;
     if (trace_n) *trace_n = tn;
     free(qrot); free(qq.qbar); free(visited); free(pool); free(vflag); free(res); free(cand);
+    free(qn);
     return ORC_OK;
 }

@@ -314,12 +314,21 @@ extern "C" int sqg_build_graph(const float *data, uint64_t n, uint32_t d, const 
 
 extern "C" int sqg_write_index2(const char *path, const float *data, uint64_t n, uint32_t d, const uint32_t *adj,
                                 uint32_t R, const float *rot, uint32_t entry, uint64_t seed_rotation,
-                                uint64_t seed_graph, int threads, uint32_t rotation_kind) {
+                                uint64_t seed_graph, int threads, uint32_t rotation_kind, uint32_t metric) {
     if (!path || !data || !adj || !rot || n == 0 || d == 0 || d % 32 != 0 || R == 0 || R % 32 != 0 || entry >= n ||
-        rotation_kind > 1 || (rotation_kind == 1 && (d & (d - 1)) != 0))
+        rotation_kind > 1 || (rotation_kind == 1 && (d & (d - 1)) != 0) || metric > sqg_fmt::kMetricCosine)
         return SQG_ERR_INVALID_ARG;
     for (uint64_t i = 0; i < n * R; ++i)
         if (adj[i] >= n) return SQG_ERR_INVALID_ARG;
+    if (metric == sqg_fmt::kMetricCosine) {  // a cosine index holds unit vectors (or zero vectors)
+        std::atomic<uint64_t> bad{0};
+        parallel_for(n, threads, [&](uint64_t v) {
+            double s = 0.0;
+            for (uint32_t i = 0; i < d; ++i) s += (double)data[v * d + i] * data[v * d + i];
+            if (s != 0.0 && std::fabs(s - 1.0) > 1e-4) bad++;
+        }, 4096);
+        if (bad.load()) return SQG_ERR_INVALID_ARG;
+    }
     sqg_fmt::Layout lay = sqg_fmt::layout(n, d, R);
 
     // P^-1 x for every vertex, fp64 (the rotation is linear, so the rotated
@@ -417,7 +426,7 @@ extern "C" int sqg_write_index2(const char *path, const float *data, uint64_t n,
         ok = put(buf.data(), buf.size());
     }
     sqg_fmt::fill_header(header.data(), lay, entry, seed_rotation, seed_graph, h,
-                         rotation_kind == 1 ? sqg_fmt::kVersionFjlt : sqg_fmt::kVersion);
+                         rotation_kind == 1 ? sqg_fmt::kVersionFjlt : sqg_fmt::kVersion, metric);
     ok = ok && std::fseek(f, 0, SEEK_SET) == 0 && std::fwrite(header.data(), 1, header.size(), f) == header.size();
     ok = (std::fclose(f) == 0) && ok;
     return ok ? SQG_OK : SQG_ERR_IO;
@@ -426,5 +435,6 @@ extern "C" int sqg_write_index2(const char *path, const float *data, uint64_t n,
 extern "C" int sqg_write_index(const char *path, const float *data, uint64_t n, uint32_t d, const uint32_t *adj,
                                uint32_t R, const float *rot, uint32_t entry, uint64_t seed_rotation,
                                uint64_t seed_graph, int threads) {
-    return sqg_write_index2(path, data, n, d, adj, R, rot, entry, seed_rotation, seed_graph, threads, 0);
+    return sqg_write_index2(path, data, n, d, adj, R, rot, entry, seed_rotation, seed_graph, threads, 0,
+                            sqg_fmt::kMetricL2);
 }

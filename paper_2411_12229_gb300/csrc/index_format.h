@@ -62,8 +62,13 @@ inline uint64_t fnv_words(uint64_t h, const unsigned char *p, uint64_t nbytes) {
     return h;
 }
 
+// Metric of an index: squared Euclidean, or cosine similarity served as
+// Euclidean search between unit vectors (the file holds unit-norm vectors,
+// the search normalizes every query first).
+constexpr uint32_t kMetricL2 = 0, kMetricCosine = 1;
+
 inline void fill_header(unsigned char *h, const Layout &l, uint32_t entry, uint64_t seed_rot, uint64_t seed_graph,
-                        uint64_t payload_hash, uint32_t version = kVersion) {
+                        uint64_t payload_hash, uint32_t version = kVersion, uint32_t metric = kMetricL2) {
     std::memset(h, 0, kHeaderBytes);
     std::memcpy(h, "SQG1", 4);
     store_u32(h + 4, version);
@@ -72,7 +77,7 @@ inline void fill_header(unsigned char *h, const Layout &l, uint32_t entry, uint6
     store_u32(h + 20, l.R);
     store_u32(h + 24, l.block_bytes);
     store_u32(h + 28, entry);
-    store_u32(h + 32, 0);  // metric: squared Euclidean
+    store_u32(h + 32, metric);
     store_u32(h + 36, l.off_codes);
     store_u32(h + 40, l.off_factors);
     store_u32(h + 44, l.off_ids);
@@ -125,7 +130,7 @@ inline bool parse_header(const unsigned char *h, uint64_t file_size, Header &out
     out.version = version;
     out.payload_hash = load_u64(h + 88);
     out.seed_rot = load_u64(h + 72);
-    return out.entry < n && out.metric == 0;
+    return out.entry < n && out.metric <= kMetricCosine;
 }
 
 }  // namespace sqg_fmt

@@ -104,13 +104,25 @@ def build_graph(data: np.ndarray, cand: np.ndarray, R: int, entry: int, seed: in
                      repairs=int(st[3]))
 
 
+def unit_rows(data: np.ndarray, chunk: int = 1 << 16) -> np.ndarray:
+    """Each row scaled to unit norm (norm in fp64; zero rows stay zero):
+    the vectors of a cosine index."""
+    out = np.empty(data.shape, np.float32)
+    for a in range(0, data.shape[0], chunk):
+        x = data[a:a + chunk].astype(np.float64)
+        nrm = np.sqrt((x * x).sum(axis=1, keepdims=True))
+        out[a:a + chunk] = np.where(nrm > 0, x / np.where(nrm > 0, nrm, 1.0), 0.0)
+    return out
+
+
 def write_index(path, data: np.ndarray, adj: np.ndarray, rot: np.ndarray, entry: int, seed_rotation: int,
-                seed_graph: int, threads: int = 0, rotation_kind: int = 0) -> None:
+                seed_graph: int, threads: int = 0, rotation_kind: int = 0, metric: int = 0) -> None:
     data = np.ascontiguousarray(data, dtype=np.float32)
     adj = np.ascontiguousarray(adj, dtype=np.uint32)
     rot = np.ascontiguousarray(rot, dtype=np.float32)
     B.check(B.lib().sqg_write_index2(str(path).encode(), _p(data), data.shape[0], data.shape[1], _p(adj),
-                                     adj.shape[1], _p(rot), entry, seed_rotation, seed_graph, threads, rotation_kind),
+                                     adj.shape[1], _p(rot), entry, seed_rotation, seed_graph, threads, rotation_kind,
+                                     metric),
             f"sqg_write_index2({path})")
 
 
@@ -137,7 +149,7 @@ def random_graph(n: int, R: int, seed: int) -> np.ndarray:
 def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None, ef_build: int = 128,
                 cand_k: int | None = None, path_cand: int | None = None, rot_seed: int = 2, graph_seed: int = 3,
                 device: int | None = None, init: str = "auto", threads: int = 0, rotation: str = "dense",
-                log=None) -> dict:
+                metric: str = "l2", log=None) -> dict:
     """Build an index file at `path` from base vectors `data` (n x d).
 
     device=None: host-only build from an exact kNN (small n).
@@ -149,9 +161,18 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
 
     rotation "dense": a Haar-random P^-1 (stored, applied as a d x d
     product); "fjlt": the fast JLT of Sec. 3.1.4, the data zero-padded to
-    the next power of 2 (queries are padded the same way by the API)."""
+    the next power of 2 (queries are padded the same way by the API).
+
+    metric "l2": squared Euclidean; "cosine": cosine similarity as
+    Euclidean search between unit vectors -- the data are scaled to unit
+    norm here, the library scales every query (Sec. 3 names both metrics)."""
     t0 = time.time()
     data = np.ascontiguousarray(data, dtype=np.float32)
+    if metric not in ("l2", "cosine"):
+        raise ValueError("metric is 'l2' or 'cosine'")
+    mcode = 1 if metric == "cosine" else 0
+    if mcode:
+        data = unit_rows(data)
     if rotation == "fjlt":
         dp = 1 << max(5, int(np.ceil(np.log2(data.shape[1]))))
         if dp != data.shape[1]:
@@ -175,7 +196,7 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
         adj = random_graph(n, R, graph_seed)
     if iterations is None:
         iterations = 0 if device is None else (3 if init == "random" else 1)
-    write_index(tmp if iterations else path, data, adj, rot, entry, rot_seed, graph_seed, threads, kind)
+    write_index(tmp if iterations else path, data, adj, rot, entry, rot_seed, graph_seed, threads, kind, mcode)
     if iterations:
         import torch
 
@@ -201,7 +222,7 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
             ix.close()
             adj, st = build_graph(data, cand, R, entry, graph_seed + it + 1, threads)
             final = it == iterations - 1
-            write_index(path if final else tmp, data, adj, rot, entry, rot_seed, graph_seed, threads, kind)
+            write_index(path if final else tmp, data, adj, rot, entry, rot_seed, graph_seed, threads, kind, mcode)
             info["iterations"].append(dict(source="gpu-search", seconds=time.time() - t1, **st))
             if log:
                 log(f"build iteration {it + 1}/{iterations}: {time.time() - t1:.1f}s {st}")

@@ -223,7 +223,7 @@ def test_fjlt_index_header_and_writer_checks(lib_built, oracle_mod, tmp_path):
     ptr = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
     for kind in (1, 2):
         rc = B.lib().sqg_write_index2(str(tmp_path / "bad.sqg").encode(), ptr(x), 100, 96, ptr(adj), 32, ptr(rot),
-                                      0, 5, 3, 1, kind)
+                                      0, 5, 3, 1, kind, 0)
         assert rc == -1  # SQG_ERR_INVALID_ARG
     p = tmp_path / "ok.sqg"
     ib.build_index(p, x, 32, rotation="fjlt")
@@ -232,3 +232,52 @@ def test_fjlt_index_header_and_writer_checks(lib_built, oracle_mod, tmp_path):
     O = oracle_mod.Index(p)
     assert O.d == 128
     np.testing.assert_array_equal(O.fjlt_signs(), ib.fjlt_signs(128, 2))
+
+
+def _rehash_header(buf: bytearray) -> None:
+    """FNV-1a 64 over the header's first twelve little-endian u64 words."""
+    h = 0xCBF29CE484222325
+    for i in range(0, 96, 8):
+        h = ((h ^ int.from_bytes(buf[i:i + 8], "little")) * 0x100000001B3) & 0xFFFFFFFFFFFFFFFF
+    buf[96:104] = h.to_bytes(8, "little")
+
+
+def test_metric_field_and_writer_checks(lib_built, oracle_mod, tiny_index, tmp_path):
+    """Metric 0 (squared Euclidean) and 1 (cosine) load; any other value is
+    a format error for the library and the oracle.  The writer takes metric
+    1 only for unit (or zero) vectors; the builder normalizes the data."""
+    from paper_2411_12229_gb300 import _binding as B
+    from paper_2411_12229_gb300 import index_builder as ib
+    data = bytearray(pathlib.Path(tiny_index[0]).read_bytes())
+    h = C.c_void_p()
+    for metric, ok in ((0, True), (1, True), (2, False), (7, False)):
+        buf = bytearray(data)
+        buf[32:36] = metric.to_bytes(4, "little")
+        _rehash_header(buf)
+        p = tmp_path / f"m{metric}.sqg"
+        p.write_bytes(bytes(buf))
+        if ok:
+            assert oracle_mod.Index(p).metric == metric
+        else:
+            assert lib_built.sqg_index_load(str(p).encode(), 0, C.byref(h)) == -3
+            with pytest.raises(OSError):
+                oracle_mod.Index(p)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((100, 64)).astype(np.float32)
+    adj = ib.random_graph(100, 32, 1)
+    rot = np.eye(64, dtype=np.float32)
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    out = str(tmp_path / "w.sqg").encode()
+    assert B.lib().sqg_write_index2(out, ptr(x), 100, 64, ptr(adj), 32, ptr(rot), 0, 5, 3, 1, 0, 1) == -1
+    assert B.lib().sqg_write_index2(out, ptr(x), 100, 64, ptr(adj), 32, ptr(rot), 0, 5, 3, 1, 0, 2) == -1
+    xu = ib.unit_rows(x)
+    xu[7] = 0.0  # a zero vector is allowed
+    assert B.lib().sqg_write_index2(out, ptr(xu), 100, 64, ptr(adj), 32, ptr(rot), 0, 5, 3, 1, 0, 1) == 0
+    assert oracle_mod.Index(tmp_path / "w.sqg").metric == 1
+    np.testing.assert_allclose(np.linalg.norm(np.delete(xu, 7, 0).astype(np.float64), axis=1), 1.0, atol=1e-6)
+    with pytest.raises(ValueError):
+        ib.build_index(tmp_path / "b.sqg", x, 32, metric="dot")
+    ib.build_index(tmp_path / "c.sqg", x, 32, metric="cosine")
+    O = oracle_mod.Index(tmp_path / "c.sqg")
+    assert O.metric == 1
+    np.testing.assert_allclose(O.raw_all(), ib.unit_rows(x), rtol=0, atol=0)

@@ -513,3 +513,94 @@ def test_fjlt_index_full_beam_returns_exact_knn(small_fjlt_graph, oracle_mod):
         np.testing.assert_allclose(dists, gd, rtol=1e-5)
         r = O.prepare_query(q)
         np.testing.assert_array_equal(r["qrot"], oracle_mod.fjlt_f32(O.fjlt_signs(), q))
+
+
+# --------------------------------------------------------------- cosine similarity (R16)
+
+def test_normalize_closed_form(oracle_mod):
+    """(3, 4) has norm 5 exactly, so q/||q|| is fl(3/5), fl(4/5); a power of
+    2 times a basis vector normalizes exactly to it; a zero query is kept."""
+    for d in (32, 96, 1536):
+        q = np.zeros(d, np.float32)
+        q[1], q[d - 2] = 3.0, 4.0
+        r = oracle_mod.normalize_f32(q)
+        assert r[1] == np.float32(3) / np.float32(5) and r[d - 2] == np.float32(4) / np.float32(5)
+        assert np.count_nonzero(r) == 2
+        e = np.zeros(d, np.float32)
+        e[d // 3] = -2.0 ** 40
+        r = oracle_mod.normalize_f32(e)
+        assert r[d // 3] == -1.0 and np.count_nonzero(r) == 1
+        np.testing.assert_array_equal(oracle_mod.normalize_f32(np.zeros(d, np.float32)), 0.0)
+
+
+def test_normalize_within_its_rounding_bound(oracle_mod):
+    """Against q/||q|| in fp64: ||q||^2 takes n = 4 ceil(d/128) + 5 roundings
+    on its longest path (fmaf chain of a lane, then the 5 butterfly sums), so
+    its relative error is <= n u; the square root halves that and adds u/2,
+    the division adds u/2: per coordinate |err| <= (n/2 + 1.1) u |q_i|/||q||."""
+    rng = np.random.default_rng(21)
+    u = 2.0 ** -24
+    for d in (32, 96, 128, 960, 1536, 2048):
+        for scale in (1e-3, 1.0, 37.5):
+            q = (rng.standard_normal(d) * scale).astype(np.float32)
+            r = oracle_mod.normalize_f32(q).astype(np.float64)
+            ref = q.astype(np.float64) / np.linalg.norm(q.astype(np.float64))
+            nr = 4 * -(-d // 128) + 5
+            assert np.all(np.abs(r - ref) <= (nr / 2 + 1.1) * u * np.abs(ref) + 1e-45)
+            assert abs(np.linalg.norm(r) - 1.0) < (nr / 2 + 2) * u
+
+
+def test_normalize_scale_invariance_by_powers_of_two(oracle_mod):
+    """Scaling q by 2^k scales every rounded step exactly: same unit vector."""
+    rng = np.random.default_rng(22)
+    q = rng.standard_normal(960).astype(np.float32)
+    base = oracle_mod.normalize_f32(q)
+    for k in (-20, -3, 5, 30):
+        np.testing.assert_array_equal(oracle_mod.normalize_f32(q * np.float32(2.0 ** k)), base)
+
+
+@pytest.fixture(scope="module")
+def small_cosine_graph(tmp_path_factory, lib_built, oracle_mod):
+    """300 unit vectors of d = 64 (the cosine build normalizes the data)."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    from paper_2411_12229_gb300 import synth
+    w = synth.small(synth.TINY_10K_D128.with_(d=64), 300, 20, n_components=4)
+    x = synth.base(w)
+    p = tmp_path_factory.mktemp("gc") / "g300c.sqg"
+    ib.build_index(p, x, 32, metric="cosine")
+    return oracle_mod.Index(p), x, synth.queries(w)
+
+
+def test_cosine_index_full_beam_returns_the_most_similar(small_cosine_graph, oracle_mod):
+    """R16 on a whole search: on a cosine index a full beam returns the k
+    vectors of largest cosine similarity to the raw (unnormalized) query,
+    by brute force in fp64, and distances 2 - 2 cos; the stored vectors
+    have unit norm."""
+    O, x, qs = small_cosine_graph
+    assert O.metric == 1
+    raw = O.raw_all().astype(np.float64)
+    np.testing.assert_allclose(np.linalg.norm(raw, axis=1), 1.0, atol=1e-6)
+    xn = x.astype(np.float64) / np.linalg.norm(x.astype(np.float64), axis=1, keepdims=True)
+    ef = O.n * (O.R + 1)
+    for i in range(6):
+        q = qs[i] * np.float32(3.0 + i)  # any positive scale
+        ids, dists, hops, st = O.search(q, 10, ef, hop_cap=10 * ef)
+        cos = xn @ (q.astype(np.float64) / np.linalg.norm(q.astype(np.float64)))
+        order = np.lexsort((np.arange(O.n), -cos))[:10]
+        assert hops == O.n and st == 0
+        np.testing.assert_array_equal(ids, order)
+        np.testing.assert_allclose(dists, 2.0 - 2.0 * cos[order], atol=2e-6)
+
+
+def test_cosine_search_sees_the_normalized_query(small_cosine_graph, oracle_mod):
+    """Every step uses q/||q||: a power-of-2 multiple of q gives the same
+    search bit for bit, and the prepared query is that of the unit vector
+    on a Euclidean reading of the same rotation."""
+    O, x, qs = small_cosine_graph
+    for i in range(4):
+        a = O.search(qs[i], 10, 24, path_cap=200)
+        b = O.search(qs[i] * np.float32(64.0), 10, 24, path_cap=200)
+        for u, v in zip(a, b):
+            np.testing.assert_array_equal(u, v)
+        r = O.prepare_query(qs[i])
+        np.testing.assert_array_equal(r["qrot"], oracle_mod.rotate_f32(O.rotation(), oracle_mod.normalize_f32(qs[i])))
