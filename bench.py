@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--stop-train", type=int, default=20000, help="training queries for the learned stop")
     ap.add_argument("--rotation", default="dense", choices=["dense", "fjlt"],
                     help="index rotation: dense P^-1, or the fast JLT (Sec. 3.1.4; data padded to a power of 2)")
+    ap.add_argument("--metric", default="l2", choices=["l2", "cosine"],
+                    help="index metric: squared Euclidean, or cosine similarity (unit vectors; the library "
+                         "normalizes every query, Sec. 3)")
     ap.add_argument("--prep", action="store_true",
                     help="time query preparation alone (rotation + 4-bit quantization), CUDA vs tensor cores")
     return ap.parse_args()
@@ -88,6 +91,8 @@ def cache_paths(args, w):
     c = pathlib.Path(args.cache)
     c.mkdir(parents=True, exist_ok=True)
     tag = f"{w.name}-n{w.n}-R{w.degree}-it{args.build_iters}-ef{args.ef_build}"
+    if args.metric != "l2":
+        tag += f"-{args.metric}"
     gt = c / f"{tag}-gt-q{w.n_queries}"  # the ground truth does not depend on the rotation
     if args.rotation != "dense":
         tag += f"-{args.rotation}"
@@ -106,7 +111,7 @@ def ensure_index(args, w, device, rank):
         log(f"building {idx.name}: n={w.n} d={w.d} R={w.degree}")
         info = ib.build_index(str(idx) + ".part", base, w.degree, device=device, init="random",
                               iterations=args.build_iters, ef_build=args.ef_build, cand_k=2 * w.degree,
-                              rotation=args.rotation, log=log)
+                              rotation=args.rotation, metric=args.metric, log=log)
         os.replace(str(idx) + ".part", idx)
         secs = time.time() - t
         log(f"built in {secs:.1f}s {info['iterations'][-1]}")
@@ -130,7 +135,11 @@ def ground_truth(args, w, gtp, queries, device, world):
         z = np.load(f)
         return z["ids"], z["dists"]
     t = time.time()
-    ids, dd = E.ground_truth(synth.base(w), queries, 100 if w.mixed_k else 10, device=device)
+    base = synth.base(w)
+    if args.metric == "cosine":  # the most similar = the nearest between unit vectors
+        from paper_2411_12229_gb300 import index_builder as ib
+        base, queries = ib.unit_rows(base), ib.unit_rows(queries)
+    ids, dd = E.ground_truth(base, queries, 100 if w.mixed_k else 10, device=device)
     np.savez(f, ids=ids, dists=dd)
     log(f"ground truth in {time.time() - t:.1f}s")
     return ids, dd
@@ -198,15 +207,16 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_record(workload_name, ef):
+def traffic_record(workload_name, ef, metric="l2"):
     """DRAM bytes per launch of the search kernel from a committed ncu
-    summary of the same launch (workload and ef), used only while the kernel
-    source is unchanged since."""
+    summary of the same launch (workload, index metric and ef), used only
+    while the kernel source is unchanged since."""
     p = ROOT / "profiles" / "search_kernel_traffic.json"
     if not p.exists():
         return None
     z = json.loads(p.read_text())
-    if z.get("kernel_digest") != kernel_digest() or z.get("workload") != workload_name or z.get("ef") != ef:
+    if (z.get("kernel_digest") != kernel_digest() or z.get("workload") != workload_name or z.get("ef") != ef
+            or z.get("metric", "l2") != metric):
         return None
     return z
 
@@ -324,10 +334,11 @@ def isolated_steps(graph, steps: int, flush) -> float:
     return float(np.mean(ms))
 
 
-def launches_per_step(d: int) -> int:
+def launches_per_step(d: int, metric: str = "l2") -> int:
     """Library kernels per search call: plan, rotation (tensor cores plus the
-    exact quantization from d = 512 up, else one CUDA-core kernel), search."""
-    return 4 if d >= 512 else 3
+    exact quantization from d = 512 up, else one CUDA-core kernel), search;
+    on a cosine index also the query normalization."""
+    return (4 if d >= 512 else 3) + (metric == "cosine")
 
 
 def bench_mixed(args, w, ix, qd, q, gt_ids, rank, world, dist, local):
@@ -390,7 +401,7 @@ def bench_mixed(args, w, ix, qd, q, gt_ids, rank, world, dist, local):
                          "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4), "peak_source": src,
                          "note": "step time (plan + rotation + search), not the search kernel alone"},
             "autotune": sorted(tune["table"], key=lambda r: r["ms"])[:6], "clocks": clk,
-            "hops_mean": round(float(hops.mean()), 2), "gpu_launches": launches_per_step(w.d) * args.steps}
+            "hops_mean": round(float(hops.mean()), 2), "gpu_launches": launches_per_step(w.d, args.metric) * args.steps}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -453,10 +464,10 @@ def bench_prep(args):
     n, nq, d = args.n or 1000, args.nq or w.n_queries, w.d
     ws = synth.small(w, n, 64)
     x = synth.base(ws)
-    path = pathlib.Path(args.cache) / f"prep-{w.name}-n{n}-{args.rotation}.sqg"
+    path = pathlib.Path(args.cache) / f"prep-{w.name}-n{n}-{args.rotation}-{args.metric}.sqg"
     path.parent.mkdir(parents=True, exist_ok=True)
     if not path.exists():
-        ib.build_index(path, x, w.degree, rotation=args.rotation)
+        ib.build_index(path, x, w.degree, rotation=args.rotation, metric=args.metric)
     ix = Index(path, 0)
     q = ix.fit_queries(torch.from_numpy(synth.queries(w.with_(n_queries=nq))).cuda())
     if ix.fjlt:  # the fast transform (no dense contraction, no tensor-core path)
@@ -656,7 +667,7 @@ def main():
     kern_mean = float(np.mean(kern_ms))
     achieved = alg_bytes / (kern_mean / 1e3) / 1e9
     peak, peak_src = measured_peaks()
-    tr = traffic_record(w.name, ef_sel)
+    tr = traffic_record(w.name, ef_sel, args.metric)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_src,
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
@@ -680,7 +691,7 @@ def main():
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_max, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "d": w.d, "degree": w.degree, "rotation": args.rotation,
+        "config": {"workload": w.name, "n": w.n, "d": w.d, "degree": w.degree, "rotation": args.rotation, "metric": args.metric,
                    "k": k, "ef": ef_sel,
                    "queries_per_step": nq, "recall@10": round(rec_sel, 4), "parallelism": f"replicas{world}",
                    "l2": f"index ({ix.n * ix.block_bytes / 1e9:.2f} GB) larger than L2, no flush between job "
@@ -693,7 +704,7 @@ def main():
                 "api": "Index.host_pipeline (2 streams), host wall clock"},
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "gpu_launches": launches_per_step(w.d) * args.steps,
+        "gpu_launches": launches_per_step(w.d, args.metric) * args.steps,
         "clocks": clk,
         "qps_at_recall": {str(t): next((s["qps"] for s in sweep if s["recall"] >= t), None)
                           for t in (0.90, 0.95, 0.99)},

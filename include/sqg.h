@@ -75,6 +75,8 @@ typedef struct {
     uint32_t off_codes, off_factors, off_ids; /* byte offsets inside a block */
     int32_t device;        /* CUDA device holding the index */
     uint64_t device_bytes; /* device memory held by the index */
+    uint32_t metric;       /* 0 squared Euclidean; 1 cosine (see sqg_index_load) */
+    uint32_t version;      /* file format version: 1 dense rotation, 2 fast JLT */
 } sqg_info;
 
 typedef struct {
@@ -132,7 +134,7 @@ const char *sqg_error_string(int code);
  * File v1, little-endian: 256-byte header
  *   0 "SQG1" | 4 version u32 (1: dense rotation; 2: the fast JLT, see
  *   sqg_write_index2) | 8 n u64 | 16 d u32 | 20 R u32 |
- *   24 block_bytes u32 | 28 entry u32 | 32 metric u32 (0 = squared L2) |
+ *   24 block_bytes u32 | 28 entry u32 | 32 metric u32 (see below) |
  *   36 off_codes | 40 off_factors | 44 off_ids (u32) | 48 rot_offset u64 |
  *   56 blocks_offset u64 | 64 file_bytes u64 | 72 seed_rotation u64 |
  *   80 seed_graph u64 | 88 payload_hash u64 | 96 header_hash u64
@@ -142,7 +144,16 @@ const char *sqg_error_string(int code);
  *   raw[d] fp32 | codes: u32 word w of neighbour j at index w*R + j, bit
  *   (i mod 32) of word i/32 = code bit of dimension i | f_add[R],
  *   f_rescale[R], f_err[R] fp32, popcount[R] u32 | ids[R] u32 | zero pad
- *   to a multiple of 128 bytes. */
+ *   to a multiple of 128 bytes.
+ * Metric (Sec. 3: the method serves Euclidean distance and cosine
+ * similarity): 0 = squared Euclidean; 1 = cosine, served as Euclidean
+ * search between unit vectors -- the raw vectors are unit-norm (or zero),
+ * and every search, sqg_prepare_queries(_tc) and sqg_estimate_block first
+ * scales each query to unit norm: s = ||q||^2 as 32 partial fmaf sums over
+ * float4 chunks l, l+32, ... then pairwise sums of partials l and l^16, ^8,
+ * ^4, ^2, ^1, and q_i / fl(sqrt(s)) per coordinate (a query with s = 0 or s
+ * not finite is used as it is).  Distances returned are then
+ * ||q/||q|| - x||^2 = 2 - 2 cos(q, x). */
 int sqg_index_load(const char *path, int device, sqg_index **out);
 
 /* Free an index and its device memory (synchronizes the device). NULL is a no-op. */
@@ -157,7 +168,8 @@ size_t sqg_workspace_size(const sqg_index *ix, int nq, int max_k, int max_ef);
 
 /* Search nq queries (Algorithm 1 per query, with multiple estimated
  * distances and implicit re-ranking, Sec. 3.1).
- *   queries  nq x d fp32 row-major
+ *   queries  nq x d fp32 row-major, 16-byte aligned (else SQG_ERR_INVALID_ARG,
+ *            nothing launched; every CUDA allocation is)
  *   k, ef    nq int32 each: results wanted and beam size n_b per query
  *            (1 <= k <= SQG_MAX_K, k <= ef <= SQG_MAX_EF)
  *   out_ids, out_dists: ragged, query i at offset sum_{j<i} k[j]; k[i]
@@ -172,7 +184,7 @@ int sqg_search(const sqg_index *ix, const float *queries, int nq, const int32_t 
                uint32_t *out_ids, float *out_dists, sqg_stream_t stream);
 
 /* sqg_search with explicit parameters (NULL = defaults), a caller-owned
- * workspace (NULL = stream-ordered allocation) of ws_bytes >=
+ * workspace (NULL = stream-ordered allocation; else 256-byte aligned) of ws_bytes >=
  * sqg_workspace_size(), and optional per-query stats (nq entries, device).
  * With params->max_k and max_ef given and a workspace, the call is
  * asynchronous and allocates nothing.  SQG_ERR_CAPACITY when the workspace
@@ -196,7 +208,8 @@ size_t sqg_workspace_size_ex(const sqg_index *ix, int nq, int max_k, int max_ef,
  *              of the 4-bit code qbar_i
  *   out_scal   nq x 4: (v_l, delta, Sq as float, 1/sqrt(d)) with
  *              delta = (v_r - v_l)/15 and qbar_i = min(15,
- *              trunc((q'_i - v_l) * 15/(v_r - v_l) + 0.5)) */
+ *              trunc((q'_i - v_l) * 15/(v_r - v_l) + 0.5))
+ * queries and the three outputs 16-byte aligned, else SQG_ERR_INVALID_ARG. */
 int sqg_prepare_queries(const sqg_index *ix, const float *queries, int nq, float *out_qrot,
                         uint32_t *out_planes, float *out_scal, sqg_stream_t stream);
 
@@ -215,7 +228,8 @@ int sqg_prepare_queries_tc(const sqg_index *ix, const float *queries, int nq, fl
  *   est    = f_add + dist_c + f_rescale * ip,
  *            ip = fmaf(delta, 2S - Sq, v_l (2 popcount - d)) / sqrt(d)
  *   key    = est - eps0 * f_err * sqrt(dist_c)
- * and dist_c[i] = exact squared distance of query i to v[i]. */
+ * and dist_c[i] = exact squared distance of query i to v[i]; queries
+ * 16-byte aligned. */
 int sqg_estimate_block(const sqg_index *ix, const float *queries, int nq, const uint32_t *v, float eps0,
                        int32_t *out_S, float *out_est, float *out_key, float *out_dist_c, sqg_stream_t stream);
 
@@ -322,15 +336,18 @@ int sqg_write_index(const char *path, const float *data, uint64_t n, uint32_t d,
                     uint32_t R, const float *rot, uint32_t entry, uint64_t seed_rotation, uint64_t seed_graph,
                     int threads);
 
-/* sqg_write_index with the rotation's kind: 0 = the dense P^-1 (version 1);
+/* sqg_write_index with the rotation's kind and the metric.  rotation_kind
+ * 0 = the dense P^-1 (version 1);
  * 1 = the fast JLT of Sec. 3.1.4 (version 2, d a power of 2): three rounds
  * of a sign flip s_r and the Walsh-Hadamard transform scaled by 1/sqrt(d),
  * s_r[i] = -1 when bit 63 of splitmix64(seed_rotation ^ (r << 32 | i)) is
  * set.  `rot` must then hold that transform as a dense matrix (the edges'
- * codes are built with it); queries are rotated by the fast transform. */
+ * codes are built with it); queries are rotated by the fast transform.
+ * metric 0 = squared Euclidean; 1 = cosine: every vector of `data` must have
+ * ||x||^2 within 1e-4 of 1 (or be zero), else SQG_ERR_INVALID_ARG. */
 int sqg_write_index2(const char *path, const float *data, uint64_t n, uint32_t d, const uint32_t *adj,
                      uint32_t R, const float *rot, uint32_t entry, uint64_t seed_rotation, uint64_t seed_graph,
-                     int threads, uint32_t rotation_kind);
+                     int threads, uint32_t rotation_kind, uint32_t metric);
 
 #ifdef __cplusplus
 }

@@ -42,7 +42,8 @@ class SearchParams(C.Structure):
 class Info(C.Structure):
     _fields_ = [("n", C.c_uint64), ("d", C.c_uint32), ("degree", C.c_uint32), ("block_bytes", C.c_uint32),
                 ("entry", C.c_uint32), ("off_codes", C.c_uint32), ("off_factors", C.c_uint32),
-                ("off_ids", C.c_uint32), ("device", C.c_int32), ("device_bytes", C.c_uint64)]
+                ("off_ids", C.c_uint32), ("device", C.c_int32), ("device_bytes", C.c_uint64),
+                ("metric", C.c_uint32), ("version", C.c_uint32)]
 
 
 _lock = threading.Lock()
@@ -68,7 +69,7 @@ _SIGS = {
     "sqg_build_graph": (I32, [P, U64, U32, P, U32, U32, U32, U64, P, P, I32]),
     "sqg_medoid": (U32, [P, U64, U32, I32]),
     "sqg_write_index": (I32, [C.c_char_p, P, U64, U32, P, U32, P, U32, U64, U64, I32]),
-    "sqg_write_index2": (I32, [C.c_char_p, P, U64, U32, P, U32, P, U32, U64, U64, I32, U32]),
+    "sqg_write_index2": (I32, [C.c_char_p, P, U64, U32, P, U32, P, U32, U64, U64, I32, U32, U32]),
     "sqg_search_noalloc": (I32, [P, P, I32, P, P, I32, I32, P, P, P]),
     "sqg_noalloc_scratch_bytes": (SZ, []),
     "sqg_mlp_grad": (I32, [P, P, P, P, I32, P, P, P, P]),

@@ -44,8 +44,10 @@ class Index:
         self.n, self.d, self.degree = int(info.n), int(info.d), int(info.degree)
         self.block_bytes, self.entry = int(info.block_bytes), int(info.entry)
         self.device_bytes = int(info.device_bytes)
-        with open(path, "rb") as f:  # header version 2: the fast JLT (data zero-padded to d)
-            self.fjlt = int.from_bytes(f.read(8)[4:8], "little") == 2
+        self.fjlt = int(info.version) == 2  # the fast JLT (data zero-padded to d)
+        # "l2" (squared Euclidean) or "cosine" (unit vectors; queries are
+        # normalized by the library, distances are 2 - 2 cos)
+        self.metric = "cosine" if int(info.metric) == 1 else "l2"
 
     def fit_queries(self, queries: torch.Tensor) -> torch.Tensor:
         """Queries of a fast-JLT index may have fewer columns than d (the data

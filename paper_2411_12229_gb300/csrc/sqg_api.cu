@@ -26,6 +26,8 @@ struct sqg_index {
     float *d_rot;
     float *d_rot_hi, *d_rot_lo;  // tf32 split of the rotation for the tensor-core path
     bool fjlt;                   // version 2: queries are rotated by the fast JLT
+    bool cosine;                 // metric 1: queries are scaled to unit norm first
+    uint32_t version;
     float *d_signs;              // its 3 x d signs
     uint32_t *d_status;
     int num_sms;
@@ -48,6 +50,8 @@ struct DeviceGuard {
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+// The kernels read query rows as float4 and workspace regions as uint4.
+inline bool aligned(const void *p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
 
 // ---------------------------------------------------------------- kernels
 
@@ -196,6 +200,44 @@ __global__ void __launch_bounds__(256) rotate_kernel(const float *__restrict__ q
     }
 }
 
+// Cosine similarity as Euclidean search between unit vectors: q / ||q||,
+// one warp per query.  ||q||^2 in the exact distance's order (lane l sums
+// float4 chunks l, l+32, ... with fmaf(x, x, acc), then the xor butterfly
+// 16, 8, 4, 2, 1), then each coordinate divided by fl(sqrt(||q||^2)); a
+// query whose squared norm is 0 or not finite is copied as it is.
+constexpr int kNormWarps = 8;
+__global__ void __launch_bounds__(kNormWarps * 32) normalize_kernel(const float *__restrict__ q,
+                                                                    float *__restrict__ out, int nq, uint32_t d) {
+    const int lane = threadIdx.x & 31;
+    const long long qi = (long long)blockIdx.x * kNormWarps + (threadIdx.x >> 5);
+    if (qi >= nq) return;  // uniform over the warp
+    const float4 *src = reinterpret_cast<const float4 *>(q + (size_t)qi * d);
+    float4 *dst = reinterpret_cast<float4 *>(out + (size_t)qi * d);
+    const uint32_t nch = d / 4;
+    float acc = 0.0f;
+    for (uint32_t c = lane; c < nch; c += 32) {
+        const float4 x = src[c];
+        acc = __fmaf_rn(x.x, x.x, acc);
+        acc = __fmaf_rn(x.y, x.y, acc);
+        acc = __fmaf_rn(x.z, x.z, acc);
+        acc = __fmaf_rn(x.w, x.w, acc);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    const bool scale = acc > 0.0f && acc <= 3.40282347e38f;
+    const float r = __fsqrt_rn(acc);
+    for (uint32_t c = lane; c < nch; c += 32) {
+        float4 x = src[c];
+        if (scale) {
+            x.x = __fdiv_rn(x.x, r);
+            x.y = __fdiv_rn(x.y, r);
+            x.z = __fdiv_rn(x.z, r);
+            x.w = __fdiv_rn(x.w, r);
+        }
+        dst[c] = x;
+    }
+}
+
 // Quantized query export (test entry point): one warp per query.
 __global__ void quantize_kernel(const float *qrot, int nq, int d, uint32_t *planes, float *scal) {
     const int lane = threadIdx.x & 31;
@@ -277,7 +319,8 @@ struct LaunchPlan {
     SearchArgs a;  // layout fields filled in
     bool ghash;
     // workspace layout
-    size_t ws_offsets, ws_qrot, ws_queue, ws_maxes, ws_stats, ws_ghash, ws_planes, ws_scal, ws_mlp, ws_total;
+    size_t ws_offsets, ws_qrot, ws_queue, ws_maxes, ws_stats, ws_ghash, ws_planes, ws_scal, ws_mlp, ws_qnorm,
+        ws_total;
 };
 
 int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_search_params &p, LaunchPlan &pl) {
@@ -373,8 +416,23 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     // the stop network, its two weight matrices transposed to [in][out]
     pl.ws_mlp = w;
     if (p.stop_mlp) w = align_up(w + sizeof(float) * SQG_MLP_NPARAM, 256);
+    // the unit-norm queries of a cosine index
+    pl.ws_qnorm = w;
+    if (ix->cosine) w = align_up(w + 4 * (size_t)std::max(nq, 1) * d, 256);
     pl.ws_total = w;
     return SQG_OK;
+}
+
+// The queries every later step reads: on a cosine index their unit-norm
+// copies, written to `scratch` (nq x d floats), else the caller's.
+const float *queries_for(const sqg_index *ix, const float *queries, int nq, float *scratch, cudaStream_t stream,
+                         cudaError_t *e) {
+    *e = cudaSuccess;
+    if (!ix->cosine) return queries;
+    const long long blocks = ((long long)nq + kNormWarps - 1) / kNormWarps;
+    normalize_kernel<<<(unsigned)blocks, kNormWarps * 32, 0, stream>>>(queries, scratch, nq, ix->lay.d);
+    *e = cudaGetLastError();
+    return scratch;
 }
 
 // q' on the CUDA cores: the fast JLT for a version-2 index, else the dense
@@ -469,6 +527,8 @@ extern "C" int sqg_index_load(const char *path, int device, sqg_index **out) {
     ix->lay = L;
     ix->entry = h.entry;
     ix->fjlt = h.version == sqg_fmt::kVersionFjlt;
+    ix->cosine = h.metric == sqg_fmt::kMetricCosine;
+    ix->version = h.version;
     cudaDeviceGetAttribute(&ix->num_sms, cudaDevAttrMultiProcessorCount, device);
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -575,6 +635,8 @@ extern "C" int sqg_index_info(const sqg_index *ix, sqg_info *out) {
     out->off_ids = ix->lay.off_ids;
     out->device = ix->device;
     out->device_bytes = (uint64_t)ix->lay.n * ix->lay.block_bytes + 4ull * ix->lay.d * ix->lay.d + 4;
+    out->metric = ix->cosine ? sqg_fmt::kMetricCosine : sqg_fmt::kMetricL2;
+    out->version = ix->version;
     return SQG_OK;
 }
 
@@ -611,6 +673,7 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     if (!ix || nq < 0) return SQG_ERR_INVALID_ARG;
     if (nq == 0) return SQG_OK;
     if (!queries || !k || !ef || !out_ids || !out_dists) return SQG_ERR_INVALID_ARG;
+    if (!aligned(queries, 16) || (workspace && !aligned(workspace, 256))) return SQG_ERR_INVALID_ARG;
     sqg_search_params p = params ? *params : default_params();
     if (params && p.stop_every == 0) p.stop_every = 1;
     if (check_params(p) != SQG_OK) return SQG_ERR_INVALID_ARG;
@@ -642,6 +705,11 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
         return SQG_ERR_CAPACITY;
     }
     char *ws = reinterpret_cast<char *>(workspace);
+    queries = queries_for(ix, queries, nq, reinterpret_cast<float *>(ws + pl.ws_qnorm), stream, &e);
+    if (e != cudaSuccess) {
+        if (own_ws) cudaFreeAsync(workspace, stream);
+        return SQG_ERR_CUDA;
+    }
     SearchArgs &a = pl.a;
     a.blocks = ix->d_blocks;
     a.block_bytes = ix->lay.block_bytes;
@@ -755,10 +823,19 @@ extern "C" int sqg_prepare_queries(const sqg_index *ix, const float *queries, in
     if (!ix || nq < 0) return SQG_ERR_INVALID_ARG;
     if (nq == 0) return SQG_OK;
     if (!queries || !out_qrot || !out_planes || !out_scal) return SQG_ERR_INVALID_ARG;
+    if (!aligned(queries, 16) || !aligned(out_qrot, 16) || !aligned(out_planes, 16) || !aligned(out_scal, 16))
+        return SQG_ERR_INVALID_ARG;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     DeviceGuard g(ix->device);
     const int d = (int)ix->lay.d;
-    if (rotate_simt(ix, queries, out_qrot, nq, stream) != cudaSuccess) return SQG_ERR_CUDA;
+    float *qn = nullptr;
+    if (ix->cosine && cudaMallocAsync(&qn, sizeof(float) * (size_t)nq * d, stream) != cudaSuccess)
+        return SQG_ERR_OOM;
+    cudaError_t e;
+    queries = queries_for(ix, queries, nq, qn, stream, &e);
+    if (e == cudaSuccess) e = rotate_simt(ix, queries, out_qrot, nq, stream);
+    if (qn) cudaFreeAsync(qn, stream);
+    if (e != cudaSuccess) return SQG_ERR_CUDA;
     const int wpb = 4;
     quantize_kernel<<<(nq + wpb - 1) / wpb, wpb * 32, sizeof(uint32_t) * wpb * 4 * (d / 32), stream>>>(
         out_qrot, nq, d, out_planes, out_scal);
@@ -771,14 +848,23 @@ extern "C" int sqg_prepare_queries_tc(const sqg_index *ix, const float *queries,
     if (!ix || nq < 0) return SQG_ERR_INVALID_ARG;
     if (nq == 0) return SQG_OK;
     if (!queries || !out_qrot || !out_planes || !out_scal || !recomputed) return SQG_ERR_INVALID_ARG;
+    if (!aligned(queries, 16) || !aligned(out_qrot, 16) || !aligned(out_planes, 16) || !aligned(out_scal, 16))
+        return SQG_ERR_INVALID_ARG;
     if (ix->fjlt) return SQG_ERR_UNSUPPORTED;  // the fast JLT has no dense contraction to put on tensor cores
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     DeviceGuard g(ix->device);
     const int d = (int)ix->lay.d;
-    cudaError_t e = launch_rotate_tc(queries, ix->d_rot_hi, ix->d_rot_lo, out_qrot, nq, d, ix->d_status, stream);
+    float *qn = nullptr;
+    if (ix->cosine && cudaMallocAsync(&qn, sizeof(float) * (size_t)nq * d, stream) != cudaSuccess)
+        return SQG_ERR_OOM;
+    cudaError_t e;
+    queries = queries_for(ix, queries, nq, qn, stream, &e);
+    if (e == cudaSuccess)
+        e = launch_rotate_tc(queries, ix->d_rot_hi, ix->d_rot_lo, out_qrot, nq, d, ix->d_status, stream);
     if (e == cudaSuccess)
         e = launch_quantize_exact(queries, ix->d_rot, out_qrot, nq, d, out_planes,
                                   reinterpret_cast<float4 *>(out_scal), recomputed, true, stream);
+    if (qn) cudaFreeAsync(qn, stream);
     return e == cudaSuccess ? SQG_OK : SQG_ERR_CUDA;
 }
 
@@ -788,12 +874,16 @@ extern "C" int sqg_estimate_block(const sqg_index *ix, const float *queries, int
     if (!ix || nq < 0 || !std::isfinite(eps0)) return SQG_ERR_INVALID_ARG;
     if (nq == 0) return SQG_OK;
     if (!queries || !v || !out_S || !out_est || !out_key || !out_dist_c) return SQG_ERR_INVALID_ARG;
+    if (!aligned(queries, 16)) return SQG_ERR_INVALID_ARG;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     DeviceGuard g(ix->device);
     const int d = (int)ix->lay.d;
-    float *qrot = nullptr;
-    if (cudaMallocAsync(&qrot, sizeof(float) * (size_t)nq * d, stream) != cudaSuccess) return SQG_ERR_OOM;
-    if (rotate_simt(ix, queries, qrot, nq, stream) != cudaSuccess) {
+    float *qrot = nullptr;  // q', then on a cosine index the unit-norm queries after it
+    const size_t qbytes = sizeof(float) * (size_t)nq * d;
+    if (cudaMallocAsync(&qrot, ix->cosine ? 2 * qbytes : qbytes, stream) != cudaSuccess) return SQG_ERR_OOM;
+    cudaError_t qe;
+    queries = queries_for(ix, queries, nq, qrot + (size_t)nq * d, stream, &qe);
+    if (qe != cudaSuccess || rotate_simt(ix, queries, qrot, nq, stream) != cudaSuccess) {
         cudaFreeAsync(qrot, stream);
         return SQG_ERR_CUDA;
     }

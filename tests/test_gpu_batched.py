@@ -64,3 +64,35 @@ def test_host_pipeline_returns_each_batch_in_order(tiny_index, oracle_mod):
         np.testing.assert_array_equal(ids, ref_ids.cpu().numpy())
         np.testing.assert_array_equal(dists, ref_d.cpu().numpy())
     assert pipe.drain() == []
+
+
+def test_misaligned_pointers_are_rejected_before_any_launch(tiny_index):
+    """Query rows are read as float4 and the workspace regions as uint4: a
+    query pointer off a 16-byte boundary, or a workspace off 256 bytes, is
+    an argument error caught on the host (nothing is launched)."""
+    from paper_2411_12229_gb300 import _binding as B
+    from paper_2411_12229_gb300.api import Index
+    p, x, q = tiny_index
+    ix = Index(p, 0)
+    nq = 16
+    qd = torch.from_numpy(q[:nq]).cuda()
+    k = torch.full((nq,), 10, dtype=torch.int32, device="cuda")
+    ef = torch.full((nq,), 32, dtype=torch.int32, device="cuda")
+    ids = torch.empty(nq * 10, dtype=torch.int32, device="cuda")
+    dd = torch.empty(nq * 10, dtype=torch.float32, device="cuda")
+    ws = torch.empty(1 << 22, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    L = B.lib()
+    # nq - 1 rows from one float in: in bounds even if it were read
+    assert L.sqg_search_ex(ix.handle, qd.data_ptr() + 4, nq - 1, k.data_ptr(), ef.data_ptr(), ids.data_ptr(),
+                           dd.data_ptr(), None, None, 0, None, s) == -1
+    assert L.sqg_search_ex(ix.handle, qd.data_ptr(), nq, k.data_ptr(), ef.data_ptr(), ids.data_ptr(),
+                           dd.data_ptr(), None, ws.data_ptr() + 16, ws.numel() - 16, None, s) == -1
+    qr = torch.empty((nq, ix.d), dtype=torch.float32, device="cuda")
+    pl = torch.empty((nq, 4, ix.d // 32), dtype=torch.int32, device="cuda")
+    sc = torch.empty((nq, 4), dtype=torch.float32, device="cuda")
+    assert L.sqg_prepare_queries(ix.handle, qd.data_ptr() + 4, nq - 1, qr.data_ptr(), pl.data_ptr(),
+                                 sc.data_ptr(), s) == -1
+    torch.cuda.synchronize()
+    a = ix.search(qd, 10, 32)  # the aligned call still works
+    assert a[0].shape == (nq, 10)
