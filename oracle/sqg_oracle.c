@@ -902,3 +902,186 @@ int orc_search(const orc_index *ix, const float *q, uint32_t k, uint32_t ef, flo
     free(qn);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Index construction: the "adjust G" step of Algorithm 2 (Sec. 3.2)  */
+/* ------------------------------------------------------------------ */
+
+/* An edge candidate of a vertex u: (exact distance to u, id).  Ordered by
+ * (dist, id) (R4); distances are orc_exact_dist_f32, symmetric in its two
+ * arguments (the differences are negated exactly). */
+typedef struct {
+    float d;
+    uint32_t id;
+} orc_cand;
+
+static int cand_less(orc_cand a, orc_cand b) { return a.d < b.d || (a.d == b.d && a.id < b.id); }
+
+static void sort_by_dist(orc_cand *a, int n) { /* insertion sort: plain and stable */
+    for (int i = 1; i < n; ++i) {
+        orc_cand x = a[i];
+        int j = i;
+        while (j > 0 && cand_less(x, a[j - 1])) { a[j] = a[j - 1]; --j; }
+        a[j] = x;
+    }
+}
+
+/* Drop repeated ids (their distances are equal), keep one of each. */
+static int unique_ids(orc_cand *a, int n) {
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        int seen = 0;
+        for (int j = 0; j < m && !seen; ++j) seen = a[j].id == a[i].id;
+        if (!seen) a[m++] = a[i];
+    }
+    return m;
+}
+
+static float vdist(const float *data, uint32_t d, uint32_t a, uint32_t b) {
+    return orc_exact_dist_f32(data + (uint64_t)a * d, data + (uint64_t)b * d, d);
+}
+
+/* NSG's occlusion rule (Sec. 3.2.1): walk the candidates nearest first and
+ * keep c unless an already kept w is nearer to c than u is (dist(w, c) <
+ * dist(u, c)); stop at R kept.  `c` sorted by (dist, id). */
+static int nsg_prune(const float *data, uint32_t d, const orc_cand *c, int nc, int R, orc_cand *kept) {
+    int nk = 0;
+    for (int i = 0; i < nc && nk < R; ++i) {
+        int occluded = 0;
+        for (int j = 0; j < nk && !occluded; ++j) occluded = vdist(data, d, kept[j].id, c[i].id) < c[i].d;
+        if (!occluded) kept[nk++] = c[i];
+    }
+    return nk;
+}
+
+/* The adaptive angle rule (Sec. 3.2.2), reading R11.  Every extra candidate
+ * c gets the largest cosine, at u, between c and a candidate w before it in
+ * (dist, id) order among kept and extra together: cos = (|uw|^2 + |uc|^2 -
+ * |wc|^2) / (2 |uw| |uc|) in fp32 (1 when a length is 0; -2 when nothing is
+ * before c).  Raising the angle threshold theta drops every c whose score
+ * is above cos(theta); the largest theta that leaves `need` candidates
+ * keeps exactly those scoring at most the need-th smallest score, and the
+ * `need` nearest of them are added.  Returns how many were added to out. */
+static int angle_supplement(const float *data, uint32_t d, const orc_cand *kept, int nk, const orc_cand *extra,
+                            int ne, int need, orc_cand *out) {
+    if (need <= 0 || ne == 0) return 0;
+    orc_cand *all = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)(nk + ne));
+    float *score = (float *)malloc(sizeof(float) * (size_t)ne);
+    float *sorted = (float *)malloc(sizeof(float) * (size_t)ne);
+    memcpy(all, kept, sizeof(orc_cand) * (size_t)nk);
+    memcpy(all + nk, extra, sizeof(orc_cand) * (size_t)ne);
+    sort_by_dist(all, nk + ne);
+    for (int e = 0; e < ne; ++e) {
+        float best = -2.0f;
+        for (int j = 0; j < nk + ne && cand_less(all[j], extra[e]); ++j) {
+            float dwc = vdist(data, d, all[j].id, extra[e].id);
+            float den = 2.0f * sqrtf(all[j].d) * sqrtf(extra[e].d);
+            float cs = den > 0.0f ? (all[j].d + extra[e].d - dwc) / den : 1.0f;
+            if (cs > best) best = cs;
+        }
+        score[e] = best;
+        sorted[e] = best;
+    }
+    int take = need < ne ? need : ne;
+    for (int i = 1; i < ne; ++i) { /* ascending scores */
+        float x = sorted[i];
+        int j = i;
+        while (j > 0 && x < sorted[j - 1]) { sorted[j] = sorted[j - 1]; --j; }
+        sorted[j] = x;
+    }
+    float thr = sorted[take - 1];
+    int no = 0;
+    for (int e = 0; e < ne && no < take; ++e) /* extra is in (dist, id) order */
+        if (score[e] <= thr) out[no++] = extra[e];
+    free(all); free(score); free(sorted);
+    return no;
+}
+
+/* The own candidates of u: ids from its candidate list (invalid ids, u
+ * itself and repeats dropped) with their distances, sorted by (dist, id). */
+static int own_candidates(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L, uint32_t u,
+                          orc_cand *c) {
+    int m = 0;
+    for (uint32_t t = 0; t < L; ++t) {
+        uint32_t v = cand[(uint64_t)u * L + t];
+        if (v == ORC_NO_ID || v >= n || v == u) continue;
+        c[m].id = v;
+        c[m].d = vdist(data, d, u, v);
+        ++m;
+    }
+    m = unique_ids(c, m);
+    sort_by_dist(c, m);
+    return m;
+}
+
+/* "Adjust G" of Algorithm 2 for every vertex, readings R11: (1) NSG-prune
+ * the vertex's own candidates to at most R' = min(R, n-1) edges; (2) offer
+ * every kept edge u -> v to v as the reverse candidate (u, dist) and prune
+ * v's kept edges plus its reverse candidates again; (3) a vertex left with
+ * fewer than R' edges is supplemented by the adaptive angle rule from its
+ * own and reverse candidates not yet kept, the nearest 2R' (d >= 512) or
+ * 3R' of them.  Writes each vertex's list sorted by (dist, id) to
+ * out[u*R ...] (ORC_NO_ID after its count) and its count to counts[u].
+ * The builder's random fill of a list still short and its reachability
+ * repair come after this and are not part of it. */
+int orc_adjust_graph(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L, uint32_t R,
+                     uint32_t *out, uint32_t *counts) {
+    if (!data || !cand || !out || !counts || n < 2 || R == 0 || L == 0 || d == 0 || d % 4 != 0) return ORC_ERR_ARG;
+    const int Rr = (int)(R < n - 1 ? R : n - 1);
+    orc_cand *k1 = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)n * (size_t)Rr);
+    int *n1 = (int *)calloc(n, sizeof(int));
+    int *indeg = (int *)calloc(n, sizeof(int));
+    orc_cand *c = (orc_cand *)malloc(sizeof(orc_cand) * L);
+    for (uint32_t u = 0; u < n; ++u) { /* (1) */
+        int m = own_candidates(data, n, d, cand, L, u, c);
+        n1[u] = nsg_prune(data, d, c, m, Rr, k1 + (size_t)u * Rr);
+        for (int j = 0; j < n1[u]; ++j) indeg[k1[(size_t)u * Rr + j].id]++;
+    }
+    uint64_t *roff = (uint64_t *)calloc(n + 1, sizeof(uint64_t));
+    for (uint64_t v = 0; v < n; ++v) roff[v + 1] = roff[v] + (uint64_t)indeg[v];
+    orc_cand *rev = (orc_cand *)malloc(sizeof(orc_cand) * (roff[n] ? roff[n] : 1));
+    uint64_t *fill = (uint64_t *)malloc(sizeof(uint64_t) * n);
+    memcpy(fill, roff, sizeof(uint64_t) * n);
+    for (uint32_t u = 0; u < n; ++u) /* (2) reverse candidates */
+        for (int j = 0; j < n1[u]; ++j) {
+            orc_cand e = k1[(size_t)u * Rr + j];
+            rev[fill[e.id]].id = u;
+            rev[fill[e.id]].d = e.d;
+            fill[e.id]++;
+        }
+    for (uint32_t u = 0; u < n; ++u) {
+        const int nr = (int)(roff[u + 1] - roff[u]);
+        orc_cand *pool = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)(n1[u] + nr + L));
+        memcpy(pool, k1 + (size_t)u * Rr, sizeof(orc_cand) * (size_t)n1[u]);
+        memcpy(pool + n1[u], rev + roff[u], sizeof(orc_cand) * (size_t)nr);
+        int np = unique_ids(pool, n1[u] + nr);
+        sort_by_dist(pool, np);
+        orc_cand *k2 = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)Rr);
+        int nk = nsg_prune(data, d, pool, np, Rr, k2);
+        if (nk < Rr) { /* (3) */
+            int m = own_candidates(data, n, d, cand, L, u, pool);
+            memcpy(pool + m, rev + roff[u], sizeof(orc_cand) * (size_t)nr);
+            int na = unique_ids(pool, m + nr);
+            int ne = 0;
+            for (int i = 0; i < na; ++i) {
+                int have = 0;
+                for (int j = 0; j < nk && !have; ++j) have = k2[j].id == pool[i].id;
+                if (!have) pool[ne++] = pool[i];
+            }
+            sort_by_dist(pool, ne);
+            int cap = d >= 512 ? 2 * Rr : 3 * Rr;
+            if (ne > cap) ne = cap;
+            orc_cand *sup = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)(ne ? ne : 1));
+            int ns = angle_supplement(data, d, k2, nk, pool, ne, Rr - nk, sup);
+            for (int i = 0; i < ns; ++i) k2[nk++] = sup[i];
+            sort_by_dist(k2, nk);
+            free(sup);
+        }
+        for (int t = 0; t < (int)R; ++t) out[(uint64_t)u * R + t] = t < nk ? k2[t].id : ORC_NO_ID;
+        counts[u] = (uint32_t)nk;
+        free(pool);
+        free(k2);
+    }
+    free(k1); free(n1); free(indeg); free(c); free(roff); free(rev); free(fill);
+    return ORC_OK;
+}

@@ -59,6 +59,28 @@ inline float l2(const float *a, const float *b, uint32_t d) {
     return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
 
+// Squared L2 distance in the search's exact-distance order, which the
+// pruning and the angle rule use so that their decisions are those of the
+// GPU graph kernels: 32 partial sums, partial l over the float4 chunks l,
+// l+32, ... with fma(x, x, acc) on their four coordinates in order, then
+// pairwise sums of partials l and l+16, l and l+8, ..., l and l+1.
+inline float l2c(const float *a, const float *b, uint32_t d) {
+    float p[32];
+    const uint32_t nch = d / 4;
+    for (uint32_t l = 0; l < 32; ++l) {
+        float acc = 0.0f;
+        for (uint32_t c = l; c < nch; c += 32)
+            for (uint32_t t = 0; t < 4; ++t) {
+                const float x = a[4 * c + t] - b[4 * c + t];
+                acc = std::fma(x, x, acc);
+            }
+        p[l] = acc;
+    }
+    for (uint32_t o = 16; o >= 1; o >>= 1)
+        for (uint32_t l = 0; l < o; ++l) p[l] = p[l] + p[l + o];
+    return p[0];
+}
+
 struct Cand {
     float d;
     uint32_t id;
@@ -84,7 +106,7 @@ void nsg_prune(const float *data, uint32_t d, const std::vector<Cand> &cands, ui
         const float *xc = data + (uint64_t)c.id * d;
         bool ok = true;
         for (const Cand &w : kept)
-            if (l2(data + (uint64_t)w.id * d, xc, d) < c.d) { ok = false; break; }
+            if (l2c(data + (uint64_t)w.id * d, xc, d) < c.d) { ok = false; break; }
         if (ok) kept.push_back(c);
     }
 }
@@ -109,7 +131,7 @@ void angle_supplement(const float *data, uint32_t d, const float *xu, const std:
         float best = -2.0f;
         for (const Cand &w : all) {
             if (!(w < c)) break;
-            float dwc = l2(data + (uint64_t)w.id * d, xc, d);
+            float dwc = l2c(data + (uint64_t)w.id * d, xc, d);
             float den = 2.0f * std::sqrt(w.d) * std::sqrt(c.d);
             float cs = den > 0.0f ? (w.d + c.d - dwc) / den : 1.0f;
             best = std::max(best, cs);
@@ -175,7 +197,7 @@ extern "C" int sqg_build_graph(const float *data, uint64_t n, uint32_t d, const 
         for (uint32_t t = 0; t < L; ++t) {
             uint32_t v = cand[u * L + t];
             if (v == SQG_NO_ID || v >= n || v == u) continue;
-            c.push_back({l2(xu, data + (uint64_t)v * d, d), v});
+            c.push_back({l2c(xu, data + (uint64_t)v * d, d), v});
         }
         std::sort(c.begin(), c.end(), [](const Cand &a, const Cand &b) { return a.id < b.id; });
         c.erase(std::unique(c.begin(), c.end(), [](const Cand &a, const Cand &b) { return a.id == b.id; }),
@@ -248,7 +270,7 @@ extern "C" int sqg_build_graph(const float *data, uint64_t n, uint32_t d, const 
                 uint32_t v = (uint32_t)(splitmix64(st) % n);
                 if (v == u || std::find(have.begin(), have.end(), v) != have.end()) continue;
                 have.push_back(v);
-                k2.push_back({l2(xu, data + (uint64_t)v * d, d), v});
+                k2.push_back({l2c(xu, data + (uint64_t)v * d, d), v});
             }
             std::sort(k2.begin(), k2.end());
         }

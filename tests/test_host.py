@@ -281,3 +281,24 @@ def test_metric_field_and_writer_checks(lib_built, oracle_mod, tiny_index, tmp_p
     O = oracle_mod.Index(tmp_path / "c.sqg")
     assert O.metric == 1
     np.testing.assert_allclose(O.raw_all(), ib.unit_rows(x), rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("n,d,R,L", [(600, 64, 32, 64), (400, 160, 32, 96)])
+def test_host_graph_adjust_matches_the_oracle(oracle_mod, lib_built, n, d, R, L):
+    """The builder's prune, reverse edges, re-prune and angle rule give the
+    oracle's lists exactly (same distance order, same (dist, id) order)
+    when no list needs the random fill and no reachability repair ran."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    rng = np.random.default_rng(n)
+    cen = rng.standard_normal((8, d)) * 3
+    x = (cen[rng.integers(0, 8, n)] + rng.standard_normal((n, d))).astype(np.float32)
+    dist = ((x[:, None, :].astype(np.float64) - x[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(dist, np.inf)
+    cand = np.argsort(dist, axis=1, kind="stable")[:, :L].astype(np.uint32)
+    cand[::7, -3:] = rng.integers(0, n, (cand[::7].shape[0], 3))  # some repeats and far ids
+    cand[::11, 1] = np.arange(0, n, 11)  # self ids, dropped
+    adj, st = ib.build_graph(x, cand, R, 0, 3, 0)
+    assert st["random_filled"] == 0 and st["repairs"] == 0
+    out, cnt = oracle_mod.adjust_graph(x, cand, R)
+    assert np.all(cnt == R)
+    np.testing.assert_array_equal(adj, out)

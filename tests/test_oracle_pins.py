@@ -604,3 +604,58 @@ def test_cosine_search_sees_the_normalized_query(small_cosine_graph, oracle_mod)
             np.testing.assert_array_equal(u, v)
         r = O.prepare_query(qs[i])
         np.testing.assert_array_equal(r["qrot"], oracle_mod.rotate_f32(O.rotation(), oracle_mod.normalize_f32(qs[i])))
+
+
+# --------------------------------------------------------------- index construction: "adjust G" (R11)
+
+def _all_others(n):
+    return np.array([[v for v in range(n) if v != u] for u in range(n)], dtype=np.uint32)
+
+
+def test_adjust_graph_on_a_line(oracle_mod):
+    """Points on a line at 0, 1, 2, 3, -1, -2 (ids 0..5), R = 2.  NSG keeps
+    the nearest point on each side; the end point 3 keeps only 2 (2 occludes
+    the rest), gets no other reverse edge, and the angle rule adds the
+    nearest remaining candidate, 1 (every cosine is 1 on a line)."""
+    x = np.zeros((6, 4), np.float32)
+    x[:, 0] = [0, 1, 2, 3, -1, -2]
+    out, cnt = oracle_mod.adjust_graph(x, _all_others(6), 2)
+    assert list(out[0]) == [1, 4] and list(out[1]) == [0, 2] and list(out[2]) == [1, 3]
+    assert list(out[3]) == [2, 1]
+    assert list(out[4]) == [0, 5] and list(out[5]) == [4, 0]
+    assert np.all(cnt == 2)
+
+
+def test_adjust_graph_angle_rule_closed_form(oracle_mod):
+    """u at the origin; A (1, 0); B at 30 deg, radius 2; C at 90 deg, r 3;
+    D at 180 deg, r 4; E at 20 deg, r 5.  NSG keeps A, C, D (A occludes B
+    and E: |AB|^2 = 1.54 < 4, |AE|^2 = 16.6 < 25).  With R = 4 one edge is
+    missing: B's largest cosine to a nearer candidate is cos 30 (to A), E's
+    is cos 10 (to B), so the angle rule adds B."""
+    deg = np.pi / 180
+    pts = [(0, 0), (1, 0), (2 * np.cos(30 * deg), 2 * np.sin(30 * deg)), (0, 3), (-4, 0),
+           (5 * np.cos(20 * deg), 5 * np.sin(20 * deg))]
+    x = np.zeros((6, 4), np.float32)
+    x[:, :2] = np.array(pts)
+    out, cnt = oracle_mod.adjust_graph(x, _all_others(6), 4)
+    assert list(out[0]) == [1, 2, 3, 4] and cnt[0] == 4
+
+
+def test_adjust_graph_lists_are_valid(oracle_mod):
+    """Random data with kNN candidates: every vertex gets exactly R distinct
+    neighbours, never itself, in ascending exact distance; the first is the
+    nearest of its candidates (NSG never prunes the nearest)."""
+    rng = np.random.default_rng(31)
+    n, d, R = 300, 32, 8
+    x = rng.standard_normal((n, d)).astype(np.float32)
+    dist = ((x[:, None, :].astype(np.float64) - x[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(dist, np.inf)
+    cand = np.argsort(dist, axis=1, kind="stable")[:, :24].astype(np.uint32)
+    out, cnt = oracle_mod.adjust_graph(x, cand, R)
+    assert np.all(cnt == R)
+    for u in range(n):
+        row = out[u]
+        assert len(set(row.tolist())) == R and u not in row
+        dd = [oracle_mod.exact_dist_f32(x[u], x[v]) for v in row]
+        assert dd == sorted(dd)
+        assert row[0] == cand[u, 0]
