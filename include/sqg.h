@@ -315,11 +315,28 @@ int sqg_knn_host(const float *data, uint64_t n, uint32_t d, uint32_t k, uint32_t
  *   re-pruned, and the adaptive angle rule supplements pruned candidates
  *   until exactly R edges remain (Sec. 3.2.2); random vertices fill any
  *   remaining gap (Sec. 3.2.2, footnote).  Every vertex is then made
- *   reachable from `entry` by replacing the farthest edge of a reachable
- *   vertex.  out_stats (host, 4): [avg degree after NSG pruning x 1000,
+ *   reachable from `entry` by replacing the edge of a reachable vertex
+ *   whose target has the most in-edges.  Distances are the search's exact
+ *   distance in its canonical fp32 order, candidates ordered by (distance,
+ *   id).  out_stats (host, 4): [avg degree after NSG pruning x 1000,
  *   vertices needing supplement, vertices randomly filled, repairs]. */
 int sqg_build_graph(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L, uint32_t R,
                     uint32_t entry, uint64_t seed, uint32_t *out_adj, uint64_t *out_stats, int threads);
+
+/* sqg_build_graph with steps (1)-(3) on CUDA device `device`: one warp per
+ * vertex prunes its own candidates, then re-prunes them with its reverse
+ * candidates and supplements by the angle rule (Sec. 3.2.1-3.2.2), with the
+ * same distance order and the same (distance, id) order as the host, so the
+ * rows are sqg_build_graph's bit for bit.  The reverse lists, a vertex whose
+ * lists exceed a warp's 512-entry lists, the random fill and the
+ * reachability repair run on the host.  data and cand are HOST arrays
+ * (copied to the device; synchronous); every value of data must be finite;
+ * L <= 512 and min(R, n-1) <= 64, else SQG_ERR_UNSUPPORTED.  out_stats (5
+ * u64, optional): as sqg_build_graph's four, then the vertices refined on
+ * the host. */
+int sqg_build_graph_gpu(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L, uint32_t R,
+                        uint32_t entry, uint64_t seed, uint32_t *out_adj, uint64_t *out_stats, int threads,
+                        int device);
 
 /* Vertex nearest to the mean of the data (host), the entry point used by
  * the builder. */

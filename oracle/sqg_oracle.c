@@ -18,6 +18,8 @@
  *                                                       (Sec. 3.1.1)
  *   - Algorithm 1 (Querying) with multiple estimated distances and implicit
  *     re-ranking                                        (Sec. 3.1.2-3.1.3)
+ *   - Algorithm 2's "adjust G": NSG's occlusion rule and the adaptive
+ *     angle supplement                                   (Sec. 3.2.1-3.2.2)
  *
  * Readings taken where the paper is silent (each also stated at its use):
  *   R1 the query is quantized to 4 bits per coordinate, uniform on

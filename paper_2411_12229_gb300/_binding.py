@@ -67,6 +67,7 @@ _SIGS = {
     "sqg_get_status": (I32, [P, P, C.POINTER(U32)]),
     "sqg_knn_host": (I32, [P, U64, U32, U32, P, I32]),
     "sqg_build_graph": (I32, [P, U64, U32, P, U32, U32, U32, U64, P, P, I32]),
+    "sqg_build_graph_gpu": (I32, [P, U64, U32, P, U32, U32, U32, U64, P, P, I32, I32]),
     "sqg_medoid": (U32, [P, U64, U32, I32]),
     "sqg_write_index": (I32, [C.c_char_p, P, U64, U32, P, U32, P, U32, U64, U64, I32]),
     "sqg_write_index2": (I32, [C.c_char_p, P, U64, U32, P, U32, P, U32, U64, U64, I32, U32, U32]),

@@ -4,7 +4,8 @@
 // together: candidate lists come from a brute-force kNN (sqg_knn_host) or
 // from the GPU search on the previous iteration's graph; sqg_build_graph
 // prunes them with NSG's rule and refines the graph so that every vertex has
-// exactly R edges (Sec. 3.2.2); sqg_write_index prepares the FastScan data
+// exactly R edges (Sec. 3.2.2; the steps are in graph_host.h, and graph.cu
+// runs them on the GPU); sqg_write_index prepares the FastScan data
 // (RaBitQ codes and factors of every edge, normalized about the source
 // vertex, Sec. 3.1.1) and writes the file the search loads.
 //
@@ -14,41 +15,20 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
-#include <numeric>
-#include <thread>
 #include <vector>
 
 #include "../../include/sqg.h"
+#include "graph_host.h"
 #include "index_format.h"
 
 namespace {
 
-int resolve_threads(int t) {
-    if (t > 0) return t;
-    unsigned h = std::thread::hardware_concurrency();
-    return h ? (int)h : 1;
-}
+using sqg_graph::Cand;
+using sqg_graph::parallel_for;
 
-template <class F>
-void parallel_for(uint64_t n, int threads, F f, uint64_t chunk = 64) {
-    threads = resolve_threads(threads);
-    std::atomic<uint64_t> next{0};
-    auto work = [&]() {
-        for (;;) {
-            uint64_t a = next.fetch_add(chunk);
-            if (a >= n) break;
-            uint64_t b = std::min(n, a + chunk);
-            for (uint64_t i = a; i < b; ++i) f(i);
-        }
-    };
-    std::vector<std::thread> ts;
-    for (int t = 1; t < threads; ++t) ts.emplace_back(work);
-    work();
-    for (auto &t : ts) t.join();
-}
-
-// Squared L2 distance, fp32, eight independent partial sums (d % 32 == 0).
+// Squared L2 distance, fp32, eight independent partial sums (d % 32 == 0):
+// the brute-force kNN and the medoid, whose order decides nothing the
+// search or the oracle must reproduce.
 inline float l2(const float *a, const float *b, uint32_t d) {
     float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (uint32_t i = 0; i < d; i += 8)
@@ -57,96 +37,6 @@ inline float l2(const float *a, const float *b, uint32_t d) {
             s[t] += x * x;
         }
     return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
-}
-
-// Squared L2 distance in the search's exact-distance order, which the
-// pruning and the angle rule use so that their decisions are those of the
-// GPU graph kernels: 32 partial sums, partial l over the float4 chunks l,
-// l+32, ... with fma(x, x, acc) on their four coordinates in order, then
-// pairwise sums of partials l and l+16, l and l+8, ..., l and l+1.
-inline float l2c(const float *a, const float *b, uint32_t d) {
-    float p[32];
-    const uint32_t nch = d / 4;
-    for (uint32_t l = 0; l < 32; ++l) {
-        float acc = 0.0f;
-        for (uint32_t c = l; c < nch; c += 32)
-            for (uint32_t t = 0; t < 4; ++t) {
-                const float x = a[4 * c + t] - b[4 * c + t];
-                acc = std::fma(x, x, acc);
-            }
-        p[l] = acc;
-    }
-    for (uint32_t o = 16; o >= 1; o >>= 1)
-        for (uint32_t l = 0; l < o; ++l) p[l] = p[l] + p[l + o];
-    return p[0];
-}
-
-struct Cand {
-    float d;
-    uint32_t id;
-    bool operator<(const Cand &o) const { return d < o.d || (d == o.d && id < o.id); }
-};
-
-uint64_t splitmix64(uint64_t &x) {
-    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-// NSG's pruning rule (Sec. 3.2.1, after NSG): walk the candidates nearest
-// first and keep c unless a kept w is closer to c than the vertex is
-// (d(w,c) < d(u,c)), which keeps every pair of out-edges at least 60
-// degrees apart.
-void nsg_prune(const float *data, uint32_t d, const std::vector<Cand> &cands, uint32_t R,
-               std::vector<Cand> &kept) {
-    kept.clear();
-    for (const Cand &c : cands) {
-        if (kept.size() >= R) break;
-        const float *xc = data + (uint64_t)c.id * d;
-        bool ok = true;
-        for (const Cand &w : kept)
-            if (l2c(data + (uint64_t)w.id * d, xc, d) < c.d) { ok = false; break; }
-        if (ok) kept.push_back(c);
-    }
-}
-
-// Adaptive angle rule (Sec. 3.2.2): a pruned candidate c is dropped at
-// threshold theta if a candidate closer to u makes an angle < theta with it.
-// The count of survivors falls monotonically as theta grows; the largest
-// theta that still leaves `need` survivors is the need-th smallest of the
-// candidates' largest cosines to a closer candidate, which is what a binary
-// search over theta converges to.  Returns the chosen candidates.
-void angle_supplement(const float *data, uint32_t d, const float *xu, const std::vector<Cand> &kept,
-                      const std::vector<Cand> &extra, uint32_t need, std::vector<Cand> &out) {
-    out.clear();
-    if (need == 0 || extra.empty()) return;
-    std::vector<Cand> all(kept);
-    all.insert(all.end(), extra.begin(), extra.end());
-    std::sort(all.begin(), all.end());
-    std::vector<std::pair<float, Cand>> score;  // (max cosine to a closer candidate, c)
-    score.reserve(extra.size());
-    for (const Cand &c : extra) {
-        const float *xc = data + (uint64_t)c.id * d;
-        float best = -2.0f;
-        for (const Cand &w : all) {
-            if (!(w < c)) break;
-            float dwc = l2c(data + (uint64_t)w.id * d, xc, d);
-            float den = 2.0f * std::sqrt(w.d) * std::sqrt(c.d);
-            float cs = den > 0.0f ? (w.d + c.d - dwc) / den : 1.0f;
-            best = std::max(best, cs);
-        }
-        score.push_back({best, c});
-    }
-    std::vector<float> cs;
-    for (auto &s : score) cs.push_back(s.first);
-    uint32_t take = std::min<uint32_t>(need, (uint32_t)cs.size());
-    std::nth_element(cs.begin(), cs.begin() + (take - 1), cs.end());
-    float thr = cs[take - 1];
-    for (auto &s : score)
-        if (s.first <= thr) out.push_back(s.second);
-    std::sort(out.begin(), out.end());
-    if (out.size() > take) out.resize(take);
 }
 
 }  // namespace
@@ -188,143 +78,32 @@ extern "C" int sqg_build_graph(const float *data, uint64_t n, uint32_t d, const 
         entry >= n || n > 0xFFFFFFF0ull)
         return SQG_ERR_INVALID_ARG;
     const uint32_t Rr = (uint32_t)std::min<uint64_t>(R, n - 1);  // tiny graphs: R distinct targets may not exist
-    std::vector<std::vector<Cand>> kept(n);
+    // 1. prune every vertex's own candidates (NSG rule)
+    std::vector<Cand> k1((size_t)n * Rr);
+    std::vector<uint32_t> n1(n, 0);
     std::atomic<uint64_t> deg_sum{0};
-
-    auto own_cands = [&](uint64_t u, std::vector<Cand> &c) {
-        c.clear();
-        const float *xu = data + u * d;
-        for (uint32_t t = 0; t < L; ++t) {
-            uint32_t v = cand[u * L + t];
-            if (v == SQG_NO_ID || v >= n || v == u) continue;
-            c.push_back({l2c(xu, data + (uint64_t)v * d, d), v});
-        }
-        std::sort(c.begin(), c.end(), [](const Cand &a, const Cand &b) { return a.id < b.id; });
-        c.erase(std::unique(c.begin(), c.end(), [](const Cand &a, const Cand &b) { return a.id == b.id; }),
-                c.end());
-        std::sort(c.begin(), c.end());
-    };
-
-    // 1. prune every vertex's candidates (NSG rule)
     parallel_for(n, threads, [&](uint64_t u) {
-        std::vector<Cand> c;
-        own_cands(u, c);
-        nsg_prune(data, d, c, Rr, kept[u]);
-        deg_sum += kept[u].size();
+        std::vector<Cand> c, kept;
+        sqg_graph::own_cands(data, n, d, cand, L, u, c);
+        sqg_graph::nsg_prune(data, d, c, Rr, kept);
+        std::copy(kept.begin(), kept.end(), k1.begin() + (size_t)u * Rr);
+        n1[u] = (uint32_t)kept.size();
+        deg_sum += kept.size();
     });
-
-    // 2. offer every kept edge u -> v back to v as a candidate (reverse edges)
-    std::vector<uint32_t> indeg(n + 1, 0);
-    for (uint64_t u = 0; u < n; ++u)
-        for (const Cand &c : kept[u]) indeg[c.id + 1]++;
-    std::vector<uint64_t> roff(n + 1, 0);
-    for (uint64_t v = 0; v < n; ++v) roff[v + 1] = roff[v] + indeg[v + 1];
-    std::vector<Cand> rev(roff[n]);
-    {
-        std::vector<uint64_t> fill(roff.begin(), roff.end() - 1);
-        for (uint64_t u = 0; u < n; ++u)
-            for (const Cand &c : kept[u]) rev[fill[c.id]++] = {c.d, (uint32_t)u};
-    }
-
+    // 2. reverse edges, re-prune; 3. angle rule; 4. random fill and rows
+    std::vector<uint64_t> roff;
+    std::vector<Cand> rev;
+    sqg_graph::reverse_edges(n, k1.data(), n1.data(), Rr, roff, rev);
     std::atomic<uint64_t> n_supp{0}, n_fill{0};
     parallel_for(n, threads, [&](uint64_t u) {
-        const float *xu = data + u * d;
-        std::vector<Cand> pool(kept[u]);
-        for (uint64_t t = roff[u]; t < roff[u + 1]; ++t) pool.push_back(rev[t]);
-        std::sort(pool.begin(), pool.end(), [](const Cand &a, const Cand &b) { return a.id < b.id; });
-        pool.erase(std::unique(pool.begin(), pool.end(), [](const Cand &a, const Cand &b) { return a.id == b.id; }),
-                   pool.end());
-        std::sort(pool.begin(), pool.end());
         std::vector<Cand> k2;
-        nsg_prune(data, d, pool, Rr, k2);
-        // 3. supplement to exactly R with the adaptive angle rule
-        if (k2.size() < Rr) {
+        if (sqg_graph::refine_vertex(data, n, d, cand, L, Rr, u, k1.data() + (size_t)u * Rr, n1[u],
+                                     rev.data() + roff[u], roff[u + 1] - roff[u], k2))
             n_supp++;
-            std::vector<Cand> all;
-            own_cands(u, all);
-            for (uint64_t t = roff[u]; t < roff[u + 1]; ++t) all.push_back(rev[t]);
-            std::sort(all.begin(), all.end(), [](const Cand &a, const Cand &b) { return a.id < b.id; });
-            all.erase(std::unique(all.begin(), all.end(), [](const Cand &a, const Cand &b) { return a.id == b.id; }),
-                      all.end());
-            std::vector<uint32_t> have;
-            for (auto &c : k2) have.push_back(c.id);
-            std::sort(have.begin(), have.end());
-            std::vector<Cand> extra;
-            for (auto &c : all)
-                if (!std::binary_search(have.begin(), have.end(), c.id)) extra.push_back(c);
-            std::sort(extra.begin(), extra.end());
-            uint32_t cap = d >= 512 ? 2 * Rr : 3 * Rr;
-            if (extra.size() > cap) extra.resize(cap);
-            std::vector<Cand> sup;
-            angle_supplement(data, d, xu, k2, extra, Rr - (uint32_t)k2.size(), sup);
-            k2.insert(k2.end(), sup.begin(), sup.end());
-            std::sort(k2.begin(), k2.end());
-        }
-        // 4. random fill when the candidates run out (footnote of Sec. 3.2.2)
-        if (k2.size() < Rr) {
-            n_fill++;
-            uint64_t st = seed ^ (u * 0x9E3779B97F4A7C15ull);
-            std::vector<uint32_t> have;
-            for (auto &c : k2) have.push_back(c.id);
-            while (k2.size() < Rr) {
-                uint32_t v = (uint32_t)(splitmix64(st) % n);
-                if (v == u || std::find(have.begin(), have.end(), v) != have.end()) continue;
-                have.push_back(v);
-                k2.push_back({l2c(xu, data + (uint64_t)v * d, d), v});
-            }
-            std::sort(k2.begin(), k2.end());
-        }
-        for (uint32_t t = 0; t < R; ++t) out_adj[u * R + t] = t < k2.size() ? k2[t].id : k2[t % k2.size()].id;
+        if (sqg_graph::fill_and_write(data, n, d, R, Rr, seed, u, k2, out_adj)) n_fill++;
     });
-
-    // 5. reachability from the entry point: connect each unreachable vertex
-    //    from a nearby reachable vertex, replacing that vertex's edge whose
-    //    target has the most other in-edges.
-    std::vector<uint32_t> in(n, 0);
-    for (uint64_t i = 0; i < n * R; ++i) in[out_adj[i]]++;
-    uint64_t repairs = 0;
-    for (int round = 0; round < 16; ++round) {
-        std::vector<uint8_t> seen(n, 0);
-        std::vector<uint32_t> stack{entry};
-        seen[entry] = 1;
-        auto flood = [&]() {
-            while (!stack.empty()) {
-                uint32_t u = stack.back();
-                stack.pop_back();
-                for (uint32_t t = 0; t < R; ++t) {
-                    uint32_t v = out_adj[(uint64_t)u * R + t];
-                    if (!seen[v]) { seen[v] = 1; stack.push_back(v); }
-                }
-            }
-        };
-        flood();
-        uint64_t fixed = 0;
-        for (uint64_t v = 0; v < n; ++v) {
-            if (seen[v]) continue;
-            uint32_t r = entry;
-            for (uint32_t t = 0; t < L; ++t) {
-                uint32_t c = cand[v * L + t];
-                if (c != SQG_NO_ID && c < n && c != v && seen[c]) { r = c; break; }
-            }
-            uint32_t *row = out_adj + (uint64_t)r * R;
-            bool dup = false;
-            for (uint32_t t = 0; t < R; ++t) dup |= row[t] == v;
-            if (dup) continue;
-            // replace the edge whose target has the most in-edges (farthest on ties)
-            int slot = (int)R - 1;
-            for (int t = (int)R - 2; t >= 0; --t)
-                if (in[row[t]] > in[row[slot]]) slot = t;
-            in[row[slot]]--;
-            row[slot] = (uint32_t)v;
-            in[v]++;
-            ++fixed;
-            seen[v] = 1;
-            stack.push_back((uint32_t)v);
-            flood();
-        }
-        repairs += fixed;
-        if (fixed == 0) break;
-    }
+    // 5. reachability from the entry point
+    const uint64_t repairs = sqg_graph::repair_reachability(n, cand, L, R, entry, out_adj);
     if (out_stats) {
         out_stats[0] = deg_sum.load() * 1000 / n;
         out_stats[1] = n_supp.load();

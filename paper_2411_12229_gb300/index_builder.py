@@ -92,16 +92,28 @@ def medoid(data: np.ndarray, threads: int = 0) -> int:
 
 
 def build_graph(data: np.ndarray, cand: np.ndarray, R: int, entry: int, seed: int = 3,
-                threads: int = 0) -> tuple[np.ndarray, dict]:
+                threads: int = 0, device: int | None = None) -> tuple[np.ndarray, dict]:
+    """Algorithm 2's adjust step: prune, reverse edges, angle rule, random
+    fill, reachability (Sec. 3.2).  device=None: on the host threads; a
+    device: the per-vertex steps on that GPU (the same rows bit for bit)."""
     data = np.ascontiguousarray(data, dtype=np.float32)
     cand = np.ascontiguousarray(cand, dtype=np.uint32)
     n = data.shape[0]
     adj = np.empty((n, R), dtype=np.uint32)
-    st = np.zeros(4, dtype=np.uint64)
-    B.check(B.lib().sqg_build_graph(_p(data), n, data.shape[1], _p(cand), cand.shape[1], R, entry, seed,
-                                    _p(adj), _p(st), threads), "sqg_build_graph")
-    return adj, dict(avg_nsg_degree=st[0] / 1000.0, supplemented=int(st[1]), random_filled=int(st[2]),
-                     repairs=int(st[3]))
+    st = np.zeros(5, dtype=np.uint64)
+    if device is not None and (cand.shape[1] > 512 or min(R, n - 1) > 64):
+        device = None  # longer lists than the GPU kernels keep: the host builds it
+    if device is None:
+        B.check(B.lib().sqg_build_graph(_p(data), n, data.shape[1], _p(cand), cand.shape[1], R, entry, seed,
+                                        _p(adj), _p(st), threads), "sqg_build_graph")
+    else:
+        B.check(B.lib().sqg_build_graph_gpu(_p(data), n, data.shape[1], _p(cand), cand.shape[1], R, entry, seed,
+                                            _p(adj), _p(st), threads, int(device)), "sqg_build_graph_gpu")
+    out = dict(avg_nsg_degree=st[0] / 1000.0, supplemented=int(st[1]), random_filled=int(st[2]),
+               repairs=int(st[3]))
+    if device is not None:
+        out["host_refined"] = int(st[4])
+    return adj, out
 
 
 def unit_rows(data: np.ndarray, chunk: int = 1 << 16) -> np.ndarray:
@@ -190,7 +202,7 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
         init = "knn" if (device is None or n <= 50_000) else "random"
     if init == "knn":
         cand = knn_host(data, min(cand_k, n - 1), threads)
-        adj, st = build_graph(data, cand, R, entry, graph_seed, threads)
+        adj, st = build_graph(data, cand, R, entry, graph_seed, threads, device)
         info["iterations"].append(dict(source="knn", **st))
     else:
         adj = random_graph(n, R, graph_seed)
@@ -220,9 +232,12 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
                         ids, _ = ix.search(xd[a:b], k_res, max(ef_build, k_res))
                         cand[a:b] = ids.cpu().numpy().view(np.uint32)
             ix.close()
-            adj, st = build_graph(data, cand, R, entry, graph_seed + it + 1, threads)
+            t2 = time.time()
+            adj, st = build_graph(data, cand, R, entry, graph_seed + it + 1, threads, device)
+            t3 = time.time()
             final = it == iterations - 1
             write_index(path if final else tmp, data, adj, rot, entry, rot_seed, graph_seed, threads, kind, mcode)
+            st.update(search_s=round(t2 - t1, 2), graph_s=round(t3 - t2, 2), write_s=round(time.time() - t3, 2))
             info["iterations"].append(dict(source="gpu-search", seconds=time.time() - t1, **st))
             if log:
                 log(f"build iteration {it + 1}/{iterations}: {time.time() - t1:.1f}s {st}")
