@@ -193,6 +193,8 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
         raise ValueError("rotation is 'dense' or 'fjlt'")
     kind = 1 if rotation == "fjlt" else 0
     n, d = data.shape
+    if n <= R:  # every vertex needs R distinct neighbours other than itself
+        raise ValueError(f"an index of degree {R} needs more than {R} vectors (got {n})")
     cand_k = cand_k or 2 * R
     rot = fjlt_matrix(d, rot_seed) if kind else random_rotation(d, rot_seed)
     entry = medoid(data, threads)

@@ -340,3 +340,45 @@ def test_host_buffers_end_to_end(gpu_tiny, oracle_mod):
     O = oracle_mod.Index(p)
     for i in range(0, q.shape[0], 7):
         np.testing.assert_array_equal(ids[i].view(np.uint32), O.search(q[i], 10, 64)[0])
+
+
+def test_max_k_and_max_ef(gpu_tiny, oracle_mod):
+    """k = SQG_MAX_K (256) and ef = SQG_MAX_EF (2048) on the 2,000-vertex
+    graph: the largest result and beam the kernels take.  With multiple
+    estimates the beam fills with copies (visited copies keep their slots,
+    R5) long before the graph is exhausted; both sides stop at the same
+    hop, past the visited set's move to global memory (128 shared slots
+    here, moved at 64 expansions)."""
+    ix, p, x, q = gpu_tiny
+    O = oracle_mod.Index(p)
+    ids, dists, st = _check_search(ix, O, q[:16], 256, 2048, visited_smem_log2=7)
+    assert np.all(st[:, 1] == 0) and np.all(st[:, 0] > 64)
+
+
+@pytest.fixture(scope="module")
+def gpu_ties(tmp_path_factory, lib_built):
+    """Integer-valued vectors, a fifth of them exact copies of others: many
+    equal distances and keys (ordered by id, R4) and neighbours equal to
+    their centre (zero codes and factors, R3); queries with integer values
+    and some equal to data vectors (distance 0)."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    from paper_2411_12229_gb300.api import Index
+    rng = np.random.default_rng(42)
+    base = rng.integers(-2, 3, size=(1200, 64)).astype(np.float32)
+    x = np.concatenate([base, base[rng.integers(0, 1200, 300)]])
+    x = x[rng.permutation(x.shape[0])]
+    q = rng.integers(-2, 3, size=(48, 64)).astype(np.float32)
+    q[:8] = x[rng.integers(0, x.shape[0], 8)]
+    p = tmp_path_factory.mktemp("ties") / "ties.sqg"
+    ib.build_index(p, x, 32)
+    return Index(p, 0), p, x, q
+
+
+def test_ties_and_duplicates_parity(gpu_ties, oracle_mod):
+    ix, p, x, q = gpu_ties
+    O = oracle_mod.Index(p)
+    for ef in (16, 64, 200):
+        ids, dists, st = _check_search(ix, O, q, 10, ef)
+    assert np.all(dists[:8, 0] == 0.0)  # the query's own vector
+    _check_search(ix, O, q, 10, 64, eps0=1.9)
+    _check_search(ix, O, q, 10, 64, multi_estimate=False)

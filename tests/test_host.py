@@ -302,3 +302,13 @@ def test_host_graph_adjust_matches_the_oracle(oracle_mod, lib_built, n, d, R, L)
     out, cnt = oracle_mod.adjust_graph(x, cand, R)
     assert np.all(cnt == R)
     np.testing.assert_array_equal(adj, out)
+
+
+def test_builder_needs_more_vectors_than_the_degree(lib_built, tmp_path):
+    """The loader takes only R distinct neighbours per vertex, none itself,
+    so an index of degree R needs n > R vectors."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    x = np.random.default_rng(0).standard_normal((32, 32)).astype(np.float32)
+    with pytest.raises(ValueError):
+        ib.build_index(tmp_path / "t.sqg", x, 32)
+    ib.build_index(tmp_path / "ok.sqg", np.vstack([x, x[:1] + 1]), 32)

@@ -659,3 +659,27 @@ def test_adjust_graph_lists_are_valid(oracle_mod):
         dd = [oracle_mod.exact_dist_f32(x[u], x[v]) for v in row]
         assert dd == sorted(dd)
         assert row[0] == cand[u, 0]
+
+
+def test_duplicate_neighbour_estimate_is_the_centre_distance(oracle_mod, lib_built, tmp_path):
+    """R3: a neighbour equal to its centre (||o - c|| = 0) has all-zero code
+    bits and zero factors, so its estimate is the centre's exact distance
+    whatever the query, and its error bound is 0 (eps0 changes nothing)."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    rng = np.random.default_rng(41)
+    x = rng.standard_normal((60, 32)).astype(np.float32)
+    x[1] = x[0]
+    adj = np.array([[v for v in range(60) if v != u][:32] for u in range(60)], dtype=np.uint32)
+    p = tmp_path / "dup.sqg"
+    ib.write_index(p, x, adj, ib.random_rotation(32, 2), 0, 2, 3)
+    O = oracle_mod.Index(p)
+    v0 = O.vertex(0)
+    j = list(v0["ids"]).index(1)
+    assert not v0["bits"][j].any() and v0["popcount"][j] == 0
+    assert v0["f_add"][j] == 0 and v0["f_rescale"][j] == 0 and v0["f_err"][j] == 0
+    for t in range(5):
+        q = (rng.standard_normal(32) * (t + 1)).astype(np.float32)
+        for eps0 in (0.0, 2.0):
+            r = O.estimate_block(q, 0, eps0)
+            assert r["est"][j] == r["dist_c"] and r["key"][j] == r["dist_c"]
+            assert r["dist_c"] == oracle_mod.exact_dist_f32(q, x[0])
