@@ -75,7 +75,7 @@ def lib():
                 "orc_mlp_logit_f32": (F32, [P, P]),
                 "orc_mlp_loss_grad_f64": (F64, [P, P, P, P, C.c_int, P]),
                 "orc_adam_step_f64": (None, [P, P, P, P, C.c_int, C.c_int, F64, F64, F64, F64]),
-                "orc_adjust_graph": (C.c_int, [P, U64, U32, P, U32, U32, P, P]),
+                "orc_adjust_graph": (C.c_int, [P, U64, U32, P, U32, U32, C.c_int, P, P]),
                 "orc_search": (C.c_int, [P, P, U32, U32, F32, C.c_int, U32, P, F32, U32, P, P, P,
                                          P, P, P, I32, P, P, U32]),
             }
@@ -314,15 +314,16 @@ def adam_step_f64(p, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     lib().orc_adam_step_f64(_p(p), _p(m), _p(v), _p(g), p.shape[0], t, lr, b1, b2, eps)
 
 
-def adjust_graph(data, cand, R: int) -> tuple[np.ndarray, np.ndarray]:
+def adjust_graph(data, cand, R: int, regular: bool = True) -> tuple[np.ndarray, np.ndarray]:
     """Algorithm 2's "adjust G" (readings R11): each vertex's edge list
-    (n x R, sorted by (dist, id), NO_ID after its count) and the counts."""
+    (n x R, sorted by (dist, id), NO_ID after its count) and the counts;
+    regular=False: without the angle rule (the "w/o GR" ablation, R17)."""
     data = _f32(data)
     cand = np.ascontiguousarray(cand, dtype=np.uint32)
     n, d = data.shape
     out = np.empty((n, R), np.uint32)
     cnt = np.empty(n, np.uint32)
-    rc = lib().orc_adjust_graph(_p(data), n, d, _p(cand), cand.shape[1], R, _p(out), _p(cnt))
+    rc = lib().orc_adjust_graph(_p(data), n, d, _p(cand), cand.shape[1], R, int(regular), _p(out), _p(cnt))
     if rc != 0:
         raise ValueError(f"oracle adjust_graph failed (code {rc})")
     return out, cnt

@@ -38,7 +38,11 @@
  *      cosine similarity) is served as Euclidean search between unit
  *      vectors: an index of metric 1 stores unit-norm vectors, and every
  *      query is scaled to unit norm before anything else (orc_normalize_f32);
- *      the distances returned are ||q/|q| - x||^2 = 2 - 2 cos(q, x).
+ *      the distances returned are ||q/|q| - x||^2 = 2 - 2 cos(q, x);
+ *   R17 a degree-unaligned graph (the "w/o GR" ablation of Sec. 5, no
+ *      degree alignment by the angle rule) keeps R slots per vertex and
+ *      marks the empty ones with id ORC_NO_ID, zero code bits and zero
+ *      factors; the search skips an empty slot.
  *
  * Floating point.  Fp64 functions give the plain definitions (used by the
  * pins).  The search takes its decisions (which vertex to expand, what
@@ -836,7 +840,8 @@ int orc_search(const orc_index *ix, const float *q, uint32_t k, uint32_t ef, flo
         int nc = 0;
         for (uint32_t j = 0; j < R; ++j) {
             uint32_t id = nbr(ix, p, j);
-            if (visited[id]) continue; /* line 6: unvisited neighbours only */
+            if (id == ORC_NO_ID) continue; /* an empty slot (R17) */
+            if (visited[id]) continue;     /* line 6: unvisited neighbours only */
             int32_t S;
             float est, key;
             estimate(ix, &qq, p, j, dist_c, eps0, &S, &est, &key);
@@ -1016,7 +1021,8 @@ static int own_candidates(const float *data, uint64_t n, uint32_t d, const uint3
     return m;
 }
 
-/* "Adjust G" of Algorithm 2 for every vertex, readings R11: (1) NSG-prune
+/* "Adjust G" of Algorithm 2 for every vertex, readings R11 (with regular =
+ * 0, the "w/o GR" ablation, R17: steps (1)-(2) only): (1) NSG-prune
  * the vertex's own candidates to at most R' = min(R, n-1) edges; (2) offer
  * every kept edge u -> v to v as the reverse candidate (u, dist) and prune
  * v's kept edges plus its reverse candidates again; (3) a vertex left with
@@ -1027,7 +1033,7 @@ static int own_candidates(const float *data, uint64_t n, uint32_t d, const uint3
  * The builder's random fill of a list still short and its reachability
  * repair come after this and are not part of it. */
 int orc_adjust_graph(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L, uint32_t R,
-                     uint32_t *out, uint32_t *counts) {
+                     int regular, uint32_t *out, uint32_t *counts) {
     if (!data || !cand || !out || !counts || n < 2 || R == 0 || L == 0 || d == 0 || d % 4 != 0) return ORC_ERR_ARG;
     const int Rr = (int)(R < n - 1 ? R : n - 1);
     orc_cand *k1 = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)n * (size_t)Rr);
@@ -1060,7 +1066,7 @@ int orc_adjust_graph(const float *data, uint64_t n, uint32_t d, const uint32_t *
         sort_by_dist(pool, np);
         orc_cand *k2 = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)Rr);
         int nk = nsg_prune(data, d, pool, np, Rr, k2);
-        if (nk < Rr) { /* (3) */
+        if (regular && nk < Rr) { /* (3) */
             int m = own_candidates(data, n, d, cand, L, u, pool);
             memcpy(pool + m, rev + roff[u], sizeof(orc_cand) * (size_t)nr);
             int na = unique_ids(pool, m + nr);

@@ -683,3 +683,54 @@ def test_duplicate_neighbour_estimate_is_the_centre_distance(oracle_mod, lib_bui
             r = O.estimate_block(q, 0, eps0)
             assert r["est"][j] == r["dist_c"] and r["key"][j] == r["dist_c"]
             assert r["dist_c"] == oracle_mod.exact_dist_f32(q, x[0])
+
+
+def test_irregular_lists_keep_the_nsg_property(oracle_mod):
+    """R17 ("w/o GR"): without the angle rule a vertex keeps only its
+    re-pruned NSG edges, so every pair w before c in its list satisfies
+    |wc|^2 >= |uc|^2 (exact fp32 distances), and the lists are mostly
+    shorter than R (empty slots NO_ID), where the regular graph's are full."""
+    rng = np.random.default_rng(51)
+    n, d, R = 400, 32, 32
+    x = rng.standard_normal((n, d)).astype(np.float32)
+    dist = ((x[:, None, :].astype(np.float64) - x[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(dist, np.inf)
+    cand = np.argsort(dist, axis=1, kind="stable")[:, :64].astype(np.uint32)
+    out, cnt = oracle_mod.adjust_graph(x, cand, R, regular=False)
+    reg, _ = oracle_mod.adjust_graph(x, cand, R)
+    assert np.all(cnt >= 1) and cnt.mean() < R / 2 and np.all(reg != oracle_mod.NO_ID)
+    for u in range(n):
+        row = out[u, :cnt[u]]
+        assert np.all(out[u, cnt[u]:] == oracle_mod.NO_ID)
+        du = [oracle_mod.exact_dist_f32(x[u], x[v]) for v in row]
+        assert du == sorted(du)
+        for a in range(len(row)):
+            for b in range(a + 1, len(row)):
+                assert oracle_mod.exact_dist_f32(x[row[a]], x[row[b]]) >= du[b]
+
+
+@pytest.fixture(scope="module")
+def small_irregular_graph(tmp_path_factory, lib_built, oracle_mod):
+    from paper_2411_12229_gb300 import index_builder as ib
+    from paper_2411_12229_gb300 import synth
+    w = synth.small(synth.TINY_10K_D128, 200, 20, n_components=4)
+    x = synth.base(w)
+    p = tmp_path_factory.mktemp("gi") / "g200i.sqg"
+    ib.build_index(p, x, 32, regular=False)
+    return oracle_mod.Index(p), x, synth.queries(w)
+
+
+def test_irregular_index_full_beam_returns_exact_knn(small_irregular_graph, oracle_mod):
+    """Empty slots (id NO_ID, zero codes and factors) are skipped; a full
+    beam still expands every vertex and returns the exact kNN."""
+    O, x, qs = small_irregular_graph
+    v = O.vertex(0)
+    empty = v["ids"] == oracle_mod.NO_ID
+    assert empty.any() and not v["bits"][empty].any() and np.all(v["f_add"][empty] == 0)
+    ef = O.n * (O.R + 1)
+    for i in range(5):
+        ids, dists, hops, st = O.search(qs[i], 10, ef, hop_cap=10 * ef)
+        gt, gd = oracle_mod.bruteforce(x, qs[i], 10)
+        assert hops == O.n and st == 0
+        np.testing.assert_array_equal(ids, gt)
+        np.testing.assert_allclose(dists, gd, rtol=1e-5)
