@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--metric", default="l2", choices=["l2", "cosine"],
                     help="index metric: squared Euclidean, or cosine similarity (unit vectors; the library "
                          "normalizes every query, Sec. 3)")
+    ap.add_argument("--graph", default="regular", choices=["regular", "irregular"],
+                    help="index graph: degree-aligned by the angle rule, or the w/o GR ablation (Sec. 5) "
+                         "with unused slots left empty")
     ap.add_argument("--prep", action="store_true",
                     help="time query preparation alone (rotation + 4-bit quantization), CUDA vs tensor cores")
     return ap.parse_args()
@@ -93,9 +96,11 @@ def cache_paths(args, w):
     tag = f"{w.name}-n{w.n}-R{w.degree}-it{args.build_iters}-ef{args.ef_build}"
     if args.metric != "l2":
         tag += f"-{args.metric}"
-    gt = c / f"{tag}-gt-q{w.n_queries}"  # the ground truth does not depend on the rotation
+    gt = c / f"{tag}-gt-q{w.n_queries}"  # the ground truth depends on neither the rotation nor the graph
     if args.rotation != "dense":
         tag += f"-{args.rotation}"
+    if args.graph != "regular":
+        tag += f"-{args.graph}"
     return c / f"{tag}.sqg", gt
 
 
@@ -111,7 +116,8 @@ def ensure_index(args, w, device, rank):
         log(f"building {idx.name}: n={w.n} d={w.d} R={w.degree}")
         info = ib.build_index(str(idx) + ".part", base, w.degree, device=device, init="random",
                               iterations=args.build_iters, ef_build=args.ef_build, cand_k=2 * w.degree,
-                              rotation=args.rotation, metric=args.metric, log=log)
+                              rotation=args.rotation, metric=args.metric, regular=args.graph == "regular",
+                              log=log)
         os.replace(str(idx) + ".part", idx)
         secs = time.time() - t
         log(f"built in {secs:.1f}s {info['iterations'][-1]}")
@@ -207,16 +213,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_record(workload_name, ef, metric="l2"):
+def traffic_record(workload_name, ef, metric="l2", rotation="dense", graph="regular"):
     """DRAM bytes per launch of the search kernel from a committed ncu
-    summary of the same launch (workload, index metric and ef), used only
-    while the kernel source is unchanged since."""
+    summary of the same launch (workload, index metric, rotation, graph and
+    ef), used only while the kernel source is unchanged since."""
     p = ROOT / "profiles" / "search_kernel_traffic.json"
     if not p.exists():
         return None
     z = json.loads(p.read_text())
     if (z.get("kernel_digest") != kernel_digest() or z.get("workload") != workload_name or z.get("ef") != ef
-            or z.get("metric", "l2") != metric):
+            or z.get("metric", "l2") != metric or z.get("rotation", "dense") != rotation
+            or z.get("graph", "regular") != graph):
         return None
     return z
 
@@ -667,7 +674,7 @@ def main():
     kern_mean = float(np.mean(kern_ms))
     achieved = alg_bytes / (kern_mean / 1e3) / 1e9
     peak, peak_src = measured_peaks()
-    tr = traffic_record(w.name, ef_sel, args.metric)
+    tr = traffic_record(w.name, ef_sel, args.metric, args.rotation, args.graph)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_src,
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
@@ -691,7 +698,7 @@ def main():
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_max, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "d": w.d, "degree": w.degree, "rotation": args.rotation, "metric": args.metric,
+        "config": {"workload": w.name, "n": w.n, "d": w.d, "degree": w.degree, "rotation": args.rotation, "metric": args.metric, "graph": args.graph,
                    "k": k, "ef": ef_sel,
                    "queries_per_step": nq, "recall@10": round(rec_sel, 4), "parallelism": f"replicas{world}",
                    "l2": f"index ({ix.n * ix.block_bytes / 1e9:.2f} GB) larger than L2, no flush between job "

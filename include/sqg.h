@@ -144,7 +144,10 @@ const char *sqg_error_string(int code);
  *   raw[d] fp32 | codes: u32 word w of neighbour j at index w*R + j, bit
  *   (i mod 32) of word i/32 = code bit of dimension i | f_add[R],
  *   f_rescale[R], f_err[R] fp32, popcount[R] u32 | ids[R] u32 | zero pad
- *   to a multiple of 128 bytes.
+ *   to a multiple of 128 bytes.  A neighbour id is < n, not the vertex
+ *   itself and distinct within the block, or SQG_NO_ID: an empty slot of a
+ *   degree-unaligned graph (zero code bits and factors), which the search
+ *   skips.
  * Metric (Sec. 3: the method serves Euclidean distance and cosine
  * similarity): 0 = squared Euclidean; 1 = cosine, served as Euclidean
  * search between unit vectors -- the raw vectors are unit-norm (or zero),
@@ -323,20 +326,27 @@ int sqg_knn_host(const float *data, uint64_t n, uint32_t d, uint32_t k, uint32_t
 int sqg_build_graph(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L, uint32_t R,
                     uint32_t entry, uint64_t seed, uint32_t *out_adj, uint64_t *out_stats, int threads);
 
-/* sqg_build_graph with steps (1)-(3) on CUDA device `device`: one warp per
- * vertex prunes its own candidates, then re-prunes them with its reverse
- * candidates and supplements by the angle rule (Sec. 3.2.1-3.2.2), with the
- * same distance order and the same (distance, id) order as the host, so the
- * rows are sqg_build_graph's bit for bit.  The reverse lists, a vertex whose
- * lists exceed a warp's 512-entry lists, the random fill and the
- * reachability repair run on the host.  data and cand are HOST arrays
- * (copied to the device; synchronous); every value of data must be finite;
+/* Flag of sqg_build_graph_ex: the degree-unaligned graph of the "w/o GR"
+ * ablation (Sec. 5): NSG pruning and reverse edges only, no angle-rule
+ * supplement and no random fill; a row's unused slots are SQG_NO_ID. */
+#define SQG_GRAPH_IRREGULAR 1u
+
+/* sqg_build_graph with flags (0 or SQG_GRAPH_IRREGULAR) and a device.
+ * device < 0: on the host threads.  device >= 0: steps (1)-(3) run on that
+ * CUDA device, one warp per vertex pruning its own candidates, then
+ * re-pruning them with its reverse candidates and (regular graphs)
+ * supplementing by the angle rule (Sec. 3.2.1-3.2.2), with the same
+ * distance order and the same (distance, id) order as the host, so the rows
+ * are the host's bit for bit; the reverse lists, a vertex whose lists
+ * exceed a warp's 512-entry lists, the random fill and the reachability
+ * repair run on the host.  data and cand are HOST arrays (copied to the
+ * device; synchronous); every value of data must be finite; on a device
  * L <= 512 and min(R, n-1) <= 64, else SQG_ERR_UNSUPPORTED.  out_stats (5
  * u64, optional): as sqg_build_graph's four, then the vertices refined on
  * the host. */
-int sqg_build_graph_gpu(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L, uint32_t R,
-                        uint32_t entry, uint64_t seed, uint32_t *out_adj, uint64_t *out_stats, int threads,
-                        int device);
+int sqg_build_graph_ex(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L, uint32_t R,
+                       uint32_t entry, uint64_t seed, uint32_t flags, uint32_t *out_adj, uint64_t *out_stats,
+                       int threads, int device);
 
 /* Vertex nearest to the mean of the data (host), the entry point used by
  * the builder. */
@@ -348,7 +358,8 @@ uint32_t sqg_medoid(const float *data, uint64_t n, uint32_t d, int threads);
  * alpha = sum|v_i|/sqrt(d), xc = <x_bar, P^-1 c>,
  * f_add = ||o-c||^2 + 2||o-c|| xc/alpha, f_rescale = -2||o-c||/alpha,
  * f_err = 2||o-c|| sqrt((1-alpha^2)/alpha^2)/sqrt(d-1); o = c gives zero
- * bits and factors.  Writes `path` (host) in the format of sqg_index_load. */
+ * bits and factors; adj entries SQG_NO_ID are empty slots (zero bits and
+ * factors).  Writes `path` (host) in the format of sqg_index_load. */
 int sqg_write_index(const char *path, const float *data, uint64_t n, uint32_t d, const uint32_t *adj,
                     uint32_t R, const float *rot, uint32_t entry, uint64_t seed_rotation, uint64_t seed_graph,
                     int threads);

@@ -21,6 +21,7 @@ SQG_ERR = {-1: "invalid argument", -2: "i/o error", -3: "bad index file format",
 STATUS_CAPACITY, STATUS_LEARNED_STOP, STATUS_BAD_PARAM, STATUS_TIMEOUT = 1, 2, 4, 8
 MAX_K, MAX_EF = 256, 2048
 NO_ID = 0xFFFFFFFF
+GRAPH_IRREGULAR = 1  # sqg_build_graph_ex: the degree-unaligned "w/o GR" graph
 MLP_IN, MLP_HIDDEN, MLP_NPARAM = 16, 64, 5313
 
 
@@ -67,7 +68,7 @@ _SIGS = {
     "sqg_get_status": (I32, [P, P, C.POINTER(U32)]),
     "sqg_knn_host": (I32, [P, U64, U32, U32, P, I32]),
     "sqg_build_graph": (I32, [P, U64, U32, P, U32, U32, U32, U64, P, P, I32]),
-    "sqg_build_graph_gpu": (I32, [P, U64, U32, P, U32, U32, U32, U64, P, P, I32, I32]),
+    "sqg_build_graph_ex": (I32, [P, U64, U32, P, U32, U32, U32, U64, U32, P, P, I32, I32]),
     "sqg_medoid": (U32, [P, U64, U32, I32]),
     "sqg_write_index": (I32, [C.c_char_p, P, U64, U32, P, U32, P, U32, U64, U64, I32]),
     "sqg_write_index2": (I32, [C.c_char_p, P, U64, U32, P, U32, P, U32, U64, U64, I32, U32, U32]),

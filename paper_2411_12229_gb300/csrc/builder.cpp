@@ -71,9 +71,9 @@ extern "C" uint32_t sqg_medoid(const float *data, uint64_t n, uint32_t d, int th
     return (uint32_t)best;
 }
 
-extern "C" int sqg_build_graph(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L,
-                               uint32_t R, uint32_t entry, uint64_t seed, uint32_t *out_adj, uint64_t *out_stats,
-                               int threads) {
+int sqg_graph::build_graph_host(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L,
+                                uint32_t R, uint32_t entry, uint64_t seed, bool regular, uint32_t *out_adj,
+                                uint64_t *out_stats, int threads) {
     if (!data || !cand || !out_adj || n < 2 || d == 0 || d % 32 != 0 || R == 0 || R % 32 != 0 || L == 0 ||
         entry >= n || n > 0xFFFFFFF0ull)
         return SQG_ERR_INVALID_ARG;
@@ -98,9 +98,9 @@ extern "C" int sqg_build_graph(const float *data, uint64_t n, uint32_t d, const 
     parallel_for(n, threads, [&](uint64_t u) {
         std::vector<Cand> k2;
         if (sqg_graph::refine_vertex(data, n, d, cand, L, Rr, u, k1.data() + (size_t)u * Rr, n1[u],
-                                     rev.data() + roff[u], roff[u + 1] - roff[u], k2))
+                                     rev.data() + roff[u], roff[u + 1] - roff[u], regular, k2))
             n_supp++;
-        if (sqg_graph::fill_and_write(data, n, d, R, Rr, seed, u, k2, out_adj)) n_fill++;
+        if (sqg_graph::fill_and_write(data, n, d, R, Rr, seed, u, regular, k2, out_adj)) n_fill++;
     });
     // 5. reachability from the entry point
     const uint64_t repairs = sqg_graph::repair_reachability(n, cand, L, R, entry, out_adj);
@@ -113,6 +113,12 @@ extern "C" int sqg_build_graph(const float *data, uint64_t n, uint32_t d, const 
     return SQG_OK;
 }
 
+extern "C" int sqg_build_graph(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L,
+                               uint32_t R, uint32_t entry, uint64_t seed, uint32_t *out_adj, uint64_t *out_stats,
+                               int threads) {
+    return sqg_graph::build_graph_host(data, n, d, cand, L, R, entry, seed, true, out_adj, out_stats, threads);
+}
+
 extern "C" int sqg_write_index2(const char *path, const float *data, uint64_t n, uint32_t d, const uint32_t *adj,
                                 uint32_t R, const float *rot, uint32_t entry, uint64_t seed_rotation,
                                 uint64_t seed_graph, int threads, uint32_t rotation_kind, uint32_t metric) {
@@ -120,7 +126,7 @@ extern "C" int sqg_write_index2(const char *path, const float *data, uint64_t n,
         rotation_kind > 1 || (rotation_kind == 1 && (d & (d - 1)) != 0) || metric > sqg_fmt::kMetricCosine)
         return SQG_ERR_INVALID_ARG;
     for (uint64_t i = 0; i < n * R; ++i)
-        if (adj[i] >= n) return SQG_ERR_INVALID_ARG;
+        if (adj[i] >= n && adj[i] != SQG_NO_ID) return SQG_ERR_INVALID_ARG;  // an empty slot is SQG_NO_ID
     if (metric == sqg_fmt::kMetricCosine) {  // a cosine index holds unit vectors (or zero vectors)
         std::atomic<uint64_t> bad{0};
         parallel_for(n, threads, [&](uint64_t v) {
@@ -187,6 +193,12 @@ extern "C" int sqg_write_index2(const char *path, const float *data, uint64_t n,
             for (uint32_t j = 0; j < R; ++j) {
                 uint32_t o = adj[c * R + j];
                 ids[j] = o;
+                if (o == SQG_NO_ID) {  // an empty slot of a degree-unaligned row: zero codes and factors
+                    for (uint32_t w = 0; w < d / 32; ++w) codes[w * R + j] = 0u;
+                    fa[j] = fr[j] = fe[j] = 0.0f;
+                    pc[j] = 0;
+                    continue;
+                }
                 double n2 = 0.0;
                 for (uint32_t i = 0; i < d; ++i) {
                     double u = (double)data[(uint64_t)o * d + i] - (double)data[c * d + i];

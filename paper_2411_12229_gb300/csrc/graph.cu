@@ -9,7 +9,8 @@
 // sums of fmaf over float4 chunks, then the xor butterfly), the same
 // (distance, id) order, the same cosine arithmetic.  A vertex whose lists
 // do not fit a warp's shared-memory lists (a hub with many reverse
-// candidates) is marked and refined on the host with the same code.
+// candidates) is marked and refined on the host with the same code.  A
+// degree-unaligned graph ("w/o GR", Sec. 5) skips the angle rule.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -170,7 +171,8 @@ __global__ void __launch_bounds__(kWarps * 32) adjust_prune_kernel(const float *
 __global__ void __launch_bounds__(kWarps * 32) adjust_refine_kernel(
     const float *__restrict__ data, uint64_t n, uint32_t d, uint32_t L, uint32_t Rr, const u64 *__restrict__ c_own,
     const uint32_t *__restrict__ c_cnt, const u64 *__restrict__ k1, const uint32_t *__restrict__ n1,
-    const u64 *__restrict__ rev, const uint64_t *__restrict__ roff, u64 *k2, uint32_t *n2, uint32_t *flag) {
+    const u64 *__restrict__ rev, const uint64_t *__restrict__ roff, int regular, u64 *k2, uint32_t *n2,
+    uint32_t *flag) {
     __shared__ WarpLists lists[kWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     WarpLists &S = lists[w];
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kWarps * 32) adjust_refine_kernel(
         warp_sort(S.b, np, lane);
         int nk = nsg_prune_warp(S.b, np, S.k, (int)Rr, data, d, lane);
         uint32_t fl = 0;
-        if (nk < (int)Rr) {
+        if (regular && nk < (int)Rr) {
             fl = kFlagAngle;
             // own and reverse candidates not kept, the nearest `cap` of them
             const int nc = (int)c_cnt[u];
@@ -302,11 +304,17 @@ inline sqg_graph::Cand unpack_host(uint64_t k) {
 
 }  // namespace
 
-extern "C" int sqg_build_graph_gpu(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L,
-                                   uint32_t R, uint32_t entry, uint64_t seed, uint32_t *out_adj, uint64_t *out_stats,
-                                   int threads, int device) {
+extern "C" int sqg_build_graph_ex(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L,
+                                  uint32_t R, uint32_t entry, uint64_t seed, uint32_t flags, uint32_t *out_adj,
+                                  uint64_t *out_stats, int threads, int device) {
+    if ((flags & ~SQG_GRAPH_IRREGULAR) != 0) return SQG_ERR_INVALID_ARG;
+    const bool regular = !(flags & SQG_GRAPH_IRREGULAR);
+    if (device < 0) {
+        if (out_stats) out_stats[4] = n;  // every vertex refined on the host
+        return sqg_graph::build_graph_host(data, n, d, cand, L, R, entry, seed, regular, out_adj, out_stats, threads);
+    }
     if (!data || !cand || !out_adj || n < 2 || d == 0 || d % 32 != 0 || R == 0 || R % 32 != 0 || L == 0 ||
-        entry >= n || n > 0xFFFFFFF0ull || device < 0)
+        entry >= n || n > 0xFFFFFFF0ull)
         return SQG_ERR_INVALID_ARG;
     const uint32_t Rr = (uint32_t)std::min<uint64_t>(R, n - 1);
     if (L > (uint32_t)kCap || Rr > (uint32_t)kMaxR) return SQG_ERR_UNSUPPORTED;
@@ -369,8 +377,8 @@ extern "C" int sqg_build_graph_gpu(const float *data, uint64_t n, uint32_t d, co
         std::vector<u64> h_k2;
         std::vector<uint32_t> h_n2(n), h_flag(n);
         if (rc == SQG_OK) {  // (3) re-prune and angle rule
-            adjust_refine_kernel<<<grid, kWarps * 32>>>(d_data, n, d, L, Rr, c_own, c_cnt, k1, n1, d_rev, d_roff, k2, n2,
-                                                        flag);
+            adjust_refine_kernel<<<grid, kWarps * 32>>>(d_data, n, d, L, Rr, c_own, c_cnt, k1, n1, d_rev, d_roff,
+                                                        regular ? 1 : 0, k2, n2, flag);
             h_k2.resize((size_t)n * Rr);
             if (cudaGetLastError() != cudaSuccess ||
                 cudaMemcpy(h_k2.data(), k2, sizeof(u64) * h_k2.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
@@ -386,13 +394,13 @@ extern "C" int sqg_build_graph_gpu(const float *data, uint64_t n, uint32_t d, co
                 if (h_flag[u] & kFlagHost) {
                     n_host++;
                     if (sqg_graph::refine_vertex(data, n, d, cand, L, Rr, u, k1c.data() + u * Rr, h_n1[u],
-                                                 rev.data() + roff[u], roff[u + 1] - roff[u], l2))
+                                                 rev.data() + roff[u], roff[u + 1] - roff[u], regular, l2))
                         n_supp++;
                 } else {
                     for (uint32_t j = 0; j < h_n2[u]; ++j) l2.push_back(unpack_host(h_k2[u * Rr + j]));
                     if (h_flag[u] & kFlagAngle) n_supp++;
                 }
-                if (sqg_graph::fill_and_write(data, n, d, R, Rr, seed, u, l2, out_adj)) n_fill++;
+                if (sqg_graph::fill_and_write(data, n, d, R, Rr, seed, u, regular, l2, out_adj)) n_fill++;
             });
             const uint64_t repairs = sqg_graph::repair_reachability(n, cand, L, R, entry, out_adj);
             if (out_stats) {

@@ -9,6 +9,9 @@
 //   (3) supplement a list still short of R' by the adaptive angle rule;
 //   (4) fill a list that is still short with random vertices;
 //   (5) connect every vertex the entry point cannot reach.
+// A degree-unaligned graph (the "w/o GR" ablation of Sec. 5) stops after
+// step (2): a row keeps its re-pruned edges and marks the rest of its R
+// slots SQG_NO_ID.
 // Distances are the search's exact distance in its canonical fp32 order;
 // candidates are ordered by (distance, id).
 #pragma once
@@ -176,18 +179,18 @@ inline void reverse_edges(uint64_t n, const Cand *k1, const uint32_t *n1, uint32
 }
 
 // (2)-(3) for vertex u: re-prune its kept edges with its reverse candidates,
-// then supplement by the angle rule from its own and reverse candidates not
-// kept, the nearest 2R' (d >= 512) or 3R' of them.  Returns whether the
-// angle rule ran.
+// then (regular graphs) supplement by the angle rule from its own and
+// reverse candidates not kept, the nearest 2R' (d >= 512) or 3R' of them.
+// Returns whether the angle rule ran.
 inline bool refine_vertex(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L, uint32_t Rr,
-                          uint64_t u, const Cand *k1u, uint32_t n1u, const Cand *rev, uint64_t nrev,
+                          uint64_t u, const Cand *k1u, uint32_t n1u, const Cand *rev, uint64_t nrev, bool regular,
                           std::vector<Cand> &k2) {
     std::vector<Cand> pool(k1u, k1u + n1u);
     pool.insert(pool.end(), rev, rev + nrev);
     unique_ids(pool);
     std::sort(pool.begin(), pool.end());
     nsg_prune(data, d, pool, Rr, k2);
-    if (k2.size() >= Rr) return false;
+    if (!regular || k2.size() >= Rr) return false;
     std::vector<Cand> all;
     own_cands(data, n, d, cand, L, u, all);
     all.insert(all.end(), rev, rev + nrev);
@@ -210,9 +213,14 @@ inline bool refine_vertex(const float *data, uint64_t n, uint32_t d, const uint3
 
 // (4) a list still short of R' gets random distinct vertices (footnote of
 // Sec. 3.2.2); then the n x R rows (tiny graphs with R' < R repeat entries).
-// Returns whether vertex u needed the fill.
+// A degree-unaligned row instead ends in SQG_NO_ID slots.  Returns whether
+// vertex u needed the fill.
 inline bool fill_and_write(const float *data, uint64_t n, uint32_t d, uint32_t R, uint32_t Rr, uint64_t seed, uint64_t u,
-                           std::vector<Cand> &k2, uint32_t *out_adj) {
+                           bool regular, std::vector<Cand> &k2, uint32_t *out_adj) {
+    if (!regular) {
+        for (uint32_t t = 0; t < R; ++t) out_adj[u * R + t] = t < k2.size() ? k2[t].id : SQG_NO_ID;
+        return false;
+    }
     bool filled = false;
     if (k2.size() < Rr) {
         filled = true;
@@ -238,7 +246,8 @@ inline bool fill_and_write(const float *data, uint64_t n, uint32_t d, uint32_t R
 inline uint64_t repair_reachability(uint64_t n, const uint32_t *cand, uint32_t L, uint32_t R, uint32_t entry,
                                     uint32_t *out_adj) {
     std::vector<uint32_t> in(n, 0);
-    for (uint64_t i = 0; i < n * R; ++i) in[out_adj[i]]++;
+    for (uint64_t i = 0; i < n * R; ++i)
+        if (out_adj[i] != SQG_NO_ID) in[out_adj[i]]++;
     uint64_t repairs = 0;
     for (int round = 0; round < 16; ++round) {
         std::vector<uint8_t> seen(n, 0);
@@ -250,7 +259,7 @@ inline uint64_t repair_reachability(uint64_t n, const uint32_t *cand, uint32_t L
                 stack.pop_back();
                 for (uint32_t t = 0; t < R; ++t) {
                     uint32_t v = out_adj[(uint64_t)u * R + t];
-                    if (!seen[v]) { seen[v] = 1; stack.push_back(v); }
+                    if (v != SQG_NO_ID && !seen[v]) { seen[v] = 1; stack.push_back(v); }
                 }
             }
         };
@@ -267,11 +276,17 @@ inline uint64_t repair_reachability(uint64_t n, const uint32_t *cand, uint32_t L
             bool dup = false;
             for (uint32_t t = 0; t < R; ++t) dup |= row[t] == v;
             if (dup) continue;
-            // replace the edge whose target has the most in-edges (farthest on ties)
-            int slot = (int)R - 1;
-            for (int t = (int)R - 2; t >= 0; --t)
-                if (in[row[t]] > in[row[slot]]) slot = t;
-            in[row[slot]]--;
+            // an empty slot if the row has one, else replace the edge whose
+            // target has the most in-edges (farthest on ties)
+            int slot = -1;
+            for (uint32_t t = 0; t < R && slot < 0; ++t)
+                if (row[t] == SQG_NO_ID) slot = (int)t;
+            if (slot < 0) {
+                slot = (int)R - 1;
+                for (int t = (int)R - 2; t >= 0; --t)
+                    if (in[row[t]] > in[row[slot]]) slot = t;
+                in[row[slot]]--;
+            }
             row[slot] = (uint32_t)v;
             in[v]++;
             ++fixed;
@@ -284,5 +299,10 @@ inline uint64_t repair_reachability(uint64_t n, const uint32_t *cand, uint32_t L
     }
     return repairs;
 }
+
+// Steps (1)-(5) on the host threads (builder.cpp); regular = false builds
+// the degree-unaligned graph.
+int build_graph_host(const float *data, uint64_t n, uint32_t d, const uint32_t *cand, uint32_t L, uint32_t R,
+                     uint32_t entry, uint64_t seed, bool regular, uint32_t *out_adj, uint64_t *out_stats, int threads);
 
 }  // namespace sqg_graph

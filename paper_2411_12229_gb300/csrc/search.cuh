@@ -676,7 +676,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                 ck[t] = e.key;
                 // line 6: only unvisited neighbours enter; an entry that the cut
                 // to ef would drop at once is skipped early
-                adm[t] = !full || kless(ck[t], cid[t], wk, wi);
+                adm[t] = cid[t] != kEmpty && (!full || kless(ck[t], cid[t], wk, wi));  // kEmpty: an empty slot
                 if (adm[t]) adm[t] = !hash_contains(H, hbits, cid[t]);
             }
             if (!a.multi_estimate) {  // ablation w/o ME: skip ids already in the beam

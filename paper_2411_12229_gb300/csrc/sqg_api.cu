@@ -592,8 +592,10 @@ extern "C" int sqg_index_load(const char *path, int device, sqg_index **out) {
             const unsigned char *b = stage + t * L.block_bytes + L.off_ids;
             for (uint32_t j = 0; j < L.R; ++j) ids[j] = sqg_fmt::load_u32(b + 4 * j);
             std::sort(ids.begin(), ids.end());
-            for (uint32_t j = 0; j < L.R; ++j)
-                if (ids[j] >= L.n || ids[j] == v0 + t || (j > 0 && ids[j] == ids[j - 1])) rc = SQG_ERR_FORMAT;
+            for (uint32_t j = 0; j < L.R; ++j)  // SQG_NO_ID (sorted last, repeats allowed): an empty slot
+                if (ids[j] != SQG_NO_ID &&
+                    (ids[j] >= L.n || ids[j] == v0 + t || (j > 0 && ids[j] == ids[j - 1])))
+                    rc = SQG_ERR_FORMAT;
         }
         if (rc == SQG_OK && cudaMemcpy(ix->d_blocks + v0 * L.block_bytes, stage, nbytes, cudaMemcpyHostToDevice) !=
                                 cudaSuccess)

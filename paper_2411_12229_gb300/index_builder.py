@@ -92,10 +92,12 @@ def medoid(data: np.ndarray, threads: int = 0) -> int:
 
 
 def build_graph(data: np.ndarray, cand: np.ndarray, R: int, entry: int, seed: int = 3,
-                threads: int = 0, device: int | None = None) -> tuple[np.ndarray, dict]:
+                threads: int = 0, device: int | None = None, regular: bool = True) -> tuple[np.ndarray, dict]:
     """Algorithm 2's adjust step: prune, reverse edges, angle rule, random
     fill, reachability (Sec. 3.2).  device=None: on the host threads; a
-    device: the per-vertex steps on that GPU (the same rows bit for bit)."""
+    device: the per-vertex steps on that GPU (the same rows bit for bit).
+    regular=False: the degree-unaligned graph of the "w/o GR" ablation
+    (Sec. 5): no angle rule, no random fill, unused slots NO_ID."""
     data = np.ascontiguousarray(data, dtype=np.float32)
     cand = np.ascontiguousarray(cand, dtype=np.uint32)
     n = data.shape[0]
@@ -103,12 +105,14 @@ def build_graph(data: np.ndarray, cand: np.ndarray, R: int, entry: int, seed: in
     st = np.zeros(5, dtype=np.uint64)
     if device is not None and (cand.shape[1] > 512 or min(R, n - 1) > 64):
         device = None  # longer lists than the GPU kernels keep: the host builds it
-    if device is None:
+    flags = 0 if regular else B.GRAPH_IRREGULAR
+    if device is None and regular:
         B.check(B.lib().sqg_build_graph(_p(data), n, data.shape[1], _p(cand), cand.shape[1], R, entry, seed,
                                         _p(adj), _p(st), threads), "sqg_build_graph")
     else:
-        B.check(B.lib().sqg_build_graph_gpu(_p(data), n, data.shape[1], _p(cand), cand.shape[1], R, entry, seed,
-                                            _p(adj), _p(st), threads, int(device)), "sqg_build_graph_gpu")
+        B.check(B.lib().sqg_build_graph_ex(_p(data), n, data.shape[1], _p(cand), cand.shape[1], R, entry, seed,
+                                           flags, _p(adj), _p(st), threads, -1 if device is None else int(device)),
+                "sqg_build_graph_ex")
     out = dict(avg_nsg_degree=st[0] / 1000.0, supplemented=int(st[1]), random_filled=int(st[2]),
                repairs=int(st[3]))
     if device is not None:
@@ -161,7 +165,7 @@ def random_graph(n: int, R: int, seed: int) -> np.ndarray:
 def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None, ef_build: int = 128,
                 cand_k: int | None = None, path_cand: int | None = None, rot_seed: int = 2, graph_seed: int = 3,
                 device: int | None = None, init: str = "auto", threads: int = 0, rotation: str = "dense",
-                metric: str = "l2", log=None) -> dict:
+                metric: str = "l2", regular: bool = True, log=None) -> dict:
     """Build an index file at `path` from base vectors `data` (n x d).
 
     device=None: host-only build from an exact kNN (small n).
@@ -174,6 +178,10 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
     rotation "dense": a Haar-random P^-1 (stored, applied as a d x d
     product); "fjlt": the fast JLT of Sec. 3.1.4, the data zero-padded to
     the next power of 2 (queries are padded the same way by the API).
+
+    regular=False builds the degree-unaligned graph of the "w/o GR"
+    ablation (Sec. 5) in every iteration: rows keep their pruned edges and
+    end in NO_ID slots.
 
     metric "l2": squared Euclidean; "cosine": cosine similarity as
     Euclidean search between unit vectors -- the data are scaled to unit
@@ -204,7 +212,7 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
         init = "knn" if (device is None or n <= 50_000) else "random"
     if init == "knn":
         cand = knn_host(data, min(cand_k, n - 1), threads)
-        adj, st = build_graph(data, cand, R, entry, graph_seed, threads, device)
+        adj, st = build_graph(data, cand, R, entry, graph_seed, threads, device, regular)
         info["iterations"].append(dict(source="knn", **st))
     else:
         adj = random_graph(n, R, graph_seed)
@@ -235,7 +243,7 @@ def build_index(path, data: np.ndarray, R: int, *, iterations: int | None = None
                         cand[a:b] = ids.cpu().numpy().view(np.uint32)
             ix.close()
             t2 = time.time()
-            adj, st = build_graph(data, cand, R, entry, graph_seed + it + 1, threads, device)
+            adj, st = build_graph(data, cand, R, entry, graph_seed + it + 1, threads, device, regular)
             t3 = time.time()
             final = it == iterations - 1
             write_index(path if final else tmp, data, adj, rot, entry, rot_seed, graph_seed, threads, kind, mcode)

@@ -19,7 +19,7 @@ def full_index(lib_built):
     from paper_2411_12229_gb300 import synth
     from paper_2411_12229_gb300.api import Index
     args = types.SimpleNamespace(cache=os.environ.get("SQG_CACHE", "/tmp/sqg_cache"), build_iters=3, ef_build=400,
-                                 rotation="dense", metric="l2")
+                                 rotation="dense", metric="l2", graph="regular")
     w = synth.BATCHED_1M_D128
     idx, _ = bench.ensure_index(args, w, 0, 0)
     return Index(idx, 0), idx, synth.queries(w)

@@ -83,3 +83,74 @@ def test_gpu_built_index_searches_like_the_oracle(lib_built, oracle_mod, tmp_pat
         oi, od, _, _ = O.search(q[i], 10, 48)
         np.testing.assert_array_equal(ids[i], oi)
         np.testing.assert_array_equal(dists[i], od)
+
+
+@pytest.mark.parametrize("n,d,R,L", [(600, 64, 32, 64), (300, 960, 64, 192)])
+def test_gpu_irregular_graph_equals_host(lib_built, oracle_mod, n, d, R, L):
+    """The degree-unaligned "w/o GR" build on the GPU: the host's rows."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    x = _clustered(n, d, n + d + 1)
+    cand = _knn_cand(x, L, d + 1)
+    adj_h, st_h = ib.build_graph(x, cand, R, 0, 3, 0, regular=False)
+    adj_g, st_g = ib.build_graph(x, cand, R, 0, 3, 0, device=0, regular=False)
+    np.testing.assert_array_equal(adj_g, adj_h)
+    assert st_g["supplemented"] == 0 and np.any(adj_g == 0xFFFFFFFF)
+    if st_h["repairs"] == 0:
+        out, _ = oracle_mod.adjust_graph(x, cand, R, regular=False)
+        np.testing.assert_array_equal(adj_g, out)
+
+
+IRREGULAR = {  # name: (workload, n, d, R)
+    "d128-R32": ("tiny-10k-d128", 2000, 128, 32),
+    "d64-R64": ("highdim-1m-d960", 1000, 64, 64),
+}
+
+
+@pytest.fixture(scope="module", params=list(IRREGULAR))
+def irregular_index(request, tmp_path_factory, lib_built, oracle_mod):
+    from paper_2411_12229_gb300 import index_builder as ib
+    from paper_2411_12229_gb300 import synth
+    from paper_2411_12229_gb300.api import Index
+    name, n, d, R = IRREGULAR[request.param]
+    w = synth.small(synth.WORKLOADS[name].with_(d=d), n, 48)
+    x, q = synth.base(w), synth.queries(w)
+    p = tmp_path_factory.mktemp(request.param) / "irr.sqg"
+    ib.build_index(p, x, R, regular=False)
+    return Index(p, 0), oracle_mod.Index(p), q
+
+
+@pytest.mark.parametrize("team", [32, 16, 8])
+def test_irregular_index_search_parity(irregular_index, team):
+    """Empty slots are skipped on both sides: ids, distances, hops and
+    status bit for bit, for every team size that the shape allows."""
+    ix, O, q = irregular_index
+    if team < 32 and ix.d > 256:
+        pytest.skip("teams need d <= 256")
+    qd = torch.from_numpy(q).cuda()
+    for ef in (16, 64, 200):
+        ids, dists, st = ix.search(qd, 10, ef, stats=True, team=team)
+        ids, dists, st = ids.cpu().numpy().view(np.uint32), dists.cpu().numpy(), st.cpu().numpy()
+        for i in range(q.shape[0]):
+            oi, od, oh, os_ = O.search(q[i], 10, ef)
+            np.testing.assert_array_equal(ids[i], oi, err_msg=f"ef {ef} query {i}")
+            np.testing.assert_array_equal(dists[i], od)
+            assert (st[i, 0], st[i, 1]) == (oh, os_)
+
+
+def test_irregular_index_estimates(irregular_index):
+    """The estimate hook on blocks with empty slots: S = 0 and est = key =
+    dist_c there (zero codes and factors), the oracle's values everywhere."""
+    ix, O, q = irregular_index
+    qd = torch.from_numpy(q).cuda()
+    v = (np.arange(q.shape[0]) * 29 % ix.n).astype(np.int32)
+    S, est, key, dc = (t.cpu().numpy() for t in ix.estimate_block(qd, torch.from_numpy(v), 1.0))
+    seen_empty = False
+    for i in range(q.shape[0]):
+        r = O.estimate_block(q[i], int(v[i]), 1.0)
+        np.testing.assert_array_equal(S[i], r["S"])
+        np.testing.assert_array_equal(est[i], r["est"])
+        np.testing.assert_array_equal(key[i], r["key"])
+        empty = O.vertex(int(v[i]))["ids"] == 0xFFFFFFFF
+        seen_empty |= bool(empty.any())
+        assert np.all(est[i][empty] == dc[i]) and np.all(S[i][empty] == 0)
+    assert seen_empty

@@ -312,3 +312,22 @@ def test_builder_needs_more_vectors_than_the_degree(lib_built, tmp_path):
     with pytest.raises(ValueError):
         ib.build_index(tmp_path / "t.sqg", x, 32)
     ib.build_index(tmp_path / "ok.sqg", np.vstack([x, x[:1] + 1]), 32)
+
+
+def test_host_irregular_graph_matches_the_oracle(oracle_mod, lib_built):
+    """The degree-unaligned build ("w/o GR"): the host rows are the oracle's
+    lists without the angle rule, empty slots NO_ID."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    rng = np.random.default_rng(7)
+    n, d, R = 500, 64, 32
+    cen = rng.standard_normal((8, d)) * 3
+    x = (cen[rng.integers(0, 8, n)] + rng.standard_normal((n, d))).astype(np.float32)
+    dist = ((x[:, None, :].astype(np.float64) - x[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(dist, np.inf)
+    cand = np.argsort(dist, axis=1, kind="stable")[:, :64].astype(np.uint32)
+    adj, st = ib.build_graph(x, cand, R, 0, 3, 0, regular=False)
+    assert st["supplemented"] == 0 and st["random_filled"] == 0
+    if st["repairs"] == 0:
+        out, cnt = oracle_mod.adjust_graph(x, cand, R, regular=False)
+        np.testing.assert_array_equal(adj, out)
+    assert np.any(adj == 0xFFFFFFFF)
