@@ -119,6 +119,14 @@ typedef struct {
     uint32_t status; /* SQG_STATUS_* bits */
 } sqg_query_stats;
 
+/* Self-test of the bounded device waits (failure detection without a GPU
+ * fault): one thread waits, through the search kernel's bounded wait, on an
+ * mbarrier phase that nothing completes; the wait gives up after its 1 s
+ * limit.  Writes (HOST) *status = SQG_STATUS_TIMEOUT (0 had the wait
+ * completed) and *waited_ns = how long it waited.  Synchronous; the
+ * context stays usable. */
+int sqg_wait_selftest(int device, uint32_t *status, uint64_t *waited_ns);
+
 /* Name of an error code (static string). */
 const char *sqg_error_string(int code);
 

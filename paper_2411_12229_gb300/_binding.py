@@ -69,6 +69,7 @@ _SIGS = {
     "sqg_knn_host": (I32, [P, U64, U32, U32, P, I32]),
     "sqg_build_graph": (I32, [P, U64, U32, P, U32, U32, U32, U64, P, P, I32]),
     "sqg_build_graph_ex": (I32, [P, U64, U32, P, U32, U32, U32, U64, U32, P, P, I32, I32]),
+    "sqg_wait_selftest": (I32, [I32, P, P]),
     "sqg_medoid": (U32, [P, U64, U32, I32]),
     "sqg_write_index": (I32, [C.c_char_p, P, U64, U32, P, U32, P, U32, U64, U64, I32]),
     "sqg_write_index2": (I32, [C.c_char_p, P, U64, U32, P, U32, P, U32, U64, U64, I32, U32, U32]),

@@ -382,3 +382,18 @@ def test_ties_and_duplicates_parity(gpu_ties, oracle_mod):
     assert np.all(dists[:8, 0] == 0.0)  # the query's own vector
     _check_search(ix, O, q, 10, 64, eps0=1.9)
     _check_search(ix, O, q, 10, 64, multi_estimate=False)
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(gpu_tiny, oracle_mod):
+    """Failure detection without a GPU fault: the search kernel's bounded
+    wait, on an mbarrier phase that nothing completes, gives up after its
+    1 s limit and reports SQG_STATUS_TIMEOUT; searches still run after it."""
+    import ctypes as C
+
+    from paper_2411_12229_gb300 import _binding as B
+    status, ns = C.c_uint32(0), C.c_uint64(0)
+    assert B.lib().sqg_wait_selftest(0, C.byref(status), C.byref(ns)) == 0
+    assert status.value == 8  # SQG_STATUS_TIMEOUT
+    assert 1.0e9 <= ns.value < 10.0e9
+    ix, p, x, q = gpu_tiny
+    _check_search(ix, oracle_mod.Index(p), q[:8], 10, 32)

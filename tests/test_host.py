@@ -331,3 +331,19 @@ def test_host_irregular_graph_matches_the_oracle(oracle_mod, lib_built):
         out, cnt = oracle_mod.adjust_graph(x, cand, R, regular=False)
         np.testing.assert_array_equal(adj, out)
     assert np.any(adj == 0xFFFFFFFF)
+
+
+def test_recall_and_distance_ratio_on_hand_made_cases():
+    """Sec. 5.1's accuracy metrics: recall |G cap S| / K per query, averaged
+    (padding ids -1 never count), and the average distance ratio over ranks
+    of ||o_i - q|| / ||o*_i - q|| from squared distances (ranks whose true
+    distance is 0 skipped, unreachable results skipped)."""
+    from paper_2411_12229_gb300 import eval as E
+    gt = np.array([[1, 2, 3, 4], [5, 6, 7, 8]])
+    ids = np.array([[4, 3, 9, -1], [5, 6, 7, 8]])
+    assert E.recall(ids, gt, 4) == 0.75  # 2/4 and 4/4
+    assert E.recall(ids, gt, 2) == 0.5  # {4, 3} vs {1, 2}: 0; {5, 6}: 2
+    np.testing.assert_array_equal(E.recall_per_query(ids, gt, 4), [0.5, 1.0])
+    assert E.average_distance_ratio(np.array([[4.0, 9.0]]), np.array([[1.0, 9.0]]), 2) == 1.5  # (2 + 1) / 2
+    assert E.average_distance_ratio(np.array([[1.0, 16.0]]), np.array([[0.0, 4.0]]), 2) == 2.0
+    assert E.average_distance_ratio(np.array([[np.inf, 9.0]]), np.array([[1.0, 4.0]]), 2) == 1.5
