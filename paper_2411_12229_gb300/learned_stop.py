@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import ctypes as C
 import dataclasses
+import json
 
 import numpy as np
 import torch
@@ -95,26 +96,72 @@ def forward(params: torch.Tensor, x: torch.Tensor, stream=None) -> torch.Tensor:
     return z
 
 
+def save_model(path, model: StopModel) -> None:
+    """The stop network in a file of its own: weights, threshold, period,
+    fixed-ef cap and the training record."""
+    np.savez(path, params=model.params.detach().cpu().numpy().astype(np.float32), logit=np.float32(model.logit),
+             every=np.int32(model.every), ef_cap=np.int32(model.ef_cap), info=json.dumps(model.info, default=str))
+
+
+def load_model(path, device=None) -> StopModel:
+    with np.load(path, allow_pickle=False) as z:
+        params = z["params"]
+        if params.shape != (B.MLP_NPARAM,) or params.dtype != np.float32:
+            raise ValueError(f"{path}: not a stop network ({params.shape}, {params.dtype})")
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        return StopModel(torch.from_numpy(params.copy()).to(dev), float(z["logit"]), int(z["every"]),
+                         int(z["ef_cap"]), json.loads(str(z["info"])))
+
+
+def save_train_state(path, params: torch.Tensor, m: torch.Tensor, v: torch.Tensor, step: int, seed: int) -> None:
+    """Adam's state after `step` steps, to resume training from."""
+    np.savez(path, params=params.cpu().numpy(), m=m.cpu().numpy(), v=v.cpu().numpy(), step=np.int64(step),
+             seed=np.int64(seed))
+
+
+def load_train_state(path) -> dict:
+    with np.load(path, allow_pickle=False) as z:
+        return {k: z[k].copy() for k in ("params", "m", "v")} | {"step": int(z["step"]), "seed": int(z["seed"])}
+
+
 def train(feats: np.ndarray, labels: np.ndarray, *, steps: int = 3000, batch: int = 8192, lr: float = 3e-3,
-          seed: int = 0, log=None) -> torch.Tensor:
-    """Minibatch Adam on the GPU; classes balanced by sample weights."""
+          seed: int = 0, log=None, resume: str | None = None, checkpoint: str | None = None,
+          stop_after: int | None = None) -> torch.Tensor:
+    """Minibatch Adam on the GPU; classes balanced by sample weights.
+
+    Step t draws its minibatch from a generator seeded with (seed, t), so a
+    run resumed from a state file (`resume`, written by `checkpoint`) sees
+    the batches the uninterrupted run would; `stop_after` ends the run
+    after that many steps (the learning-rate schedule still follows
+    `steps`)."""
     dev = torch.device("cuda")
     X = torch.from_numpy(np.ascontiguousarray(feats, dtype=np.float32)).to(dev)
     Y = torch.from_numpy(np.ascontiguousarray(labels, dtype=np.float32)).to(dev)
     pos = float(labels.mean())
     wpos, wneg = 0.5 / max(pos, 1e-6), 0.5 / max(1 - pos, 1e-6)
     W = torch.where(Y > 0.5, torch.tensor(wpos, device=dev), torch.tensor(wneg, device=dev)).float()
-    P = torch.from_numpy(init_params(seed)).to(dev)
-    m, v = torch.zeros_like(P), torch.zeros_like(P)
+    t0 = 0
+    if resume is not None:
+        st = load_train_state(resume)
+        if st["seed"] != seed:
+            raise ValueError(f"{resume}: trained with seed {st['seed']}, not {seed}")
+        P, m, v = (torch.from_numpy(st[k]).to(dev) for k in ("params", "m", "v"))
+        t0 = st["step"]
+    else:
+        P = torch.from_numpy(init_params(seed)).to(dev)
+        m, v = torch.zeros_like(P), torch.zeros_like(P)
     gen = torch.Generator(device=dev)
-    gen.manual_seed(seed)
     n = X.shape[0]
-    for t in range(1, steps + 1):
+    last = steps if stop_after is None else min(steps, t0 + stop_after)
+    for t in range(t0 + 1, last + 1):
+        gen.manual_seed(seed * 1_000_003 + t)
         idx = torch.randint(0, n, (min(batch, n),), device=dev, generator=gen)
         loss, g = grad(P, X[idx].contiguous(), Y[idx].contiguous(), W[idx].contiguous())
         adam(P, g, m, v, t, lr * (0.1 if t > 0.8 * steps else 1.0))
         if log and (t % 1000 == 0 or t == steps):
             log(f"stop-mlp step {t}: loss {float(loss):.4f}")
+    if checkpoint is not None:
+        save_train_state(checkpoint, P, m, v, last, seed)
     return P
 
 

@@ -109,3 +109,22 @@ def test_learned_stop_gain_over_fixed_ef(stop_setup):
         print(f"stop cap={cap} logit={thr}: recall {r:.4f} hops {hops:.2f} | plain at those hops {plain_r:.4f}")
     print("plain:", [(ef, round(p[0], 4), round(p[2], 2)) for ef, p in zip(efs, plain)])
     assert max(gains) > 0.0
+
+
+def test_training_resumes_from_a_checkpoint(lib_built, tmp_path):
+    """300 Adam steps in one run, and 120 steps, a state file, then the other
+    180 resumed from it: the same minibatches and the same Adam moments, so
+    the same parameters up to the float atomics' summation order."""
+    from paper_2411_12229_gb300 import learned_stop as L
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((5000, 16)).astype(np.float32)
+    y = ((x[:, 1] - x[:, 5]) > 0.0).astype(np.float32)
+    full = L.train(x, y, steps=300, batch=1024, seed=3)
+    ck = tmp_path / "state.npz"
+    L.train(x, y, steps=300, batch=1024, seed=3, stop_after=120, checkpoint=str(ck))
+    st = L.load_train_state(ck)
+    assert st["step"] == 120 and np.any(st["m"] != 0)
+    resumed = L.train(x, y, steps=300, batch=1024, seed=3, resume=str(ck))
+    np.testing.assert_allclose(resumed.cpu().numpy(), full.cpu().numpy(), rtol=0, atol=2e-4)
+    with pytest.raises(ValueError):
+        L.train(x, y, steps=300, batch=1024, seed=4, resume=str(ck))

@@ -347,3 +347,24 @@ def test_recall_and_distance_ratio_on_hand_made_cases():
     assert E.average_distance_ratio(np.array([[4.0, 9.0]]), np.array([[1.0, 9.0]]), 2) == 1.5  # (2 + 1) / 2
     assert E.average_distance_ratio(np.array([[1.0, 16.0]]), np.array([[0.0, 4.0]]), 2) == 2.0
     assert E.average_distance_ratio(np.array([[np.inf, 9.0]]), np.array([[1.0, 4.0]]), 2) == 1.5
+
+
+def test_stop_model_and_training_state_files(tmp_path):
+    """The stop network's file and Adam's state file round-trip exactly."""
+    torch = pytest.importorskip("torch")
+    from paper_2411_12229_gb300 import learned_stop as L
+    P = torch.from_numpy(L.init_params(5))
+    m = L.StopModel(P, 1.25, 8, 40, {"recall": 0.953, "train_queries": 20000})
+    L.save_model(tmp_path / "stop.npz", m)
+    r = L.load_model(tmp_path / "stop.npz", device="cpu")
+    assert torch.equal(r.params, P) and (r.logit, r.every, r.ef_cap) == (1.25, 8, 40) and r.info == m.info
+    np.savez(tmp_path / "bad.npz", params=np.zeros(7, np.float32), logit=0.0, every=1, ef_cap=1, info="{}")
+    with pytest.raises(ValueError):
+        L.load_model(tmp_path / "bad.npz", device="cpu")
+    mm, vv = P * 0.5, P * P
+    L.save_train_state(tmp_path / "st.npz", P, mm, vv, 77, 3)
+    st = L.load_train_state(tmp_path / "st.npz")
+    assert st["step"] == 77 and st["seed"] == 3
+    np.testing.assert_array_equal(st["params"], P.numpy())
+    np.testing.assert_array_equal(st["m"], mm.numpy())
+    np.testing.assert_array_equal(st["v"], vv.numpy())
