@@ -2,8 +2,8 @@
 
 Knobs, all result-neutral (the search is bit-identical under each):
   warps_per_block    query-warps per block (occupancy granularity)
-  prefetch           1: next block into the second shared buffer;
-                     2: also L2-prefetch the runner-up vertex's block
+  prefetch           1: the next block copied into shared memory during
+                     the merge; 2: also L2-prefetch the runner-up's block
   visited_smem_log2  shared-memory slots of the visited set (2^9, 2^10)
   lean               1: the 64-register build (d <= 256, more resident
                      warps); 2: the 96-register build
