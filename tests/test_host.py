@@ -368,3 +368,23 @@ def test_stop_model_and_training_state_files(tmp_path):
     np.testing.assert_array_equal(st["params"], P.numpy())
     np.testing.assert_array_equal(st["m"], mm.numpy())
     np.testing.assert_array_equal(st["v"], vv.numpy())
+
+
+def test_build_graph_ex_on_the_host_equals_the_plain_call(lib_built):
+    """sqg_build_graph_ex with device < 0 and no flags is sqg_build_graph;
+    an unknown flag is an argument error; the host path reports every
+    vertex as refined on the host."""
+    from paper_2411_12229_gb300 import _binding as B
+    rng = np.random.default_rng(12)
+    n, d, R, L = 300, 64, 32, 48
+    x = rng.standard_normal((n, d)).astype(np.float32)
+    cand = rng.integers(0, n, (n, L)).astype(np.uint32)
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    a1, a2 = np.empty((n, R), np.uint32), np.empty((n, R), np.uint32)
+    s1, s2 = np.zeros(5, np.uint64), np.zeros(5, np.uint64)
+    assert B.lib().sqg_build_graph(ptr(x), n, d, ptr(cand), L, R, 0, 3, ptr(a1), ptr(s1), 2) == 0
+    assert B.lib().sqg_build_graph_ex(ptr(x), n, d, ptr(cand), L, R, 0, 3, 0, ptr(a2), ptr(s2), 2, -1) == 0
+    np.testing.assert_array_equal(a1, a2)
+    np.testing.assert_array_equal(s1[:4], s2[:4])
+    assert s2[4] == n
+    assert B.lib().sqg_build_graph_ex(ptr(x), n, d, ptr(cand), L, R, 0, 3, 2, ptr(a2), ptr(s2), 2, -1) == -1
