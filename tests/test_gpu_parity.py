@@ -397,3 +397,18 @@ def test_bounded_wait_runs_out_and_the_context_stays_usable(gpu_tiny, oracle_mod
     assert 1.0e9 <= ns.value < 10.0e9
     ix, p, x, q = gpu_tiny
     _check_search(ix, oracle_mod.Index(p), q[:8], 10, 32)
+
+
+def test_more_results_than_vertices_are_padded_on_the_gpu(lib_built, oracle_mod, tmp_path):
+    """k = 100 on a 60-vertex graph: the 60 vertices, then padding, as the
+    oracle gives them (ids, distances, hops)."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    from paper_2411_12229_gb300.api import Index
+    rng = np.random.default_rng(61)
+    x = rng.standard_normal((60, 32)).astype(np.float32)
+    p = tmp_path / "n60.sqg"
+    ib.build_index(p, x, 32)
+    ix = Index(p, 0)
+    q = rng.standard_normal((7, 32)).astype(np.float32)
+    ids, dists, st = _check_search(ix, oracle_mod.Index(p), q, 100, 300)
+    assert np.all(ids[:, 60:] == 0xFFFFFFFF) and np.all(np.isinf(dists[:, 60:]))

@@ -757,3 +757,22 @@ def test_multiple_estimates_help_recall(lib_built, oracle_mod, tmp_path):
         gains.append(E.recall(me, gt, 10) - E.recall(no, gt, 10))
     print("recall gain of multiple estimates per ef:", [round(g, 4) for g in gains])
     assert np.mean(gains) >= 0.0 and gains[-1] > 0.0
+
+
+def test_more_results_than_vertices_are_padded(lib_built, oracle_mod, tmp_path):
+    """Algorithm 1 on a 60-vertex graph with k = 100 and a beam that holds
+    everything: all 60 vertices in exact-distance order (the brute-force
+    kNN), then 40 padding entries (NO_ID, +inf)."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    rng = np.random.default_rng(61)
+    x = rng.standard_normal((60, 32)).astype(np.float32)
+    p = tmp_path / "n60.sqg"
+    ib.build_index(p, x, 32)
+    O = oracle_mod.Index(p)
+    q = rng.standard_normal(32).astype(np.float32)
+    ids, dists, hops, st = O.search(q, 100, 60 * 33)
+    gt, gd = oracle_mod.bruteforce(x, q, 60)
+    assert hops == 60 and st == 0
+    np.testing.assert_array_equal(ids[:60], gt)
+    np.testing.assert_allclose(dists[:60], gd, rtol=1e-5)
+    assert np.all(ids[60:] == oracle_mod.NO_ID) and np.all(np.isinf(dists[60:]))
