@@ -154,3 +154,19 @@ def test_irregular_index_estimates(irregular_index):
         seen_empty |= bool(empty.any())
         assert np.all(est[i][empty] == dc[i]) and np.all(S[i][empty] == 0)
     assert seen_empty
+
+
+def test_irregular_index_trace_features(irregular_index, oracle_mod):
+    """The learned stop's search-state features (and the trace's hit
+    counts) on blocks with empty slots: the oracle's, bit for bit."""
+    ix, O, q = irregular_index
+    x = O.raw_all()
+    nq = 16
+    gt = np.stack([oracle_mod.bruteforce(x, q[i], 10)[0] for i in range(nq)]).astype(np.int32)
+    r = ix.search_trace(torch.from_numpy(q[:nq]).cuda(), 10, 64, torch.from_numpy(gt).cuda(), 256, stop_every=3)
+    feats, hits, cnt = (t.cpu().numpy() for t in r[3:6])
+    for i in range(nq):
+        o = O.search(q[i], 10, 64, stop_every=3, gt=gt[i].view(np.uint32), trace_cap=256)
+        assert cnt[i] == len(o[4])
+        np.testing.assert_array_equal(feats[i, :cnt[i]], o[4])
+        np.testing.assert_array_equal(hits[i, :cnt[i]], o[5])
