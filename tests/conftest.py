@@ -2,7 +2,6 @@ import os
 import pathlib
 import sys
 
-import numpy as np
 import pytest
 
 ROOT = pathlib.Path(__file__).resolve().parents[1]

@@ -6,7 +6,6 @@ the timings)."""
 import os
 import socket
 
-import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
