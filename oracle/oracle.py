@@ -78,6 +78,7 @@ def lib():
                 "orc_adjust_graph": (C.c_int, [P, U64, U32, P, U32, U32, C.c_int, P, P]),
                 "orc_search": (C.c_int, [P, P, U32, U32, F32, C.c_int, U32, P, F32, U32, P, P, P,
                                          P, P, P, I32, P, P, U32]),
+                "orc_search_record": (C.c_int, [P, P, U32, U32, U32, P, P, P, U32, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -196,6 +197,28 @@ class Index:
         if path_cap > 0:
             out.append(path[:min(path_cap, int(stats[0]))])
         return tuple(out)
+
+
+    def search_record(self, q, k: int, ef: int, hop_cap: int | None = None, rec_cap: int = 64):
+        """Algorithm 1 (eps0 = 0, multiple estimates) that also returns the
+        beam after each expansion's cut to ef: (ids, dists, hops, status,
+        beams), beams[h] = list of (id, key, visited) in beam order."""
+        q = _f32(q)
+        ids = np.empty(k, np.uint32)
+        dists = np.empty(k, np.float32)
+        stats = np.zeros(2, np.uint32)
+        cap = default_hop_cap(ef) if hop_cap is None else hop_cap
+        rm = np.zeros(rec_cap, np.int32)
+        ri = np.zeros(rec_cap * ef, np.uint32)
+        rk = np.zeros(rec_cap * ef, np.float32)
+        rv = np.zeros(rec_cap * ef, np.uint8)
+        rc = lib().orc_search_record(self._h, _p(q), k, ef, cap, _p(ids), _p(dists), _p(stats), rec_cap, _p(rm),
+                                     _p(ri), _p(rk), _p(rv))
+        if rc != 0:
+            raise ValueError(f"oracle search failed (code {rc})")
+        beams = [[(int(ri[h * ef + i]), float(rk[h * ef + i]), bool(rv[h * ef + i])) for i in range(rm[h])]
+                 for h in range(min(rec_cap, int(stats[0])))]
+        return ids, dists, int(stats[0]), int(stats[1]), beams
 
 
 def default_hop_cap(ef: int) -> int:

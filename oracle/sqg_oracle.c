@@ -781,10 +781,22 @@ static void stop_features(const orc_stop_state *s, const orc_entry *pool, int m,
  * trace_feat: cap x 16, trace_hit: cap, *trace_n in/out.
  * path (optional): the ids of the first path_cap expanded vertices, in order.
  */
-int orc_search(const orc_index *ix, const float *q, uint32_t k, uint32_t ef, float eps0, int multi_estimate,
-               uint32_t hop_cap, const float *mlp, float stop_logit, uint32_t stop_every, uint32_t *ids,
-               float *dists, uint32_t *stats, const uint32_t *gt, float *trace_feat, int32_t *trace_hit,
-               int32_t trace_cap, int32_t *trace_n, uint32_t *path, uint32_t path_cap) {
+/* Optional record of the beam after every expansion's cut to ef (test
+ * export, no effect on the search): for hop h < cap, m[h] entries at
+ * ids/keys/visited[h*ef ..], in beam order. */
+typedef struct {
+    uint32_t cap;
+    int32_t *m;
+    uint32_t *ids;
+    float *keys;
+    unsigned char *visited;
+} orc_beam_record;
+
+static int search_core(const orc_index *ix, const float *q, uint32_t k, uint32_t ef, float eps0,
+                       int multi_estimate, uint32_t hop_cap, const float *mlp, float stop_logit,
+                       uint32_t stop_every, uint32_t *ids, float *dists, uint32_t *stats, const uint32_t *gt,
+                       float *trace_feat, int32_t *trace_hit, int32_t trace_cap, int32_t *trace_n, uint32_t *path,
+                       uint32_t path_cap, const orc_beam_record *rec) {
     if (!ix || !q || k == 0 || ef < k || !ids || !dists || !stats) return ORC_ERR_ARG;
     const uint32_t d = ix->d, R = ix->R;
     float *qn = query_for(ix, &q);
@@ -873,6 +885,15 @@ int orc_search(const orc_index *ix, const float *q, uint32_t k, uint32_t ef, flo
         m = w < (int)ef ? w : (int)ef;
         int inserted = 0; /* this hop's candidates that survive the cut */
         for (int i = 0; i < m; ++i) inserted += (int)pool[i].fresh;
+        if (rec && hops - 1 < rec->cap) {
+            const size_t h = hops - 1;
+            rec->m[h] = m;
+            for (int i = 0; i < m; ++i) {
+                rec->ids[h * ef + i] = pool[i].id;
+                rec->keys[h * ef + i] = pool[i].key;
+                rec->visited[h * ef + i] = visited[pool[i].id];
+            }
+        }
 
         st.hops = (int)hops;
         st.inserted_last = inserted;
@@ -908,6 +929,26 @@ int orc_search(const orc_index *ix, const float *q, uint32_t k, uint32_t ef, flo
     free(qrot); free(qq.qbar); free(visited); free(pool); free(vflag); free(res); free(cand);
     free(qn);
     return ORC_OK;
+}
+
+int orc_search(const orc_index *ix, const float *q, uint32_t k, uint32_t ef, float eps0, int multi_estimate,
+               uint32_t hop_cap, const float *mlp, float stop_logit, uint32_t stop_every, uint32_t *ids,
+               float *dists, uint32_t *stats, const uint32_t *gt, float *trace_feat, int32_t *trace_hit,
+               int32_t trace_cap, int32_t *trace_n, uint32_t *path, uint32_t path_cap) {
+    return search_core(ix, q, k, ef, eps0, multi_estimate, hop_cap, mlp, stop_logit, stop_every, ids, dists, stats,
+                       gt, trace_feat, trace_hit, trace_cap, trace_n, path, path_cap, NULL);
+}
+
+/* orc_search (eps0 = 0, multiple estimates, no learned stop) that also
+ * records the beam after each of the first rec_cap expansions: rec_m[h]
+ * entries (ids, keys, visited flags) at offset h*ef of the rec arrays. */
+int orc_search_record(const orc_index *ix, const float *q, uint32_t k, uint32_t ef, uint32_t hop_cap,
+                      uint32_t *ids, float *dists, uint32_t *stats, uint32_t rec_cap, int32_t *rec_m,
+                      uint32_t *rec_ids, float *rec_keys, unsigned char *rec_visited) {
+    if (rec_cap > 0 && (!rec_m || !rec_ids || !rec_keys || !rec_visited)) return ORC_ERR_ARG;
+    orc_beam_record rec = {rec_cap, rec_m, rec_ids, rec_keys, rec_visited};
+    return search_core(ix, q, k, ef, 0.0f, 1, hop_cap, NULL, 0.0f, 1, ids, dists, stats, NULL, NULL, NULL, 0,
+                       NULL, NULL, 0, &rec);
 }
 
 /* ------------------------------------------------------------------ */

@@ -89,6 +89,45 @@ def test_golden_closed_form_on_gpu(oracle_mod, lib_built, tmp_path):
     assert dc[0] == np.sum((x[0] - q).astype(np.int64) ** 2)
 
 
+@pytest.mark.parametrize("team", [32, 16, 8])
+@pytest.mark.parametrize("ef", [1, 2, 3, 4])
+def test_golden_beam_trace_on_gpu(oracle_mod, lib_built, tmp_path, ef, team):
+    """The hand-worked trace of tests/golden/beam_trace_d32.txt (Algorithm 1
+    below the full beam, every estimate exact) through the GPU search: the
+    expansion order, hop count, status and the k = ef results with their
+    exact distances, for whole warps and teams of 16 / 8 lanes; with whole
+    warps also the learned-stop features f5 and f6 at every evaluation
+    point against the fractions derived by hand."""
+    import golden_trace as G
+
+    from paper_2411_12229_gb300.api import Index
+    t = G.load()
+    p = tmp_path / "trace.sqg"
+    G.write_index(t, p)
+    ix = Index(p, 0)
+    nm = G.names(t)
+    D = {k: v["D"] for k, v in t["vertex"].items()}
+    q = torch.from_numpy(t["q"].astype(np.float32)[None, :]).cuda()
+    ids, dists, st = ix.search(q, ef, ef, stats=True, team=team)
+    ids, dists, st = _np(ids)[0].view(np.uint32), _np(dists)[0], _np(st)[0]
+    assert [nm[i] for i in ids] == t["result"][ef]
+    np.testing.assert_array_equal(dists, [32.0 * D[n] for n in t["result"][ef]])
+    assert (st[0], st[1]) == (len(t["path"][ef]), 0)
+    if team != 32:
+        return  # the trace export runs whole warps
+    *_, feats, _, cnt, path = ix.search_trace(q, ef, ef, None, 16, path_cap=16, stop_every=1)
+    path = _np(path)[0].view(np.uint32)
+    assert [nm[i] for i in path[:len(t["path"][ef])]] == t["path"][ef]
+    assert np.all(path[len(t["path"][ef]):] == 0xFFFFFFFF)
+    want = t["stop"][ef]
+    feats = _np(feats)[0][:int(_np(cnt)[0])]
+    assert len(feats) == len(want)
+    for f, (h, f5, f6) in zip(feats, want):
+        assert f[0] == pytest.approx(h / ef, rel=1e-6)
+        assert f[5] == pytest.approx(float(f5), rel=1e-5, abs=1e-7)
+        assert f[6] == pytest.approx(float(f6), rel=1e-6)
+
+
 def _check_search(ix, O, q, k, ef, **kw):
     qd = torch.from_numpy(q).cuda()
     ids, dists, st = ix.search(qd, k, ef, stats=True, **{a: b for a, b in kw.items() if a != "mlp_np"})

@@ -227,6 +227,84 @@ def test_golden_alpha_one_estimates_are_exact(oracle_mod, lib_built, tmp_path):
     assert r["dist_c"] == np.sum((x[0] - q).astype(np.int64) ** 2)
 
 
+# --------------------------------------------------------------- golden hand-worked trace
+
+def test_golden_beam_trace_fixture_is_consistent():
+    """tests/golden/beam_trace_d32.txt: the distances its derivation uses
+    are the vectors' (32 |a_v|^2 = ||x_v - q||^2 in integer arithmetic),
+    every tree edge moves along one Hadamard axis (so it is t times a
+    codeword), the query spans the 4-bit range exactly, and no two
+    vertices are at the same distance."""
+    import golden_trace as G
+    t = G.load()
+    x = G.vectors(t)
+    q = t["q"]
+    assert q.shape == (32,) and q.min() == 0 and q.max() == 15
+    Ds = []
+    for name, v in t["vertex"].items():
+        assert int((v["a"] ** 2).sum()) == v["D"], name
+        assert int(((x[v["id"]] - q) ** 2).sum()) == 32 * v["D"], name
+        Ds.append(v["D"])
+    assert len(set(Ds)) == len(Ds)
+    for u, w in t["edges"]:
+        diff = t["vertex"][w]["a"] - t["vertex"][u]["a"]
+        assert np.count_nonzero(diff) == 1, (u, w)
+        e = x[t["vertex"][w]["id"]] - x[t["vertex"][u]["id"]]
+        assert len(set(np.abs(e).tolist())) == 1  # +-t in every coordinate: t times a sign vector
+
+
+@pytest.mark.parametrize("ef", [1, 2, 3, 4])
+def test_golden_beam_trace_below_the_full_beam(oracle_mod, lib_built, tmp_path, ef):
+    """Algorithm 1 below the full beam against the hand-worked trace of
+    tests/golden/beam_trace_d32.txt (every estimate exact, so the search is
+    the textbook beam search on exact distances): the beam after every
+    expansion (ids in order, visited marks, keys = 32 D within fp32
+    rounding), the expansion order, the hop count and the k = ef results
+    with their exact distances.  A wrong select, a cut that keeps the wrong
+    end, visited entries that do not hold their slots (reading R5) or an
+    off-by-one in ef each change the trace."""
+    import golden_trace as G
+    t = G.load()
+    p = tmp_path / "trace.sqg"
+    G.write_index(t, p)
+    O = oracle_mod.Index(p)
+    nm = G.names(t)
+    D = {k: v["D"] for k, v in t["vertex"].items()}
+    ids, dists, hops, status, beams = O.search_record(t["q"].astype(np.float32), ef, ef)
+    assert status == 0
+    assert hops == len(t["path"][ef])
+    for h, beam in enumerate(beams, start=1):
+        want = t["beam"][(ef, h)]
+        assert [(nm[i], v) for i, _, v in beam] == [(n, v) for n, _, v in want], f"ef {ef} hop {h}"
+        for (i, key, _), (n, d, _) in zip(beam, want):
+            assert d == D[n]
+            assert key == pytest.approx(32 * d, rel=1e-5)
+    assert [nm[i] for i in ids] == t["result"][ef]
+    np.testing.assert_array_equal(dists, [32.0 * D[n] for n in t["result"][ef]])
+    *_, path = O.search(t["q"].astype(np.float32), ef, ef, path_cap=16)
+    assert [nm[i] for i in path] == t["path"][ef]
+
+
+@pytest.mark.parametrize("ef", [1, 2, 3, 4])
+def test_golden_beam_trace_stop_features(oracle_mod, lib_built, tmp_path, ef):
+    """The learned stop's features f5 (first unvisited key / k-th result
+    distance) and f6 (expanded vertex's distance / k-th result distance) at
+    every evaluation point of the hand-worked trace, k = ef, against the
+    fractions derived by hand."""
+    import golden_trace as G
+    t = G.load()
+    p = tmp_path / "trace.sqg"
+    G.write_index(t, p)
+    O = oracle_mod.Index(p)
+    _, _, hops, _, feats, _ = O.search(t["q"].astype(np.float32), ef, ef, trace_cap=16, stop_every=1)
+    want = t["stop"][ef]
+    assert len(feats) == len(want)
+    for f, (h, f5, f6) in zip(feats, want):
+        assert f[0] == pytest.approx(h / ef, rel=1e-6)  # f0 = hops / ef names the evaluation point
+        assert f[5] == pytest.approx(float(f5), rel=1e-5, abs=1e-7)
+        assert f[6] == pytest.approx(float(f6), rel=1e-6)
+
+
 # --------------------------------------------------------------- search (Algorithm 1)
 
 @pytest.fixture(scope="module")
