@@ -6,15 +6,27 @@
 // a latency-critical thread that must not take the allocator's locks or
 // risk an out-of-memory error mid-request, a plugin whose host forbids
 // allocations after start-up).  sqg_search_noalloc serves them: its scratch
-// is one fixed, file-scope device array reserved when the library is
-// loaded, so the call itself performs no cudaMalloc, cudaFree or
-// stream-ordered allocation.
+// is one fixed, file-scope device array, so the call itself performs no
+// cudaMalloc, cudaFree or stream-ordered allocation.
+//
+// When the array's memory is committed: the library is built without
+// relocatable device code and CUDA loads a module's device code lazily, so
+// the 32 MiB are committed on a device when this file's module is first
+// loaded there -- by the set-up inside the first sqg_search_noalloc call on
+// that device (cudaGetSymbolAddress), not when the library is opened.  A
+// caller that means to reserve the rest of the GPU for its own pool makes
+// that first call beforehand (a call with nq = 0 does the set-up and
+// nothing else), and before any stream capture.  The address found there
+// is cached per device ordinal for the life of the process; after a
+// cudaDeviceReset of that device it no longer points at the array and the
+// entry point must not be called again in that process.
 //
 // The array is shared by every call in the process on a given GPU and
 // keeps whatever the previous call left in it; the search clears what must
-// start at zero (the work-queue head) and overwrites the rest before
-// reading it.  Two calls whose work overlaps on the same GPU would use the
-// same array at once and race: serialize them (one stream, or events).
+// start at zero (the work-queue head, the visited tables before they are
+// used) and overwrites the rest before reading it.  Two calls whose work
+// overlaps on the same GPU would use the same array at once and race:
+// serialize them (one stream, or events).
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -66,8 +78,8 @@ extern "C" int sqg_search_noalloc(const sqg_index *ix, const float *queries, int
     if (need == 0) return SQG_ERR_INVALID_ARG;
     if (need > kScratchBytes) return SQG_ERR_CAPACITY;  // batch too large for the fixed scratch
     void *scratch = nullptr;
-    const int rc = scratch_on(info.device, &scratch);
-    if (rc != SQG_OK) return rc;
+    const int rc = scratch_on(info.device, &scratch);  // the set-up, also for nq = 0
+    if (rc != SQG_OK || nq == 0) return rc;
     sqg_search_params p;
     std::memset(&p, 0, sizeof(p));
     p.multi_estimate = 1;
