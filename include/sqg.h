@@ -55,6 +55,7 @@ typedef struct CUstream_st *sqg_stream_t; /* a cudaStream_t; NULL = legacy defau
 
 #define SQG_MAX_K 256
 #define SQG_MAX_EF 2048
+#define SQG_MAX_SHARDS 32 /* shards one sqg_merge_topk call merges */
 #define SQG_NO_ID 0xFFFFFFFFu
 
 /* Learned early stop: a 16 -> 64 -> 64 -> 1 fp32 MLP (ReLU hidden units)
@@ -101,9 +102,12 @@ typedef struct {
     int32_t prefetch;        /* 1 (default, 0): the next block is copied into shared
                                 memory during the merge; 2: also L2-prefetch the
                                 runner-up candidate's block */
-    int32_t lean;            /* d <= 256 only: 0 or 1 = the kernel build capped at 64
-                                registers (more resident warps, a few spills; the
-                                default), 2 = the 96-register build */
+    int32_t lean;            /* d <= 256 only.  General kernel: 0 or 1 = the build capped at
+                                64 registers (more resident warps, a few spills; the
+                                default), 2 = the 96-register build (and never the
+                                compact kernel).  Compact kernel: 0 = the build for 8
+                                resident blocks of 4 warps per SM (64 registers), 1 = for
+                                10 (48 registers, a few spilled bytes) */
     int32_t rotation;        /* q' = P^-1 q: 1 = the canonical fp32 order (see
                                 sqg_prepare_queries) on the CUDA cores; 2 = tcgen05 tensor
                                 cores (3xTF32) followed by an exact pass that recomputes in
@@ -112,6 +116,12 @@ typedef struct {
                                 quantized query is identical to 1; 0 = 2 for d >= 512,
                                 else 1.  Ignored for a fast-JLT index (format version 2),
                                 whose queries always take the fast transform */
+    int32_t kernel;          /* 0 (default) = the compact search kernel wherever it applies
+                                (one warp per query, d <= 256, degree 32, every k[i] <= 32
+                                and ef[i] <= 64 by max_k / max_ef, multiple estimates, no
+                                learned stop, no trace, prefetch 1), else the general one;
+                                1 = always the general kernel; 2 = the compact kernel or
+                                SQG_ERR_UNSUPPORTED.  Both return identical results. */
 } sqg_search_params;
 
 typedef struct {
@@ -271,21 +281,46 @@ int sqg_search_trace(const sqg_index *ix, const float *queries, int nq, const in
  *   (max_k, max_ef: every valid k[i] <= max_k, ef[i] <= max_ef), so nothing
  *   is read back from the device either.
  *   Scratch: one file-scope device array of sqg_noalloc_scratch_bytes()
- *   (32 MiB) that every GPU loading the library holds until the process
- *   exits.  A batch whose sqg_workspace_size(ix, nq, max_k, max_ef) exceeds
- *   it is rejected with SQG_ERR_CAPACITY (for d = 128: about 60,000
+ *   (32 MiB) that a GPU holds until the process exits once the entry point
+ *   has run on it.  A batch whose sqg_workspace_size(ix, nq, max_k, max_ef)
+ *   exceeds it is rejected with SQG_ERR_CAPACITY (for d = 128: about 60,000
  *   queries with max_ef <= 112; larger ef also needs the visited tables).
  *   The call performs no cudaMalloc, cudaFree or stream-ordered allocation.
- *   The first call on a device looks the array's address up
- *   (cudaGetSymbolAddress) and caches it; make that first call before any
- *   stream capture.  All calls share the array and it keeps the last call's
- *   contents (the search resets what must start at zero); calls whose work
- *   overlaps on one GPU race on it and must be serialized by the caller. */
+ *   Set-up: the first call on a device loads the array's module there,
+ *   which commits the 32 MiB, and looks the array's address up
+ *   (cudaGetSymbolAddress) and caches it.  Make that first call -- a call
+ *   with nq = 0 does only the set-up -- before reserving the rest of the
+ *   GPU's memory and before any stream capture.  The cached address is not
+ *   valid after a cudaDeviceReset of that device.  All calls share the
+ *   array and it keeps the last call's contents (the search resets what
+ *   must start at zero); calls whose work overlaps on one GPU race on it
+ *   and must be serialized by the caller. */
 int sqg_search_noalloc(const sqg_index *ix, const float *queries, int nq, const int32_t *k, const int32_t *ef,
                        int max_k, int max_ef, uint32_t *out_ids, float *out_dists, sqg_stream_t stream);
 
 /* Size in bytes of the fixed scratch array used by sqg_search_noalloc. */
 size_t sqg_noalloc_scratch_bytes(void);
+
+/* ---- sharded search (an index split over several graphs) ---- */
+
+/* Merge per-shard results into one top-k per query.  An index too large
+ * for one GPU is split into `shards` shards, each with its own graph
+ * (Algorithm 2, Sec. 3.2, on the shard's vectors alone); every query is
+ * searched in every shard (Algorithm 1, Sec. 3.1.3, whose output is the k
+ * nearest expanded vertices sorted by (distance, id)), and this call merges
+ * the shards' lists by (distance, global id).  The paper has no sharded
+ * form; its scalability study (Sec. 5) keeps one graph per index.
+ *   ids, dists: DEVICE, [shards][nq][k] -- shard s's result list of query i
+ *   at ((s * nq) + i) * k, local ids (SQG_NO_ID = padding, distance +inf),
+ *   each list sorted by (distance, id).
+ *   offsets: HOST, shards values; global id = local id + offsets[s] (the
+ *   shards' id ranges must not overlap).
+ *   out_ids, out_dists: DEVICE, [nq][k], the k smallest (distance, global
+ *   id) of the shards' lists, padded with (SQG_NO_ID, +inf).
+ * 1 <= shards <= SQG_MAX_SHARDS, 1 <= k <= SQG_MAX_K; stream-ordered on
+ * `stream`, no allocation. */
+int sqg_merge_topk(const uint32_t *ids, const float *dists, int shards, int nq, int k, const uint32_t *offsets,
+                   uint32_t *out_ids, float *out_dists, sqg_stream_t stream);
 
 /* ---- learned early stop: training kernels (not in the paper) ---- */
 

@@ -20,6 +20,7 @@ SQG_ERR = {-1: "invalid argument", -2: "i/o error", -3: "bad index file format",
            -8: "unsupported index shape"}
 STATUS_CAPACITY, STATUS_LEARNED_STOP, STATUS_BAD_PARAM, STATUS_TIMEOUT = 1, 2, 4, 8
 MAX_K, MAX_EF = 256, 2048
+MAX_SHARDS = 32
 NO_ID = 0xFFFFFFFF
 GRAPH_IRREGULAR = 1  # sqg_build_graph_ex: the degree-unaligned "w/o GR" graph
 MLP_IN, MLP_HIDDEN, MLP_NPARAM = 16, 64, 5313
@@ -37,7 +38,7 @@ class SearchParams(C.Structure):
                 ("stop_logit", C.c_float), ("stop_every", C.c_int32), ("team", C.c_int32),
                 ("warps_per_block", C.c_int32), ("timing_events", C.c_void_p * 2),
                 ("visited_smem_log2", C.c_int32), ("prefetch", C.c_int32), ("lean", C.c_int32),
-                ("rotation", C.c_int32)]
+                ("rotation", C.c_int32), ("kernel", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -75,6 +76,7 @@ _SIGS = {
     "sqg_write_index2": (I32, [C.c_char_p, P, U64, U32, P, U32, P, U32, U64, U64, I32, U32, U32]),
     "sqg_search_noalloc": (I32, [P, P, I32, P, P, I32, I32, P, P, P]),
     "sqg_noalloc_scratch_bytes": (SZ, []),
+    "sqg_merge_topk": (I32, [P, P, I32, I32, I32, P, P, P, P]),
     "sqg_mlp_grad": (I32, [P, P, P, P, I32, P, P, P, P]),
     "sqg_mlp_adam": (I32, [P, P, P, P, I32, F32, F32, F32, F32, P]),
     "sqg_mlp_forward": (I32, [P, P, I32, P, P]),

@@ -75,7 +75,8 @@ class Index:
     def params(self, *, eps0: float = 0.0, multi_estimate: bool = True, hop_cap: int = 0, max_k: int = 0,
                max_ef: int = 0, stop_mlp: torch.Tensor | None = None, stop_logit: float = 0.0,
                stop_every: int = 1, warps_per_block: int = 0, timing_events=None, visited_smem_log2: int = 0,
-               prefetch: int = 0, lean: int = 0, rotation: int = 0, team: int = 0) -> B.SearchParams:
+               prefetch: int = 0, lean: int = 0, rotation: int = 0, team: int = 0,
+               kernel: int = 0) -> B.SearchParams:
         p = B.SearchParams()
         p.eps0 = float(eps0)
         p.multi_estimate = 1 if multi_estimate else 0
@@ -93,6 +94,7 @@ class Index:
         p.lean = int(lean)
         p.rotation = int(rotation)
         p.team = int(team)
+        p.kernel = int(kernel)
         if timing_events is not None:  # torch.cuda.Event pair, already recorded once
             p.timing_events[0] = timing_events[0].cuda_event
             p.timing_events[1] = timing_events[1].cuda_event

@@ -5,8 +5,10 @@ Knobs, all result-neutral (the search is bit-identical under each):
   prefetch           1: the next block copied into shared memory during
                      the merge; 2: also L2-prefetch the runner-up's block
   visited_smem_log2  shared-memory slots of the visited set (2^9, 2^10)
-  lean               1: the 64-register build (d <= 256, more resident
-                     warps); 2: the 96-register build
+  lean               0 / 1: the search kernel's builds for fewer / more
+                     resident warps (d <= 256; 1 caps the registers lower,
+                     with a few spills); 2: the general kernel's
+                     96-register build
   team               lanes per query: 32, or 16 / 8 with 2 / 4 queries per
                      warp (d <= 256; always the 96-register build)
 The tuner times every combination on the caller's own batch (CUDA events,
@@ -28,7 +30,7 @@ import pathlib
 import numpy as np
 import torch
 
-KNOBS = {"warps_per_block": (1, 2, 4), "prefetch": (1, 2), "visited_smem_log2": (9, 10), "lean": (1, 2),
+KNOBS = {"warps_per_block": (1, 2, 4), "prefetch": (1, 2), "visited_smem_log2": (9, 10), "lean": (0, 1, 2),
          "team": (32, 16, 8)}
 DEFAULT = {"warps_per_block": 4, "prefetch": 1, "visited_smem_log2": 0, "lean": 0, "team": 0}
 
@@ -40,7 +42,7 @@ def combos(ix, knobs=None):
     names = list(knobs)
     for combo in itertools.product(*(knobs[n] for n in names)):
         cfg = dict(zip(names, combo))
-        if cfg.get("team", 32) < 32 and (ix.d > 256 or cfg.get("lean", 2) == 1):
+        if cfg.get("team", 32) < 32 and (ix.d > 256 or cfg.get("lean", 2) != 2):
             continue
         yield cfg
 

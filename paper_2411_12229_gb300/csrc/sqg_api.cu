@@ -315,6 +315,7 @@ int pick_ch(uint32_t d) {
 
 struct LaunchPlan {
     int ch, nb, team, warps, grid;
+    bool compact;  // the compact kernel (search_compact.cu)
     size_t smem;
     SearchArgs a;  // layout fields filled in
     bool ghash;
@@ -323,14 +324,19 @@ struct LaunchPlan {
         ws_total;
 };
 
-int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_search_params &p, LaunchPlan &pl) {
+int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_search_params &p, LaunchPlan &pl,
+              bool traced = false) {
     const uint32_t d = ix->lay.d, R = ix->lay.R, bb = ix->lay.block_bytes;
     pl.ch = pick_ch(d);
     pl.nb = (int)(R / 32);
     if (pl.ch < 0 || (pl.nb != 1 && pl.nb != 2)) return SQG_ERR_UNSUPPORTED;
     pl.team = p.team == 0 ? 32 : p.team;
     const int V = 32 / pl.team;  // queries per warp
-    if (pl.team < 32) {
+    pl.compact = p.kernel != 1 && pl.team == 32 && pl.nb == 1 && pl.ch <= 2 && max_k <= 32 && max_ef <= 64 &&
+                 p.multi_estimate && !p.stop_mlp && !traced && p.prefetch != 2 && p.lean != 2;
+    if (p.kernel == 2 && !pl.compact) return SQG_ERR_UNSUPPORTED;
+    if (pl.compact) {
+    } else if (pl.team < 32) {
         // smaller teams: d <= 256, the 96-register build, no fused stop network
         if (pl.ch > 2 || p.stop_mlp) return SQG_ERR_UNSUPPORTED;
     } else if (p.lean != 2 && pl.ch <= 2) {
@@ -356,9 +362,17 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     a.o_buf1 = a.o_buf0;
     a.o_bar = (uint32_t)o; o += 16;
     a.o_planes = (uint32_t)o; o = align_up(o + 16 * (d / 32), 16);
-    a.o_beam = (uint32_t)o; o = align_up(o + 8 * (size_t)max_ef, 16);
-    a.o_res = (uint32_t)o; o = align_up(o + 8 * (size_t)max_k, 16);
-    a.o_spos = (uint32_t)o; o = align_up(o + 4 * (size_t)R, 16);
+    if (pl.compact) {
+        // two beam buffers of 64 packed entries, the step's candidates by
+        // rank (32 packed entries); the results live in registers
+        a.o_beam = (uint32_t)o; o += 2 * 64 * 8;
+        a.o_res = (uint32_t)o;
+        a.o_spos = (uint32_t)o; o += 32 * 8;
+    } else {
+        a.o_beam = (uint32_t)o; o = align_up(o + 8 * (size_t)max_ef, 16);
+        a.o_res = (uint32_t)o; o = align_up(o + 8 * (size_t)max_k, 16);
+        a.o_spos = (uint32_t)o; o = align_up(o + 4 * (size_t)R, 16);
+    }
     // visited set: up to 2^10 slots in shared memory; a longer search moves
     // to its warp's full-size table in the workspace
     const uint32_t smem_bits_default = 9u;  // 2^10 measured slower at large beams (less residency)
@@ -373,7 +387,8 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
         const size_t sm = cta + (size_t)w * V * warp_bytes;
         *blocks = 0;
         if (sm > ix->smem_optin) return cudaSuccess;
-        return pl.team < 32 ? search_occupancy_team(pl.ch, pl.nb, pl.team, w * 32, sm, blocks)
+        return pl.compact     ? search_occupancy_compact(pl.ch, p.lean, w * 32, sm, blocks)
+             : pl.team < 32 ? search_occupancy_team(pl.ch, pl.nb, pl.team, w * 32, sm, blocks)
              : pl.nb == 1   ? search_occupancy_nb1(pl.ch, w * 32, sm, blocks)
                             : search_occupancy_nb2(pl.ch, w * 32, sm, blocks);
     };
@@ -469,6 +484,7 @@ int check_params(const sqg_search_params &p) {
         !std::isfinite(p.eps0) ||
         (p.visited_smem_log2 != 0 && (p.visited_smem_log2 < 5 || p.visited_smem_log2 > 12)) ||
         p.prefetch < 0 || p.prefetch > 2 || p.lean < 0 || p.lean > 2 || p.rotation < 0 || p.rotation > 2 ||
+        p.kernel < 0 || p.kernel > 2 ||
         (p.stop_mlp && p.stop_every < 1))
         return SQG_ERR_INVALID_ARG;
     return SQG_OK;
@@ -650,6 +666,8 @@ extern "C" size_t sqg_workspace_size(const sqg_index *ix, int nq, int max_k, int
     sqg_search_params p = default_params();
     if (make_plan(ix, nq, max_k, max_ef, p, pl) != SQG_OK) return 0;
     size_t need = pl.ws_total;
+    p.kernel = 1;  // the general kernel (its visited tables follow its own residency)
+    if (make_plan(ix, nq, max_k, max_ef, p, pl) == SQG_OK) need = std::max(need, pl.ws_total);
     p.stop_mlp = reinterpret_cast<const float *>(16);  // any non-null: only the layout is planned
     if (make_plan(ix, nq, max_k, max_ef, p, pl) == SQG_OK) need = std::max(need, pl.ws_total);
     return need;
@@ -697,7 +715,7 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
         if (max_ef == 0) max_ef = std::max(max_k, hm[1]);
     }
     LaunchPlan pl;
-    int rc = make_plan(ix, nq, max_k, max_ef, p, pl);
+    int rc = make_plan(ix, nq, max_k, max_ef, p, pl, trace_feat != nullptr || path != nullptr);
     if (rc != SQG_OK) return rc;
     bool own_ws = false;
     if (!workspace) {
@@ -780,8 +798,9 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     if (e == cudaSuccess && p.timing_events[0])
         e = cudaEventRecord(reinterpret_cast<cudaEvent_t>(p.timing_events[0]), stream);
     if (e == cudaSuccess) {
-        e = pl.team < 32 ? launch_search_team(pl.ch, pl.nb, pl.team, dim3(pl.grid), dim3(pl.warps * 32), pl.smem,
-                                              stream, a)
+        e = pl.compact ? launch_search_compact(pl.ch, p.lean, dim3(pl.grid), dim3(pl.warps * 32), pl.smem, stream, a)
+            : pl.team < 32 ? launch_search_team(pl.ch, pl.nb, pl.team, dim3(pl.grid), dim3(pl.warps * 32), pl.smem,
+                                                stream, a)
             : pl.nb == 1 ? launch_search_nb1(pl.ch, dim3(pl.grid), dim3(pl.warps * 32), pl.smem, stream, a)
                          : launch_search_nb2(pl.ch, dim3(pl.grid), dim3(pl.warps * 32), pl.smem, stream, a);
     }

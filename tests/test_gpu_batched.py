@@ -17,7 +17,7 @@ def test_every_tuning_knob_gives_identical_results(tiny_index, tmp_path, monkeyp
     qd = torch.from_numpy(q).cuda()
     ref = ix.search(qd, 10, 64)
     cfgs = list(autotune.combos(ix))
-    assert len(cfgs) == 24 + 2 * 12  # teams of 16 and 8 lanes only with the 96-register build
+    assert len(cfgs) == 36 + 2 * 12  # teams of 16 and 8 lanes only with the 96-register build
     for cfg in cfgs:
         got = ix.search(qd, 10, 64, **cfg)
         assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]), cfg

@@ -145,12 +145,14 @@ def _check_search(ix, O, q, k, ef, **kw):
     return ids, dists, st
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("ef", [10, 16, 33, 64, 128, 300])
-def test_search_parity_r32(gpu_tiny, oracle_mod, ef):
+def test_search_parity_r32(gpu_tiny, oracle_mod, ef, kernel):
     """Algorithm 1 with multiple estimates and implicit re-ranking: ids,
-    distances and hop counts identical to the oracle."""
+    distances and hop counts identical to the oracle (kernel 0: the compact
+    kernel up to ef 64; 1: the general kernel throughout)."""
     ix, p, x, q = gpu_tiny
-    _check_search(ix, oracle_mod.Index(p), q, 10, ef)
+    _check_search(ix, oracle_mod.Index(p), q, 10, ef, kernel=kernel)
 
 
 @pytest.mark.parametrize("ef", [16, 64, 200])
