@@ -112,6 +112,37 @@ def test_tc_prepare_other_shapes(shaped, oracle_mod):
     print(f"d={ix.d}: recomputed {rec} of {qq.size} coordinates; worst error / bound {worst:.3g}")
 
 
+@pytest.fixture(scope="module")
+def wide_index(tmp_path_factory, lib_built):
+    """A small d = 1536 index (the uneven workload's dimension and recipe);
+    the rotation does not depend on n."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    from paper_2411_12229_gb300 import synth
+    from paper_2411_12229_gb300.api import Index
+    w = synth.small(synth.UNEVEN_1M_D1536, 300, 16)
+    p = tmp_path_factory.mktemp("wide") / "d1536.sqg"
+    ib.build_index(p, synth.base(w), 32)
+    return Index(p, 0), p
+
+
+@pytest.mark.parametrize("nq", [20000, 20001])
+def test_tc_prepare_production_size(wide_index, oracle_mod, nq):
+    """The uneven workload's batch: 20,000 queries of d = 1536 (and a ragged
+    20,001), 157 x 12 output tiles of 128 x 128 on the persistent grid of one
+    CTA per SM, so every CTA walks several tiles: the TMEM double buffer is
+    reused and the mbarrier phases flip past the first tile.  Every row's
+    planes, v_l, Delta and Sq equal the CUDA-core path's bit for bit; 200
+    seeded rows also equal the oracle's and lie within the error model."""
+    from paper_2411_12229_gb300 import synth
+    ix, p = wide_index
+    O = oracle_mod.Index(p)
+    q = synth.queries(synth.UNEVEN_1M_D1536, nq)
+    rows = np.sort(np.random.default_rng(nq).choice(nq, 200, replace=False))
+    rows = np.concatenate([rows, [nq - 1]])  # the ragged tile's last row
+    rec, worst = _check_prepared(ix, O, oracle_mod, q, rows)
+    print(f"nq={nq}: recomputed {rec} of {q.size} coordinates; worst error / bound {worst:.3g}")
+
+
 def _search_equal(ix, O, q, k, ef):
     qd = torch.from_numpy(q).cuda()
     ids, dists, st = ix.search(qd, k, ef, stats=True, rotation=2)
