@@ -24,8 +24,14 @@ def _exact_rerank(base: np.ndarray, q: np.ndarray, cand: np.ndarray, k: int):
 
 
 def ground_truth(base: np.ndarray, queries: np.ndarray, k: int, device=None, margin: int = 32,
-                 chunk: int = 1 << 18):
-    """Exact k nearest neighbours (ids int64, squared distances fp64)."""
+                 chunk: int = 1 << 18, qchunk: int = 8192):
+    """Exact k nearest neighbours (ids int64, squared distances fp64).  On a
+    device the queries go through in chunks of `qchunk` rows, so the
+    candidate matrix stays at qchunk x chunk floats."""
+    if device is not None and queries.shape[0] > qchunk:
+        parts = [ground_truth(base, queries[a:a + qchunk], k, device, margin, chunk, qchunk)
+                 for a in range(0, queries.shape[0], qchunk)]
+        return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
     base = np.ascontiguousarray(base, dtype=np.float32)
     queries = np.ascontiguousarray(queries, dtype=np.float32)
     kc = min(base.shape[0], k + margin)

@@ -38,9 +38,12 @@ def _sp(stream=None) -> int:
 
 
 def collect(ix, queries: np.ndarray, gt: np.ndarray, k: int, ef_cap: int, every: int, chunk: int = 8192,
-            target_hits: np.ndarray | None = None):
-    """Features and labels from traces of the plain search at ef_cap.  A row
-    is positive once the result holds as many true top-k ids as
+            target_hits: np.ndarray | None = None, label: str = "final"):
+    """Features and labels from traces of the plain search at ef_cap.
+
+    label "all": a row is positive once the result holds all k true
+    nearest neighbours (nothing the search could still add would raise its
+    recall).  label "final": once it holds as many true top-k ids as
     `target_hits` (per query; default: what the traced search ends with)."""
     cap = max(1, (4 * ef_cap + 64) // every + 1)
     feats, labels, qidx = [], [], []
@@ -53,7 +56,9 @@ def collect(ix, queries: np.ndarray, gt: np.ndarray, k: int, ef_cap: int, every:
         f, h, n = f.cpu().numpy(), h.cpu().numpy(), n.cpu().numpy()
         for i in range(b - a):
             final = len(np.intersect1d(ids[i], gt[a + i, :k]))
-            if target_hits is not None:
+            if label == "all":
+                final = k
+            elif target_hits is not None:
                 final = min(final, int(target_hits[a + i]))
             m = n[i]
             if m == 0:
@@ -190,28 +195,32 @@ def hits_of(ids: np.ndarray, gt: np.ndarray, k: int) -> np.ndarray:
 
 
 def fit(ix, train_q: np.ndarray, train_gt: np.ndarray, k: int, ef_cap: int, target: float, *, every: int = 2,
-        ef_ref: int | None = None, val_frac: float = 0.2, steps: int = 3000, seed: int = 0, log=None) -> StopModel:
+        ef_ref: int | None = None, val_frac: float = 0.2, steps: int = 3000, seed: int = 0, log=None,
+        label: str = "final") -> StopModel:
     """Trace, train, then pick the stop threshold on held-out queries: the
-    most aggressive logit whose recall still reaches `target`.  With ef_ref,
-    a row is positive once the traced search (at ef_cap) holds as many true
-    top-k ids as the plain search at ef_ref ends with for that query, so the
-    stop learns to match the smaller beam's result early and keeps the
-    larger beam for the queries that need it."""
+    most aggressive logit whose recall still reaches `target`.
+
+    label "all" (the target the stop is built for): a row is positive once
+    the result holds the true top-k, so a confident stop loses nothing and
+    the queries that never get there run to the fixed-ef cap.  label
+    "final" with ef_ref: once the traced search (at ef_cap) holds as many
+    true top-k ids as the plain search at ef_ref ends with for that query;
+    without ef_ref: as many as the traced search itself ends with."""
     nv = max(1, int(train_q.shape[0] * val_frac))
     tq, tg = train_q[nv:], train_gt[nv:]
     vq, vg = train_q[:nv], train_gt[:nv]
     th = None
-    if ef_ref is not None:
+    if ef_ref is not None and label != "all":
         th = np.empty(tq.shape[0], dtype=np.int32)
         for a in range(0, tq.shape[0], 8192):
             ids, _ = ix.search(torch.from_numpy(np.ascontiguousarray(tq[a:a + 8192])).cuda(), k, ef_ref)
             th[a:a + 8192] = hits_of(ids.cpu().numpy(), tg[a:a + 8192], k)
-    f, y, _ = collect(ix, tq, tg, k, ef_cap, every, target_hits=th)
+    f, y, _ = collect(ix, tq, tg, k, ef_cap, every, target_hits=th, label=label)
     P = train(f, y, steps=steps, seed=seed, log=log)
-    model = StopModel(P, 0.0, every, ef_cap, dict(rows=int(f.shape[0]), positive=float(y.mean())))
+    model = StopModel(P, 0.0, every, ef_cap, dict(rows=int(f.shape[0]), positive=float(y.mean()), label=label))
     vqd = torch.from_numpy(np.ascontiguousarray(vq)).cuda()
     best = None
-    for thr in (4.0, 3.0, 2.0, 1.5, 1.0, 0.5, 0.0, -0.5, -1.0, -2.0):
+    for thr in (6.0, 5.0, 4.0, 3.0, 2.0, 1.5, 1.0, 0.5, 0.0, -0.5, -1.0, -2.0):
         r, qps, hops = evaluate(ix, vqd, vg, k, ef_cap, model, logit=thr, reps=2)
         if log:
             log(f"stop threshold {thr:+.1f}: recall {r:.4f} hops {hops:.1f} qps {qps:.0f}")
@@ -219,6 +228,6 @@ def fit(ix, train_q: np.ndarray, train_gt: np.ndarray, k: int, ef_cap: int, targ
             best = thr
         else:
             break
-    model.logit = 4.0 if best is None else best
+    model.logit = 6.0 if best is None else best
     model.info.update(threshold=model.logit, val_queries=nv)
     return model
