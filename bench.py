@@ -324,6 +324,18 @@ def learned_stop_comparison(args, w, ix, pool_d, gt_ids, sweep, ef_sel, device, 
                 rows.append({"every": every, "ef_cap": cap, "logit": thr, **r})
     # the plain frontier on the same test batches (recall over the first 4)
     plain = {t: next((x for x in sweep if x["recall_4"] >= t), None) for t in (0.90, 0.95, 0.99)}
+    # what a perfect stop could save at each cap (first expansion holding the
+    # true top-10, from traces), and what evaluating the network costs (a
+    # threshold it never reaches: the same expansions as the plain search)
+    test_q = pool_d[:nq].cpu().numpy()
+    bound = [L.perfect_stop(ix, test_q, gt_ids[:nq], 10, cap) for cap in caps + [int(2.5 * ef_sel)]]
+    m0 = L.fit(ix, tq, tg, 10, ef_sel, args.target, every=8, steps=1000, label="all")
+    overhead = {}
+    for every in (4, 8, 16):
+        r = stop_point(ix, pool_d, gt_ids, nq, nbe, ef_sel, dict(stop_mlp=m0.params, stop_logit=1e30,
+                                                                  stop_every=every))
+        pl = next(x for x in sweep if x["ef"] == ef_sel)
+        overhead[str(every)] = round(1.0 - r["qps"] / pl["qps"], 4)
     at = {}
     for t in (0.90, 0.95, 0.99):
         ok = [x for x in rows if x["recall"] >= t]
@@ -334,6 +346,7 @@ def learned_stop_comparison(args, w, ix, pool_d, gt_ids, sweep, ef_sel, device, 
                       "qps_ratio": round(best["qps"] / pl["qps"], 4) if best and pl else None}
     log(f"learned stop in {time.time() - t0:.1f}s: {at}")
     return {"label": "the result holds the true top-10", "train_queries": int(ntrain), "variants": models,
+            "perfect_stop_bound": bound, "evaluation_overhead_by_period": overhead,
             "timing": f"graph-captured searches of {nbe} distinct batches of {nq}, 2 streams (as the headline)",
             "points": rows, "at_recall": at, "qps_ratio_vs_plain": at["0.95"]["qps_ratio"]}
 
@@ -470,6 +483,9 @@ def bench_mixed(args, w, ix, pool_d, pool, gt_ids, rank, world, dist, local, nb)
     hops = st[:, 0].double().cpu().numpy()
     alg = float(hops.sum() * ix.block_bytes + nq * 4 * ix.d + 8 * total0)
     peak, src = measured_peaks()
+    stop = None
+    if not args.skip_stop:  # the same job with the learned stop on (each query's ef is its cap)
+        stop = mixed_stop(args, w, ix, pool_d, gt_ids, kq, efq, nq, nb, max_k, max_ef, knobs, rec, value, local)
     line = {"metric": "queries/sec, mixed k and ef in one launch", "value": round(value, 1),
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -486,10 +502,115 @@ def bench_mixed(args, w, ix, pool_d, pool, gt_ids, rank, world, dist, local, nb)
             "roofline": {"bound": "hbm", "achieved": round(alg / (ms / 1e3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4), "peak_source": src,
                          "note": "job step time (plan + rotation + search), not the search kernel alone"},
+            "learned_stop": stop,
             "autotune": sorted(tune["table"], key=lambda r: r["ms"])[:6], "clocks": clk,
             "hops_mean": round(float(hops.mean()), 2), "gpu_launches": launches_per_step(w.d, args.metric) * args.steps}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def mixed_stop(args, w, ix, pool_d, gt_ids, kq, efq, nq, nb, max_k, max_ef, knobs, rec, plain_qps, device):
+    """The mixed batch with the learned stop on: one network for k in
+    {1, 10, 100} (traces at each group's largest beam, 8k), its threshold
+    the most aggressive whose held-out recall@min(k, 10) stays within 0.005
+    of the plain job's in every group; then the job again with the stop."""
+    import torch
+
+    from paper_2411_12229_gb300 import autotune
+    from paper_2411_12229_gb300 import eval as E
+    from paper_2411_12229_gb300 import learned_stop as L
+    t0 = time.time()
+    tq = synth.train_queries(w, args.stop_train or 8000)
+    tg, _ = E.ground_truth(synth.base(w), tq, 100, device=device)
+    groups = [(kk, min(8 * kk, max_ef)) for kk in sorted(set(kq.tolist()))]
+    model = L.fit_mixed(ix, tq, tg, groups, {kk: rec[str(kk)] - 0.005 for kk, _ in groups}, every=8, steps=2000)
+    kw = dict(stop_mlp=model.params, stop_logit=model.logit, stop_every=model.every)
+    graphs = []
+    for b in range(nb):
+        sl = slice(b * nq, (b + 1) * nq)
+        g = autotune.GraphSearch(ix, nq, kq[sl], efq[sl], max_k=max_k, max_ef=max_ef,
+                                 **{**knobs, "team": 32}, **kw)
+        g.q.copy_(pool_d[sl])
+        graphs.append(g)
+    for _ in range(3):
+        for g in graphs:
+            g.graph.replay()
+    ms = time_job(graphs, 2 * nb)
+    per_k = {}
+    for b in range(nb):
+        ids = graphs[b].ids.cpu().numpy()
+        kb = kq[b * nq:(b + 1) * nq]
+        off = np.concatenate([[0], np.cumsum(kb)])
+        for kk in sorted(set(kb.tolist())):
+            sel = np.nonzero(kb == kk)[0]
+            got = np.stack([ids[off[i]:off[i + 1]] for i in sel])
+            per_k.setdefault(kk, []).append((E.recall(got, gt_ids[b * nq + sel], kk), len(sel)))
+    srec = {str(kk): round(sum(r * n for r, n in v) / sum(n for _, n in v), 4) for kk, v in per_k.items()}
+    qps = nq / (ms / 1e3)
+    return {"threshold": model.logit, "every": model.every, "groups": groups, "recall_per_k": srec,
+            "qps": round(qps, 1), "qps_ratio_vs_plain": round(qps / plain_qps, 4),
+            "seconds": round(time.time() - t0, 1)}
+
+
+def bench_serving(args, w, ix, q, gt_ids, device):
+    """The serving loop (continuous batching, serve.Server) over Poisson
+    arrivals at the workload's offered loads, k in {10, 100}: p50/p99
+    latency, achieved QPS and recall@10, with the learned stop on and, for
+    comparison, off.  Each k gets the smallest ef of the sweep (>= k) whose
+    recall@10 on the test queries reaches the target; with the stop, k = 10
+    requests may search up to twice that beam."""
+    import torch
+
+    from paper_2411_12229_gb300 import eval as E
+    from paper_2411_12229_gb300 import learned_stop as L
+    from paper_2411_12229_gb300.serve import Server
+    t0 = time.time()
+    qd = torch.from_numpy(q).cuda()
+    ef_for = {}
+    for k in (10, 100):
+        for ef in [e for e in w.ef if e >= k] + [768, 1024]:
+            ids, _ = ix.search(qd, k, ef)
+            if E.recall(ids.cpu().numpy()[:, :10], gt_ids, 10) >= args.target:
+                break
+        ef_for[k] = ef
+    caps = {10: 2 * ef_for[10], 100: ef_for[100]}
+    tq = synth.train_queries(w, args.stop_train or 20000)
+    tg, _ = E.ground_truth(synth.base(w), tq, 100, device=device)
+    model = L.fit_mixed(ix, tq, tg, [(10, caps[10]), (100, caps[100])], args.target, every=4)
+    loads = (50_000, 100_000, 200_000, 500_000, 1_000_000, 2_000_000)
+    rng = np.random.default_rng(5)
+    table = {"stop": [], "plain": []}
+    for mode in ("stop", "plain"):
+        efmap = caps if mode == "stop" else ef_for
+        srv = Server(ix, max_k=100, max_ef=max(efmap.values()), mem_budget=256 << 20, streams=8, max_batch=8192,
+                     stop_model=model if mode == "stop" else None)
+        for load in loads:
+            m = int(min(200_000, max(4000, load * 1.0)))
+            sel = rng.integers(0, q.shape[0], size=m)
+            ks = np.where(rng.integers(0, 2, size=m) == 0, 10, 100).astype(np.int32)
+            efs = np.array([efmap[int(k)] for k in ks], dtype=np.int32)
+            r = srv.run(q[sel], ks, efs, synth.poisson_arrivals(float(load), m))
+            sm = r.summary()
+            got = np.full((m, 10), -1, np.int64)
+            for i in range(m):
+                got[i] = r.ids[i][:10]
+            sm.update(offered_qps=load, recall_at_10=round(E.recall(got, gt_ids[sel], 10), 4))
+            table[mode].append(sm)
+            log(f"serving {mode} {load}: {sm}")
+    ok = [x for x in table["stop"] if x["recall_at_10"] >= args.target]
+    best = max(ok, key=lambda x: x["qps"]) if ok else None
+    okp = [x for x in table["plain"] if x["recall_at_10"] >= args.target]
+    bestp = max(okp, key=lambda x: x["qps"]) if okp else None
+    line = {"metric": "queries/sec at recall@10>=0.95, serving loop (Poisson arrivals, continuous batching)",
+            "value": best["qps"] if best else None, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "d": w.d, "degree": w.degree, "k": "{10, 100}",
+                       "ef_for_k": ef_for, "stop_caps": caps, "streams": 8, "mem_budget_mb": 256,
+                       "offered_loads": list(loads)},
+            "learned_stop": {"threshold": model.logit, "every": model.every, "positive_rows": model.info["positive"]},
+            "table": table, "plain_best_qps": bestp["qps"] if bestp else None,
+            "seconds": round(time.time() - t0, 1)}
+    print(json.dumps(line), flush=True)
 
 
 def bench_reference(args):
@@ -707,6 +828,8 @@ def main():
         pool = np.ascontiguousarray(np.pad(pool, ((0, 0), (0, ix.d - pool.shape[1]))))
     pool_d = torch.from_numpy(pool).cuda()
     q, qd = pool[:nq], pool_d[:nq]
+    if w.name.startswith("serving"):
+        return bench_serving(args, w, ix, pool[:nq], gt_ids, local)
     if w.mixed_k:
         return bench_mixed(args, w, ix, pool_d, pool, gt_ids, rank, world, dist, local, nb)
     k = 10

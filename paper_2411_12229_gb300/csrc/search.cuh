@@ -418,40 +418,63 @@ struct StopState {
 };
 __device__ __forceinline__ float clamp8(float x) { return x < -8.0f ? -8.0f : (x > 8.0f ? 8.0f : x); }
 
-// MLP 16 -> 64 -> 64 -> 1 on one warp; weights in global memory (the same
-// 21 KB for every warp, so they stay in L1), layer matrices stored
-// transposed ([in][out]) so each input's weights are one coalesced row.  Hidden
-// neuron o is an fmaf chain over its inputs in order starting from its bias;
-// the output adds p_l = fmaf(W3[l+32], h[l+32], W3[l] h[l]) by xor butterfly,
-// then b3.
-__device__ __forceinline__ float mlp_logit_warp(const float *w, const float (&f)[SQG_MLP_IN], int lane) {
-    const float *W1t = w;                         // [16][64]
-    const float *b1 = W1t + SQG_MLP_IN * 64;      // [64]
-    const float *W2t = b1 + 64;                   // [64][64]
-    const float *b2 = W2t + 64 * 64;              // [64]
-    const float *W3 = b2 + 64;                    // [64]
-    const float *b3 = W3 + 64;                    // [1]
-    float ha = __ldg(b1 + lane), hb = __ldg(b1 + lane + 32);
+// MLP 16 -> 64 -> 64 -> 1 on one warp; lane l computes hidden neurons l and
+// l + 32 of both layers.  The parameters are read from global memory (the
+// same 21 KB for every warp, so they stay in L1) in a packed layout made once
+// per call (mlp_pack_kernel), so that one 16-byte load gives a lane the
+// weights of its two neurons for two consecutive inputs:
+//   W1p[i2][l] = (W1[l][2i2], W1[l+32][2i2], W1[l][2i2+1], W1[l+32][2i2+1]),
+//   b1p[l] = (b1[l], b1[l+32]), W2p[i2][l] likewise over the 64 inputs,
+//   b2p[l], W3p[l] = (W3[l], W3[l+32]), then b3.
+// Hidden neuron o is an fmaf chain over its inputs in order starting from
+// its bias; the first layer's outputs pass to the second through `hbuf`
+// (64 floats of the warp's shared memory); the output adds
+// p_l = fmaf(W3[l+32], h[l+32], W3[l] h[l]) by xor butterfly, then b3.
+__device__ __forceinline__ float mlp_logit_warp(const float *w, const float (&f)[SQG_MLP_IN], int lane,
+                                                float *hbuf) {
+    const float4 *W1p = reinterpret_cast<const float4 *>(w);               // [8][32]
+    const float2 *b1p = reinterpret_cast<const float2 *>(w + 8 * 32 * 4);  // [32]
+    const float4 *W2p = reinterpret_cast<const float4 *>(w + 8 * 32 * 4 + 64);        // [32][32]
+    const float2 *b2p = reinterpret_cast<const float2 *>(w + 8 * 32 * 4 + 64 + 32 * 32 * 4);
+    const float2 *W3p = b2p + 32;
+    const float *b3 = reinterpret_cast<const float *>(W3p + 32);
+    const float2 bb1 = __ldg(b1p + lane);
+    float ha = bb1.x, hb = bb1.y;
 #pragma unroll
-    for (int i = 0; i < SQG_MLP_IN; ++i) {
-        ha = __fmaf_rn(__ldg(W1t + i * 64 + lane), f[i], ha);
-        hb = __fmaf_rn(__ldg(W1t + i * 64 + lane + 32), f[i], hb);
+    for (int i2 = 0; i2 < SQG_MLP_IN / 2; ++i2) {
+        const float4 wv = __ldg(W1p + i2 * 32 + lane);
+        ha = __fmaf_rn(wv.x, f[2 * i2], ha);
+        hb = __fmaf_rn(wv.y, f[2 * i2], hb);
+        ha = __fmaf_rn(wv.z, f[2 * i2 + 1], ha);
+        hb = __fmaf_rn(wv.w, f[2 * i2 + 1], hb);
     }
-    ha = ha > 0.0f ? ha : 0.0f;
-    hb = hb > 0.0f ? hb : 0.0f;
-    float ga = __ldg(b2 + lane), gb = __ldg(b2 + lane + 32);
-#pragma unroll 8
-    for (int i = 0; i < 64; ++i) {
-        float hi = __shfl_sync(kFull, i < 32 ? ha : hb, i & 31);
-        ga = __fmaf_rn(__ldg(W2t + i * 64 + lane), hi, ga);
-        gb = __fmaf_rn(__ldg(W2t + i * 64 + lane + 32), hi, gb);
+    hbuf[lane] = ha > 0.0f ? ha : 0.0f;
+    hbuf[lane + 32] = hb > 0.0f ? hb : 0.0f;
+    __syncwarp();
+    const float2 bb2 = __ldg(b2p + lane);
+    float ga = bb2.x, gb = bb2.y;
+    const float4 *h4 = reinterpret_cast<const float4 *>(hbuf);
+#pragma unroll 4
+    for (int i4 = 0; i4 < 16; ++i4) {
+        const float4 h = h4[i4];
+        const float4 w0 = __ldg(W2p + (2 * i4) * 32 + lane), w1 = __ldg(W2p + (2 * i4 + 1) * 32 + lane);
+        ga = __fmaf_rn(w0.x, h.x, ga);
+        gb = __fmaf_rn(w0.y, h.x, gb);
+        ga = __fmaf_rn(w0.z, h.y, ga);
+        gb = __fmaf_rn(w0.w, h.y, gb);
+        ga = __fmaf_rn(w1.x, h.z, ga);
+        gb = __fmaf_rn(w1.y, h.z, gb);
+        ga = __fmaf_rn(w1.z, h.w, ga);
+        gb = __fmaf_rn(w1.w, h.w, gb);
     }
+    __syncwarp();  // hbuf may be reused after this
     ga = ga > 0.0f ? ga : 0.0f;
     gb = gb > 0.0f ? gb : 0.0f;
-    float p = __fmaf_rn(__ldg(W3 + lane + 32), gb, __fmul_rn(__ldg(W3 + lane), ga));
+    const float2 w3 = __ldg(W3p + lane);
+    float p = __fmaf_rn(w3.y, gb, __fmul_rn(w3.x, ga));
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) p = __fadd_rn(p, __shfl_xor_sync(kFull, p, o));
-    return __fadd_rn(p, __ldg(b3 + 0));
+    return __fadd_rn(p, __ldg(b3));
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -472,7 +495,7 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
     const uint32_t R = a.R, d = a.d, nch = d / 4;
     const float inv_R = __fdiv_rn(1.0f, (float)R);
 
-    const float *wts = a.mlp;  // the stop network, W1 and W2 transposed (global, L1-cached)
+    const float *wts = a.mlp;  // the stop network in its packed layout (global, L1-cached)
 
     unsigned char *ws = smem + a.cta_bytes + (size_t)(warp * V + team) * a.warp_bytes;
     unsigned char *buf[2] = {ws + a.o_buf0, ws + a.o_buf1};
@@ -928,7 +951,8 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
                     }
                     ++tn;
                 }
-                if (a.mlp && mlp_logit_warp(wts, f, lane) > a.stop_logit) {
+                if (a.mlp && mlp_logit_warp(wts, f, lane, reinterpret_cast<float *>(ws + a.o_spos)) >
+                                 a.stop_logit) {
                     status |= SQG_STATUS_LEARNED_STOP;
                     break;
                 }

@@ -71,10 +71,49 @@ __device__ __forceinline__ void hash_insert_warp(uint32_t *H, uint32_t bits, uin
     }
 }
 
+// S = sum_i b_i qbar_i of neighbour j (Sec. 3.1.1): AND + popc of its code
+// words against the 4 bit-planes, out-degree 32 (word w of neighbour j at
+// w * 32 + j); nw <= 4 * CH words.
+template <int CH>
+__device__ __forceinline__ int estimate_S32(const unsigned char *codes_b, const uint32_t *planes, uint32_t nw,
+                                            int j) {
+    const uint32_t *codes = reinterpret_cast<const uint32_t *>(codes_b) + j;
+    const uint4 *pl = reinterpret_cast<const uint4 *>(planes);
+    int s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll
+    for (uint32_t w = 0; w < 4 * CH; ++w) {
+        if (w < nw) {
+            const uint32_t c = codes[w * 32];
+            const uint4 p = pl[w];
+            s0 += __popc(c & p.x);
+            s1 += __popc(c & p.y);
+            s2 += __popc(c & p.z);
+            s3 += __popc(c & p.w);
+        }
+    }
+    return s0 + 2 * s1 + 4 * s2 + 8 * s3;
+}
+
+// The key of neighbour j from its S (the estimator of Sec. 3.1.1 and the
+// bound-shifted key of reading R7), out-degree 32: the same operations in
+// the same order as estimate_from_S.
+__device__ __forceinline__ float key32(const float *fac, const QuerySide &qs, uint32_t d, int j, int S,
+                                       float dist_c, float sqrt_dc, float eps0) {
+    const float f_add = fac[j], f_rescale = fac[32 + j];
+    const int pc = (int)reinterpret_cast<const uint32_t *>(fac)[96 + j];
+    const float A = (float)(2 * S - qs.sq);
+    const float B = __fmul_rn(qs.vl, (float)(2 * pc - (int)d));
+    const float ip = __fmul_rn(__fmaf_rn(qs.delta, A, B), qs.inv_sqrt_d);
+    const float est = __fmaf_rn(f_rescale, ip, __fadd_rn(f_add, dist_c));
+    if (eps0 == 0.0f) return est;
+    const float bound = __fmul_rn(fac[64 + j], sqrt_dc);
+    return __fsub_rn(est, __fmul_rn(eps0, bound));
+}
+
 }  // namespace
 
 // MINB: resident blocks of 4 warps per SM the build is made for -- 8 (up to
-// 64 registers, no spills) or 10 (48 registers, a few spilled bytes).
+// 64 registers) or 9 (56 registers).
 template <int CH, int MINB>
 __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -150,6 +189,8 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
         uint64_t bA = lane == 0 ? pack_entry(0u, a.entry) | 1ull : kNone;  // beam[lane]
         uint64_t bB = kNone;                                                 // beam[lane + 32]
         uint64_t res = kNone;                                                // result[lane], lane < k
+        uint64_t rworst = kNone;  // result[k - 1]: the entry a new result must beat
+        uint64_t bworst = kNone;  // beam[ef - 1] once the beam holds ef entries (the early cut)
         uint32_t p = a.entry;
         __syncwarp();
         hash_insert_warp(H, hbits, p, lane);
@@ -175,7 +216,7 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
             exact_partial<CH, 32>(reinterpret_cast<const float4(&)[1][CH]>(qv),
                                   reinterpret_cast<const float *>(blk), nch, tm, dacc);
             const uint32_t cid = reinterpret_cast<const uint32_t *>(blk + a.off_ids)[lane];
-            const int S = estimate_S<CH>(blk, a, planes, (uint32_t)lane);
+            const int S = estimate_S32<CH>(blk + a.off_codes, planes, d / 32, lane);
             const float dist_c = exact_reduce<32>(dacc, tm);
             if (hops == 1) {  // reading R8: the entry's key is its exact distance
                 if (lane == 0) {
@@ -183,26 +224,27 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                     beam_a[0] = bA;
                 }
                 __syncwarp();
+                if (ef == 1) bworst = shfl64(bA, 0);
             }
             {  // result top-k in registers: (dist bits << 32) | id, dist >= 0
                 const uint64_t r = ((uint64_t)__float_as_uint(dist_c) << 32) | p;
-                const uint64_t worst = shfl64(res, k - 1);
-                if (r < worst) {
+                if (r < rworst) {
                     const int pos = __popc(__ballot_sync(kFull, lane < k && res < r));
                     const uint64_t up = shfl64_up(res, 1);
                     if (lane == pos) res = r;
                     else if (lane > pos && lane < k) res = up;
+                    rworst = shfl64(res, k - 1);
                 }
             }
 
             // ---- line 5: the estimate and key of every neighbour from the same block
             const float sqrt_dc = a.eps0 == 0.0f ? 0.0f : __fsqrt_rn(dist_c);
-            const Est e = estimate_from_S(blk, a, qs, (uint32_t)lane, S, dist_c, sqrt_dc);
-            const uint64_t cand = pack_entry(key_bits(e.key), cid);
+            const float key = key32(reinterpret_cast<const float *>(blk + a.off_factors), qs, d, lane, S, dist_c,
+                                    sqrt_dc, a.eps0);
+            const uint64_t cand = pack_entry(key_bits(key), cid);
             // ---- line 6: unvisited neighbours enter the beam; an entry the cut to
             // ef would drop at once is skipped early
-            const uint64_t worst = m == ef ? shfl64((ef - 1) < 32 ? bA : bB, (ef - 1) & 31) : kNone;
-            bool adm = cid != kEmpty && cand < worst;
+            bool adm = cid != kEmpty && cand < bworst;
             if (adm) adm = !hash_contains(H, hbits, cid);
             uint32_t am = __ballot_sync(kFull, adm);
 
@@ -256,11 +298,15 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
             }
             if (am) {
                 const int nadm = __popc(am);
-                int rank = 0;  // among the admitted candidates (their ids are distinct)
-                for (uint32_t mm = am; mm; mm &= mm - 1) {
-                    const uint64_t o = shfl64(cand, __ffs(mm) - 1);
-                    rank += o < cand ? 1 : 0;
-                }
+                // rank among the admitted candidates (their ids are distinct):
+                // the candidates are compacted into the stage, and every lane
+                // counts the smaller ones with broadcast reads
+                if (adm) stage[__popc(am & ((1u << lane) - 1u))] = cand;
+                __syncwarp();
+                int rank = 0;
+#pragma unroll 4
+                for (int j = 0; j < nadm; ++j) rank += stage[j] < cand ? 1 : 0;
+                __syncwarp();
                 const int fp = pos + rank;  // final position in the merged beam
                 if (adm) stage[rank] = cand;
                 const uint32_t lo = __reduce_or_sync(kFull, adm && fp < 32 ? 1u << fp : 0u);
@@ -293,6 +339,9 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                 beam_b = beam_a;
                 beam_a = Bn;
                 m = m2;
+                // (a visited mark set below does not matter to the early cut: no
+                // candidate shares an id with a visited entry)
+                bworst = m == ef ? shfl64((ef - 1) < 32 ? bA : bB, (ef - 1) & 31) : kNone;
             }
 
             // ---- line 3: the next vertex is visited; every copy of it in the
@@ -350,13 +399,13 @@ static cudaError_t compact_occ_one(int block, size_t smem, int *nb) {
 #define SQG_COMPACT_SWITCH(CALL)                      \
     switch (ch * 10 + (lean == 1 ? 1 : 0)) {          \
         case 10: return CALL(1, 8);                   \
-        case 11: return CALL(1, 10);                  \
+        case 11: return CALL(1, 9);                   \
         case 20: return CALL(2, 8);                   \
-        case 21: return CALL(2, 10);                  \
+        case 21: return CALL(2, 9);                   \
         default: return cudaErrorInvalidValue;        \
     }
 
-// lean 1: the build for 10 resident blocks (48 registers); else 8 (64)
+// lean 1: the build for 9 resident blocks (56 registers); else 8 (64)
 cudaError_t launch_search_compact(int ch, int lean, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                                   const SearchArgs &a) {
 #define CALL(C, M) compact_launch_one<C, M>(grid, block, smem, s, a)

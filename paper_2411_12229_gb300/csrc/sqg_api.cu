@@ -58,7 +58,7 @@ inline bool aligned(const void *p, size_t a) { return reinterpret_cast<uintptr_t
 // Output offsets (exclusive prefix sum of each query's slot count) and the
 // largest valid k / ef of the batch.  One block; each thread scans
 // kPlanItems consecutive queries of a tile, so a 10k batch takes two tiles.
-constexpr int kPlanItems = 8;
+constexpr int kPlanItems = 16;
 __global__ void plan_kernel(const int32_t *k, const int32_t *ef, int nq, long long *offsets, int *maxes) {
     __shared__ long long warp_sums[kPlanThreads / 32];
     __shared__ long long carry;
@@ -123,69 +123,108 @@ __global__ void plan_kernel(const int32_t *k, const int32_t *ef, int nq, long lo
 }
 
 // The stop network's parameters (W1 [64][16], b1, W2 [64][64], b2, W3, b3)
-// with W1 and W2 transposed to [in][out], so a warp reads a layer's weights
-// for one input as one coalesced row.
+// in the packed layout mlp_logit_warp reads: for lane l and input pair i2,
+// the weights of neurons l and l + 32 for inputs 2 i2 and 2 i2 + 1 side by
+// side (one 16-byte load), the biases and output weights of l and l + 32 as
+// pairs, then b3.
 __global__ void mlp_transpose_kernel(const float *__restrict__ src, float *__restrict__ dst) {
     const float *W1 = src, *b1 = W1 + 64 * SQG_MLP_IN, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64;
     float *t = dst;
-    for (int i = threadIdx.x; i < 64 * SQG_MLP_IN; i += blockDim.x) t[(i % SQG_MLP_IN) * 64 + i / SQG_MLP_IN] = W1[i];
-    t += 64 * SQG_MLP_IN;
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) t[i] = b1[i];
+    for (int e = threadIdx.x; e < 8 * 32; e += blockDim.x) {  // W1p[i2][l]
+        const int i2 = e / 32, l = e % 32;
+        t[4 * e + 0] = W1[l * SQG_MLP_IN + 2 * i2];
+        t[4 * e + 1] = W1[(l + 32) * SQG_MLP_IN + 2 * i2];
+        t[4 * e + 2] = W1[l * SQG_MLP_IN + 2 * i2 + 1];
+        t[4 * e + 3] = W1[(l + 32) * SQG_MLP_IN + 2 * i2 + 1];
+    }
+    t += 8 * 32 * 4;
+    for (int l = threadIdx.x; l < 32; l += blockDim.x) {
+        t[2 * l] = b1[l];
+        t[2 * l + 1] = b1[l + 32];
+    }
     t += 64;
-    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) t[(i % 64) * 64 + i / 64] = W2[i];
-    t += 64 * 64;
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) t[i] = b2[i];
-    t += 64;
-    for (int i = threadIdx.x; i < 65; i += blockDim.x) t[i] = W3[i];  // W3 and b3
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {  // W2p[i2][l]
+        const int i2 = e / 32, l = e % 32;
+        t[4 * e + 0] = W2[l * 64 + 2 * i2];
+        t[4 * e + 1] = W2[(l + 32) * 64 + 2 * i2];
+        t[4 * e + 2] = W2[l * 64 + 2 * i2 + 1];
+        t[4 * e + 3] = W2[(l + 32) * 64 + 2 * i2 + 1];
+    }
+    t += 32 * 32 * 4;
+    for (int l = threadIdx.x; l < 32; l += blockDim.x) {
+        t[2 * l] = b2[l];
+        t[2 * l + 1] = b2[l + 32];
+        t[64 + 2 * l] = W3[l];
+        t[64 + 2 * l + 1] = W3[l + 32];
+    }
+    if (threadIdx.x == 0) t[128] = W3[64];  // b3
 }
 
 // q' = P^-1 q for a batch (Eq. (4)) in the canonical chunked order:
 // out[r][i] = (((0 + s_0) + s_1) + ...) over the d/32 chunks, s_c the fmaf
 // chain of rot[i][j] * q[r][j] over j = 32c .. 32c+31 from 0.  64 x 64 output
-// tiles, 256 threads with 4 x 4 outputs each; every output walks j in order
-// with one chunk accumulator and one total, so the tiling changes no bit.
-constexpr int kRotT = 64, kRotK = 16;
-static_assert(32 % kRotK == 0, "a chunk spans whole k-steps");
+// tiles, 256 threads with 4 x 4 outputs each; one 32-wide chunk of q and of
+// P^-1 per step, double-buffered in shared memory (the next chunk's global
+// loads are in flight while this one is multiplied), so every output walks
+// j in order with one chunk accumulator and one total and the tiling changes
+// no bit.
+constexpr int kRotT = 64, kRotK = 32;
 __global__ void __launch_bounds__(256) rotate_kernel(const float *__restrict__ q, const float *__restrict__ rot,
                                                      float *__restrict__ out, int nq, int d) {
-    __shared__ float As[kRotK][kRotT + 4];  // [j][row]
-    __shared__ float Bs[kRotK][kRotT + 4];  // [j][col]
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    __shared__ __align__(16) float As[2][kRotK][kRotT + 4];  // [buffer][j][row]
+    __shared__ __align__(16) float Bs[2][kRotK][kRotT + 4];  // [buffer][j][col]
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     const int r0 = blockIdx.y * kRotT, c0 = blockIdx.x * kRotT;
+    constexpr int kPer = kRotT * kRotK / 256;  // elements of each tile a thread moves
+    float ra[kPer], rb[kPer];
+    auto load = [&](int j0) {
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+            const int e = tid + 256 * t, rr = e / kRotK, jj = e % kRotK;
+            const int gr = r0 + rr, gc = c0 + rr;
+            ra[t] = gr < nq ? q[(size_t)gr * d + j0 + jj] : 0.0f;
+            rb[t] = gc < d ? rot[(size_t)gc * d + j0 + jj] : 0.0f;
+        }
+    };
+    auto store = [&](int b) {
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+            const int e = tid + 256 * t, rr = e / kRotK, jj = e % kRotK;
+            As[b][jj][rr] = ra[t];
+            Bs[b][jj][rr] = rb[t];
+        }
+    };
     float acc[4][4], tot[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = tot[a][b] = 0.0f;
-    for (int j0 = 0; j0 < d; j0 += kRotK) {
-        for (int e = threadIdx.x; e < kRotT * kRotK; e += 256) {
-            const int rr = e / kRotK, jj = e % kRotK;
-            const int gr = r0 + rr, gc = c0 + rr;
-            As[jj][rr] = gr < nq ? q[(size_t)gr * d + j0 + jj] : 0.0f;
-            Bs[jj][rr] = gc < d ? rot[(size_t)gc * d + j0 + jj] : 0.0f;
-        }
-        __syncthreads();
+        for (int b = 0; b < 4; ++b) tot[a][b] = 0.0f;
+    load(0);
+    store(0);
+    __syncthreads();
+    const int nchunk = d / kRotK;
+    for (int c = 0; c < nchunk; ++c) {
+        const int buf = c & 1;
+        if (c + 1 < nchunk) load((c + 1) * kRotK);
 #pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+#pragma unroll 8
         for (int jj = 0; jj < kRotK; ++jj) {
-            float av[4], bv[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = As[jj][ty * 4 + a];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = Bs[jj][tx * 4 + b];
+            const float4 av = *reinterpret_cast<const float4 *>(&As[buf][jj][ty * 4]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[buf][jj][tx * 4]);
+            const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = __fmaf_rn(bv[b], av[a], acc[a][b]);
+                for (int b = 0; b < 4; ++b) acc[a][b] = __fmaf_rn(b4[b], a4[a], acc[a][b]);
         }
-        if (((j0 + kRotK) & 31) == 0) {  // end of a 32-wide chunk
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    tot[a][b] = __fadd_rn(tot[a][b], acc[a][b]);
-                    acc[a][b] = 0.0f;
-                }
-        }
+            for (int b = 0; b < 4; ++b) tot[a][b] = __fadd_rn(tot[a][b], acc[a][b]);
+        if (c + 1 < nchunk) store(buf ^ 1);
         __syncthreads();
     }
 #pragma unroll
@@ -371,7 +410,9 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     } else {
         a.o_beam = (uint32_t)o; o = align_up(o + 8 * (size_t)max_ef, 16);
         a.o_res = (uint32_t)o; o = align_up(o + 8 * (size_t)max_k, 16);
-        a.o_spos = (uint32_t)o; o = align_up(o + 4 * (size_t)R, 16);
+        // the admitted candidates' positions; also the stop network's 64
+        // hidden values between its layers
+        a.o_spos = (uint32_t)o; o = align_up(o + std::max<size_t>(4 * (size_t)R, 256), 16);
     }
     // visited set: up to 2^10 slots in shared memory; a longer search moves
     // to its warp's full-size table in the workspace

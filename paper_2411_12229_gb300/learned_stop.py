@@ -231,3 +231,76 @@ def fit(ix, train_q: np.ndarray, train_gt: np.ndarray, k: int, ef_cap: int, targ
     model.logit = 6.0 if best is None else best
     model.info.update(threshold=model.logit, val_queries=nv)
     return model
+
+
+def fit_mixed(ix, train_q: np.ndarray, train_gt: np.ndarray, groups, target, *, every: int = 4,
+              val_frac: float = 0.2, steps: int = 3000, seed: int = 0, log=None) -> StopModel:
+    """One stop network for requests of several k (the serving workload's
+    k in {10, 100}): groups = [(k, ef_cap), ...].  Traces of every group
+    are pooled with the label "the result holds the true top-k" (the
+    features carry k, so the network can tell the groups apart); the
+    threshold is the most aggressive logit whose held-out recall@10 reaches
+    `target` in every group (a float, or a {k: target} dict).  The model's
+    ef_cap is the largest group's."""
+    tgt = target if isinstance(target, dict) else {k: target for k, _ in groups}
+    nv = max(1, int(train_q.shape[0] * val_frac))
+    tq, tg = train_q[nv:], train_gt[nv:]
+    vq, vg = train_q[:nv], train_gt[:nv]
+    fs, ys = [], []
+    for k, cap in groups:
+        f, y, _ = collect(ix, tq, tg, k, cap, every, label="all")
+        fs.append(f)
+        ys.append(y)
+    f, y = np.concatenate(fs), np.concatenate(ys)
+    P = train(f, y, steps=steps, seed=seed, log=log)
+    model = StopModel(P, 0.0, every, max(c for _, c in groups),
+                      dict(rows=int(f.shape[0]), positive=float(y.mean()), label="all", groups=list(groups)))
+    vqd = torch.from_numpy(np.ascontiguousarray(vq)).cuda()
+    best = None
+    for thr in (6.0, 5.0, 4.0, 3.0, 2.0, 1.5, 1.0, 0.5, 0.0, -0.5, -1.0, -2.0):
+        ok = True
+        for k, cap in groups:
+            ids, _ = ix.search(vqd, k, cap, stop_mlp=P, stop_logit=thr, stop_every=every)
+            from .eval import recall
+            kk = min(k, 10)
+            r = recall(ids.cpu().numpy()[:, :kk], vg, kk)
+            ok = ok and r >= tgt[k]
+            if log:
+                log(f"stop threshold {thr:+.1f} k={k} ef={cap}: recall@10 {r:.4f}")
+        if not ok:
+            break
+        best = thr
+    model.logit = 6.0 if best is None else best
+    model.info.update(threshold=model.logit, val_queries=nv)
+    return model
+
+
+def perfect_stop(ix, queries: np.ndarray, gt: np.ndarray, k: int, ef_cap: int, chunk: int = 4096) -> dict:
+    """What any stop can gain at this cap: traces of the plain search
+    (features after every expansion once the result holds k entries) give,
+    per query, the first expansion after which the result holds all k true
+    nearest neighbours.  A stop that fired exactly there, and never for
+    queries that do not get there, keeps the plain search's recall and
+    expands min(that expansion, the plain count).  Returns the plain recall
+    and mean expansions and this bound's mean expansions."""
+    from .eval import recall
+    cap = 4 * ef_cap + 64
+    gt_d = torch.from_numpy(np.ascontiguousarray(gt[:, :k], dtype=np.int32)).cuda()
+    hops_all, best_all, ids_all = [], [], []
+    for a in range(0, queries.shape[0], chunk):
+        b = min(queries.shape[0], a + chunk)
+        qd = torch.from_numpy(np.ascontiguousarray(queries[a:b])).cuda()
+        ids, _, st, f, h, n = ix.search_trace(qd, k, ef_cap, gt_d[a:b], cap, stop_every=1)
+        hops = st[:, 0].cpu().numpy().astype(np.int64)
+        f0 = f[:, :, 0].cpu().numpy()  # hops / ef at each evaluation point
+        h, n = h.cpu().numpy(), n.cpu().numpy()
+        for i in range(b - a):
+            rows = np.nonzero(h[i, :n[i]] >= k)[0]
+            best_all.append(int(round(float(f0[i, rows[0]]) * ef_cap)) if rows.size else int(hops[i]))
+        hops_all.append(hops)
+        ids_all.append(ids.cpu().numpy())
+    hops = np.concatenate(hops_all)
+    best = np.minimum(np.array(best_all, dtype=np.int64), hops)
+    return {"ef": int(ef_cap), "recall": round(recall(np.concatenate(ids_all), gt, k), 4),
+            "hops": round(float(hops.mean()), 2), "perfect_stop_hops": round(float(best.mean()), 2),
+            "saving": round(1.0 - float(best.mean()) / float(hops.mean()), 4)}

@@ -12,7 +12,8 @@ Memory per request (the admission unit) is what the search holds for it:
 beam ef x 8 B, result k x 8 B, visited hash 4 x 2^ceil(log2(2(4 ef + 64)+1))
 B, the rotated query 4d B and its offset/stats (16 B), plus its output.
 The search is deterministic per query, so a request's result is the same
-alone and in any mix (tested).
+alone and in any mix (tested).  The offered-load sweep on the serving
+workload is `python bench.py --workload serving-4m-d96`.
 """
 
 from __future__ import annotations
@@ -40,6 +41,8 @@ class ServeResult:
     batches: int
     max_inflight_bytes: int
     wall_s: float
+    search_ms: float = 0.0  # device time of the batches' searches (events around each launch), summed
+    loop_s: float = 0.0     # host time spent admitting, launching and retiring (the loop's own work)
 
     def summary(self) -> dict:
         lat = self.latency_s * 1e3
@@ -47,7 +50,9 @@ class ServeResult:
         return {"requests": int(len(lat)), "qps": round(len(lat) / max(self.wall_s, 1e-9), 1),
                 "p50_ms": round(float(np.percentile(lat, 50)), 4), "p99_ms": round(float(np.percentile(lat, 99)), 4),
                 "mean_ms": round(float(lat.mean()), 4), "batches": self.batches,
-                "max_inflight_bytes": self.max_inflight_bytes, "span_s": round(span, 4)}
+                "mean_batch": round(len(lat) / max(self.batches, 1), 1),
+                "max_inflight_bytes": self.max_inflight_bytes, "span_s": round(span, 4),
+                "device_search_s": round(self.search_ms / 1e3, 4), "host_loop_s": round(self.loop_s, 4)}
 
 
 class Server:
@@ -91,29 +96,40 @@ class Server:
             if self.stop is not None:
                 kw = dict(stop_mlp=self.stop.params, stop_logit=self.stop.logit, stop_every=self.stop.every)
             tot = int(ks[sel].sum())
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
             self.ix.search(qd, kd, ed, out=(slot["ids"][:tot], slot["dists"][:tot]), workspace=slot["ws"],
                            max_k=self.max_k, max_ef=self.max_ef, stream=s, **kw)
+            e1.record(s)
             slot["ih"][:tot].copy_(slot["ids"][:tot], non_blocking=True)
             slot["dh"][:tot].copy_(slot["dists"][:tot], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
         # keep the device tensors alive until the batch completes
-        slot["busy"] = (ev, sel, tot, (qd, kd, ed))
+        slot["busy"] = (ev, sel, tot, (qd, kd, ed), (e0, e1))
 
     def run(self, queries: np.ndarray, ks: np.ndarray, efs: np.ndarray, arrivals_s: np.ndarray) -> ServeResult:
+        """Serve requests (query, k, ef) arriving at arrivals_s seconds from
+        the start.  Admission and retirement are vectorized over the
+        requests they move, so the host loop's cost per request stays small
+        next to the search's."""
         n = queries.shape[0]
         order = np.argsort(arrivals_s, kind="stable")
+        arr_sorted = np.asarray(arrivals_s, dtype=np.float64)[order]
         need = np.array([request_bytes(int(k), int(e), self.ix.d) for k, e in zip(ks, efs)], dtype=np.int64)
+        cum_need = np.concatenate([[0], np.cumsum(need[order])])  # bytes of the first i requests in arrival order
         lat = np.zeros(n)
         done_at = np.zeros(n)
-        out_ids, out_d = [None] * n, [None] * n
+        ks = np.ascontiguousarray(ks, dtype=np.int32)
+        efs = np.ascontiguousarray(efs, dtype=np.int32)
+        ids_out = np.full((n, self.max_k), -1, dtype=np.int32)
+        d_out = np.full((n, self.max_k), np.inf, dtype=np.float32)
         nxt = 0            # next request (in arrival order) not yet admitted
         inflight = 0       # bytes held by running batches
         held = {}          # slot index -> bytes
         peak, batches, finished = 0, 0, 0
+        search_ms, idle_s = 0.0, 0.0
         queries = np.ascontiguousarray(queries, dtype=np.float32)
-        ks = np.ascontiguousarray(ks, dtype=np.int32)
-        efs = np.ascontiguousarray(efs, dtype=np.int32)
         t0 = time.perf_counter()
         while finished < n:
             now = time.perf_counter() - t0
@@ -122,117 +138,46 @@ class Server:
                 b = slot["busy"]
                 if b is not None and b[0].query():
                     tdone = time.perf_counter() - t0
-                    ev, sel, tot, _ = b
-                    ih, dh = slot["ih"][:tot].numpy(), slot["dh"][:tot].numpy()
-                    off = 0
-                    for r in sel:
-                        kk = int(ks[r])
-                        out_ids[r], out_d[r] = ih[off:off + kk].copy(), dh[off:off + kk].copy()
-                        off += kk
-                        lat[r] = tdone - arrivals_s[r]
-                        done_at[r] = tdone
+                    ev, sel, tot, _, (e0, e1) = b
+                    search_ms += e0.elapsed_time(e1)
+                    kk = ks[sel]
+                    rows = np.repeat(sel, kk)
+                    cols = np.arange(tot) - np.repeat(np.cumsum(kk) - kk, kk)
+                    ids_out[rows, cols] = slot["ih"][:tot].numpy()
+                    d_out[rows, cols] = slot["dh"][:tot].numpy()
+                    lat[sel] = tdone - arrivals_s[sel]
+                    done_at[sel] = tdone
                     finished += len(sel)
                     inflight -= held.pop(si)
                     slot["busy"] = None
                     progressed = True
             for si, slot in enumerate(self.slots):  # admit arrived requests
-                if slot["busy"] is not None or nxt >= n or arrivals_s[order[nxt]] > now:
+                if slot["busy"] is not None or nxt >= n or arr_sorted[nxt] > now:
                     continue
-                sel, budget = [], self.mem_budget - inflight
-                while (nxt < n and len(sel) < self.max_batch and arrivals_s[order[nxt]] <= now
-                       and need[order[nxt]] <= budget):
-                    r = order[nxt]
-                    sel.append(r)
-                    budget -= need[r]
-                    nxt += 1
-                if not sel:
+                arrived = int(np.searchsorted(arr_sorted, now, side="right"))
+                fit = int(np.searchsorted(cum_need, cum_need[nxt] + self.mem_budget - inflight, side="right")) - 1
+                end = min(arrived, fit, nxt + self.max_batch)
+                if end <= nxt:
                     break  # memory full: wait for a completion
-                b = int(need[sel].sum())
+                sel = order[nxt:end]
+                b = int(cum_need[end] - cum_need[nxt])
+                nxt = end
                 held[si] = b
                 inflight += b
                 peak = max(peak, inflight)
-                self._launch(slot, np.array(sel), queries, ks, efs)
+                self._launch(slot, sel, queries, ks, efs)
                 batches += 1
                 progressed = True
             if not progressed:
+                ts = time.perf_counter()
                 if nxt < n and all(s["busy"] is None for s in self.slots):
-                    wait = arrivals_s[order[nxt]] - (time.perf_counter() - t0)
+                    wait = arr_sorted[nxt] - (time.perf_counter() - t0)
                     if wait > 2e-4:
                         time.sleep(wait - 1e-4)
                 else:
                     time.sleep(2e-5)
+                idle_s += time.perf_counter() - ts
         wall = time.perf_counter() - t0
-        return ServeResult(lat, done_at, out_ids, out_d, batches, peak, wall)
-
-
-def main():
-    """Offered-load sweep on the serving workload: p50/p99 latency and QPS."""
-    import argparse
-    import json
-    import os
-    import pathlib
-    import sys
-
-    sys.path.insert(0, str(pathlib.Path(__file__).resolve().parents[1]))
-    from . import eval as E
-    from . import index_builder as ib
-    from . import synth
-    from .api import Index
-
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="serving-4m-d96")
-    ap.add_argument("--n", type=int, default=0)
-    ap.add_argument("--loads", default="50000,100000,200000,500000,1000000,2000000")
-    ap.add_argument("--seconds", type=float, default=1.0)
-    ap.add_argument("--cache", default=os.environ.get("SQG_CACHE", "/tmp/sqg_cache"))
-    ap.add_argument("--mem-mb", type=int, default=256)
-    ap.add_argument("--streams", type=int, default=4)
-    ap.add_argument("--target", type=float, default=0.95)
-    args = ap.parse_args()
-    w = synth.WORKLOADS[args.workload]
-    if args.n:
-        w = synth.small(w, args.n, w.n_queries)
-    cache = pathlib.Path(args.cache)
-    cache.mkdir(parents=True, exist_ok=True)
-    path = cache / f"{w.name}-n{w.n}-R{w.degree}-it3-ef400.sqg"
-    if not path.exists():
-        base = synth.base(w)
-        ib.build_index(str(path) + ".part", base, w.degree, device=0, init="random", iterations=3, ef_build=400)
-        os.replace(str(path) + ".part", path)
-    else:
-        base = None
-    ix = Index(path, 0)
-    q = synth.queries(w)
-    base = synth.base(w) if base is None else base
-    gt, _ = E.ground_truth(base, q, 100, device=0)
-    qd = torch.from_numpy(q).cuda()
-    # ef per k calibrated on the test queries: the smallest ef reaching the
-    # target recall@k (k = 10 and k = 100)
-    ef_for = {}
-    for k in (10, 100):
-        for ef in [e for e in synth.EF_SWEEP if e >= k] + [768, 1024]:
-            ids, _ = ix.search(qd, k, ef)
-            if E.recall(ids.cpu().numpy(), gt, k) >= args.target:
-                break
-        ef_for[k] = ef
-    res = {"workload": w.name, "n": w.n, "ef_for_k": ef_for, "loads": []}
-    srv = Server(ix, max_k=100, max_ef=max(ef_for.values()), mem_budget=args.mem_mb << 20,
-                 streams=args.streams, max_batch=8192)
-    rng = np.random.default_rng(5)
-    for load in [int(x) for x in args.loads.split(",")]:
-        m = int(min(200_000, max(2000, load * args.seconds)))
-        sel = rng.integers(0, q.shape[0], size=m)
-        ks = np.where(rng.integers(0, 2, size=m) == 0, 10, 100).astype(np.int32)
-        efs = np.array([ef_for[int(k)] for k in ks], dtype=np.int32)
-        arr = synth.poisson_arrivals(float(load), m)
-        r = srv.run(q[sel], ks, efs, arr)
-        s = r.summary()
-        hit = [len(np.intersect1d(r.ids[i], gt[sel[i], :10])) / 10 for i in range(m) if ks[i] == 10]
-        s.update(offered_qps=load, recall_at_10=round(float(np.mean(hit)), 4))
-        res["loads"].append(s)
-        print(json.dumps(s), flush=True)
-    print(json.dumps(res))
-
-
-if __name__ == "__main__":
-    main()
+        out_ids = [ids_out[i, :ks[i]] for i in range(n)]
+        out_d = [d_out[i, :ks[i]] for i in range(n)]
+        return ServeResult(lat, done_at, out_ids, out_d, batches, peak, wall, search_ms, wall - idle_s)
