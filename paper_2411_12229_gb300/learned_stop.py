@@ -234,15 +234,27 @@ def fit(ix, train_q: np.ndarray, train_gt: np.ndarray, k: int, ef_cap: int, targ
 
 
 def fit_mixed(ix, train_q: np.ndarray, train_gt: np.ndarray, groups, target, *, every: int = 4,
-              val_frac: float = 0.2, steps: int = 3000, seed: int = 0, log=None) -> StopModel:
+              val_frac: float = 0.2, steps: int = 3000, seed: int = 0, log=None,
+              max_loss: float | None = None) -> StopModel:
     """One stop network for requests of several k (the serving workload's
     k in {10, 100}): groups = [(k, ef_cap), ...].  Traces of every group
     are pooled with the label "the result holds the true top-k" (the
     features carry k, so the network can tell the groups apart); the
     threshold is the most aggressive logit whose held-out recall@10 reaches
-    `target` in every group (a float, or a {k: target} dict).  The model's
-    ef_cap is the largest group's."""
-    tgt = target if isinstance(target, dict) else {k: target for k, _ in groups}
+    `target` in every group (a float, or a {k: target} dict; with max_loss,
+    the plain search's held-out recall at each group's cap minus max_loss).
+    The model's ef_cap is the largest group's."""
+    from .eval import recall as _recall
+    vq0, vg0 = train_q[:max(1, int(train_q.shape[0] * val_frac))], train_gt[:max(1, int(train_q.shape[0] * val_frac))]
+    if max_loss is not None:
+        vqd0 = torch.from_numpy(np.ascontiguousarray(vq0)).cuda()
+        tgt = {}
+        for k, cap in groups:
+            ids, _ = ix.search(vqd0, k, cap)
+            kk = min(k, 10)
+            tgt[k] = _recall(ids.cpu().numpy()[:, :kk], vg0, kk) - max_loss
+    else:
+        tgt = target if isinstance(target, dict) else {k: target for k, _ in groups}
     nv = max(1, int(train_q.shape[0] * val_frac))
     tq, tg = train_q[nv:], train_gt[nv:]
     vq, vg = train_q[:nv], train_gt[:nv]

@@ -86,12 +86,21 @@ def stop_setup(tmp_path_factory, lib_built):
 
 
 def test_learned_stop_gain_over_fixed_ef(stop_setup):
-    """What the trained stop (fused in the search kernel, fixed-ef fallback
-    cap) gains over the plain search: on the recall-vs-expansions frontier,
-    some stop threshold reaches a higher recall than the plain search's
-    curve (interpolated between beam sizes) at the same mean expansions.
-    The gain measured here is small (a few percent of expansions); the test
-    prints both frontiers."""
+    """What the trained stop gains over the plain fixed-ef search, held to
+    bars that sampling noise does not pass.  The plain search reaches
+    recall@10 0.95 at ef_t; the stop runs with twice that beam as its cap.
+    Its threshold is chosen on held-out training queries (the most
+    aggressive one whose recall still reaches 0.95), then the 1,000 test
+    queries run once:
+      * the stop ends searches early: it expands at least 5 % fewer vertices
+        than the plain search at the same cap, and its recall is at least
+        0.95 minus 2 standard errors of recall@10 over these queries;
+      * the perfect stop at the cap (each query stopped at the first
+        expansion holding its true top-10, from traces) saves at least as
+        much and is printed beside it, with the plain frontier's expansions
+        at the stop's recall.
+    Whether that saving buys QPS at equal recall is measured by the
+    benchmark (the network's evaluations cost time), not asserted here."""
     from paper_2411_12229_gb300 import learned_stop as L
     ix, q, g, tq, tg = stop_setup
     qd = torch.from_numpy(q).cuda()
@@ -99,16 +108,20 @@ def test_learned_stop_gain_over_fixed_ef(stop_setup):
     plain = np.array([L.evaluate(ix, qd, g, 10, ef, reps=1) for ef in efs])  # recall, qps, hops
     ef_t = next((ef for ef, r in zip(efs, plain) if r[0] >= 0.95), 128)
     cap = 2 * ef_t
-    f, y, _ = L.collect(ix, tq, tg, 10, cap, 2)
-    model = L.StopModel(L.train(f, y, steps=2000), 0.0, 2, cap, {})
-    gains = []
-    for thr in (3.0, 2.0, 1.5, 1.0, 0.5):
-        r, qps, hops = L.evaluate(ix, qd, g, 10, cap, model, logit=thr, reps=1)
-        plain_r = float(np.interp(hops, plain[:, 2], plain[:, 0]))
-        gains.append(r - plain_r)
-        print(f"stop cap={cap} logit={thr}: recall {r:.4f} hops {hops:.2f} | plain at those hops {plain_r:.4f}")
-    print("plain:", [(ef, round(p[0], 4), round(p[2], 2)) for ef, p in zip(efs, plain)])
-    assert max(gains) > 0.0
+    model = L.fit(ix, tq, tg, 10, cap, 0.95, every=4, steps=2000, label="final")
+    ids, _, st = ix.search(qd, 10, cap, stats=True, stop_mlp=model.params, stop_logit=model.logit, stop_every=4)
+    per_q = L.hits_of(ids.cpu().numpy(), g, 10) / 10.0
+    r_stop, hops_stop = float(per_q.mean()), float(st[:, 0].float().mean())
+    se = float(per_q.std(ddof=1) / np.sqrt(len(per_q)))
+    r_cap, _, hops_cap = L.evaluate(ix, qd, g, 10, cap, reps=1)
+    bound = L.perfect_stop(ix, q, g, 10, cap)
+    plain_hops_at_r = float(np.interp(r_stop, plain[:, 0], plain[:, 2]))
+    print(f"cap {cap}: plain recall {r_cap:.4f} hops {hops_cap:.2f}; stop (logit {model.logit}) recall "
+          f"{r_stop:.4f} (se {se:.4f}) hops {hops_stop:.2f}; perfect stop hops {bound['perfect_stop_hops']}; "
+          f"plain frontier at the stop's recall: {plain_hops_at_r:.2f} hops")
+    assert hops_stop <= 0.95 * hops_cap
+    assert r_stop >= 0.95 - 2 * se
+    assert bound["perfect_stop_hops"] <= hops_cap
 
 
 def test_training_resumes_from_a_checkpoint(lib_built, tmp_path):
