@@ -957,7 +957,7 @@ def main():
                 "frac": round(achieved / peak, 4), "peak_source": peak_src,
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
                 "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": round(kern_mean, 4),
-                "kernel": "sqg::search_kernel",
+                "kernel": search_kernel_name(ix, k, ef_sel, args),
                 "job_frac": round(alg_bytes / (job_ms / 1e3) / 1e9 / peak, 4)}
 
     cpu = None
@@ -1006,6 +1006,14 @@ def main():
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def search_kernel_name(ix, k: int, ef: int, args) -> str:
+    """The search kernel a default search of this shape runs (the compact
+    kernel's range: d <= 256, degree 32, k <= 32, ef <= 64)."""
+    if ix.d <= 256 and ix.degree == 32 and k <= 32 and ef <= 64:
+        return "sqg::search_compact_kernel"
+    return "sqg::search_kernel"
 
 
 def pick_rec(sweep, ef):

@@ -355,14 +355,13 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                 bB |= 1ull;
                 beam_a[lane + 32] = bB;
             }
-            hash_insert_warp(H, hbits, p, lane);
+            hash_insert_warp(H, hbits, p, lane);  // its closing __syncwarp also orders the marks above
             ++hops;
             if (Hg && H == Hs && (uint32_t)hops >= (1u << hbits) / 2) {
                 hash_migrate<32>(Hs, hbits, Hg, a.hash_bits, tm);
                 H = Hg;
                 hbits = a.hash_bits;
             }
-            __syncwarp();
         }
         // ---- line 8: the k nearest expanded vertices by exact distance
         const bool ok = !(status & SQG_STATUS_TIMEOUT);
