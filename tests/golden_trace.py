@@ -55,6 +55,9 @@ def load() -> dict:
             t["result"][int(f[1])] = f[2:]
         elif f[0] == "stop":
             t["stop"].setdefault(int(f[1]), []).append((int(f[2]), Fraction(f[3]), Fraction(f[4])))
+        elif f[0] == "feat":
+            t.setdefault("feat", {}).setdefault((int(f[1]), int(f[2])), []).append(
+                (int(f[3]), [Fraction(v) for v in f[4:20]]))
     return t
 
 

@@ -128,6 +128,28 @@ def test_golden_beam_trace_on_gpu(oracle_mod, lib_built, tmp_path, ef, team):
         assert f[6] == pytest.approx(float(f6), rel=1e-6)
 
 
+@pytest.mark.parametrize("ef,k", [(1, 1), (2, 2), (3, 3), (4, 4), (4, 2)])
+def test_golden_beam_trace_all_stop_features_on_gpu(lib_built, tmp_path, ef, k):
+    """The fused stop's 16 features, traced by the GPU search at every
+    evaluation point of the hand-worked trace, against the values derived
+    by hand (tests/golden/beam_trace_d32.txt)."""
+    import golden_trace as G
+
+    from paper_2411_12229_gb300.api import Index
+    t = G.load()
+    p = tmp_path / "trace.sqg"
+    G.write_index(t, p)
+    ix = Index(p, 0)
+    q = torch.from_numpy(t["q"].astype(np.float32)[None, :]).cuda()
+    *_, feats, _, cnt = ix.search_trace(q, k, ef, None, 16, stop_every=1)
+    feats = _np(feats)[0][:int(_np(cnt)[0])]
+    want = t["feat"][(ef, k)]
+    assert len(feats) == len(want)
+    for f, (h, vals) in zip(feats, want):
+        for i, v in enumerate(vals):
+            assert f[i] == pytest.approx(float(v), rel=1e-5, abs=1e-7), f"ef {ef} k {k} hop {h} f{i}"
+
+
 def _check_search(ix, O, q, k, ef, **kw):
     qd = torch.from_numpy(q).cuda()
     ids, dists, st = ix.search(qd, k, ef, stats=True, **{a: b for a, b in kw.items() if a != "mlp_np"})

@@ -283,6 +283,11 @@ def test_golden_beam_trace_below_the_full_beam(oracle_mod, lib_built, tmp_path, 
     np.testing.assert_array_equal(dists, [32.0 * D[n] for n in t["result"][ef]])
     *_, path = O.search(t["q"].astype(np.float32), ef, ef, path_cap=16)
     assert [nm[i] for i in path] == t["path"][ef]
+    # on a tree no vertex is estimated twice, so the w/o ME ablation runs
+    # the same trace
+    ids2, dists2, hops2, _, path2 = O.search(t["q"].astype(np.float32), ef, ef, multi_estimate=False, path_cap=16)
+    assert [nm[i] for i in path2] == t["path"][ef] and hops2 == hops
+    np.testing.assert_array_equal(ids2, ids)
 
 
 @pytest.mark.parametrize("ef", [1, 2, 3, 4])
@@ -303,6 +308,27 @@ def test_golden_beam_trace_stop_features(oracle_mod, lib_built, tmp_path, ef):
         assert f[0] == pytest.approx(h / ef, rel=1e-6)  # f0 = hops / ef names the evaluation point
         assert f[5] == pytest.approx(float(f5), rel=1e-5, abs=1e-7)
         assert f[6] == pytest.approx(float(f6), rel=1e-6)
+
+
+@pytest.mark.parametrize("ef,k", [(1, 1), (2, 2), (3, 3), (4, 4), (4, 2)])
+def test_golden_beam_trace_all_stop_features(oracle_mod, lib_built, tmp_path, ef, k):
+    """All 16 learned-stop features (this project's definitions) at every
+    evaluation point of the hand-worked trace, against the values derived
+    by hand in tests/golden/beam_trace_d32.txt -- including k < ef, where
+    one expansion does not enter the result (since-last-improvement 1,
+    f14 = 0)."""
+    import golden_trace as G
+    t = G.load()
+    p = tmp_path / "trace.sqg"
+    G.write_index(t, p)
+    O = oracle_mod.Index(p)
+    _, _, _, _, feats, _ = O.search(t["q"].astype(np.float32), k, ef, trace_cap=16, stop_every=1)
+    want = t["feat"][(ef, k)]
+    assert len(feats) == len(want)
+    for f, (h, vals) in zip(feats, want):
+        assert f[0] == pytest.approx(h / ef, rel=1e-6)
+        for i, v in enumerate(vals):
+            assert f[i] == pytest.approx(float(v), rel=1e-5, abs=1e-7), f"ef {ef} k {k} hop {h} f{i}"
 
 
 # --------------------------------------------------------------- search (Algorithm 1)
