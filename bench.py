@@ -414,11 +414,12 @@ def isolated_steps(graph, steps: int, flush) -> float:
     return float(np.mean(ms))
 
 
-def launches_per_step(d: int, metric: str = "l2") -> int:
-    """Library kernels per search call: plan, rotation (tensor cores plus the
+def launches_per_step(d: int, metric: str = "l2", ragged: bool = False) -> int:
+    """Library kernels per search call: rotation (tensor cores plus the
     exact quantization from d = 512 up, else one CUDA-core kernel), search;
-    on a cosine index also the query normalization."""
-    return (4 if d >= 512 else 3) + (metric == "cosine")
+    the planning kernel when k differs per query (ragged outputs); on a
+    cosine index also the query normalization."""
+    return (3 if d >= 512 else 2) + ragged + (metric == "cosine")
 
 
 def bench_mixed(args, w, ix, pool_d, pool, gt_ids, rank, world, dist, local, nb):
@@ -510,7 +511,8 @@ def bench_mixed(args, w, ix, pool_d, pool, gt_ids, rank, world, dist, local, nb)
                          "note": "job step time (plan + rotation + search), not the search kernel alone"},
             "learned_stop": stop,
             "autotune": sorted(tune["table"], key=lambda r: r["ms"])[:6], "clocks": clk,
-            "hops_mean": round(float(hops.mean()), 2), "gpu_launches": launches_per_step(w.d, args.metric) * args.steps}
+            "hops_mean": round(float(hops.mean()), 2),
+            "gpu_launches": launches_per_step(w.d, args.metric, ragged=True) * args.steps}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

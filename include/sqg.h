@@ -122,6 +122,11 @@ typedef struct {
                                 learned stop, no trace, prefetch 1), else the general one;
                                 1 = always the general kernel; 2 = the compact kernel or
                                 SQG_ERR_UNSUPPORTED.  Both return identical results. */
+    int32_t uniform_k;       /* 0 (default): k[] may differ per query, outputs ragged at the
+                                exclusive prefix sum of k[] (a planning kernel computes it);
+                                > 0: every k[i] is this value, query i's outputs start at
+                                i * uniform_k and no planning kernel runs; a query whose k[i]
+                                differs gets padding and SQG_STATUS_BAD_PARAM */
 } sqg_search_params;
 
 typedef struct {
@@ -208,7 +213,10 @@ int sqg_search(const sqg_index *ix, const float *queries, int nq, const int32_t 
  * workspace (NULL = stream-ordered allocation; else 256-byte aligned) of ws_bytes >=
  * sqg_workspace_size(), and optional per-query stats (nq entries, device).
  * With params->max_k and max_ef given and a workspace, the call is
- * asynchronous and allocates nothing.  SQG_ERR_CAPACITY when the workspace
+ * asynchronous and allocates nothing.  With params->uniform_k > 0 the
+ * outputs are nq rows of uniform_k slots (the caller sizes them nq *
+ * uniform_k), max_k must be 0 or uniform_k (else SQG_ERR_INVALID_ARG), and
+ * no planning kernel runs.  SQG_ERR_CAPACITY when the workspace
  * is too small or the bounds need more shared memory than a block has. */
 int sqg_search_ex(const sqg_index *ix, const float *queries, int nq, const int32_t *k, const int32_t *ef,
                   uint32_t *out_ids, float *out_dists, const sqg_search_params *params, void *workspace,

@@ -38,7 +38,7 @@ class SearchParams(C.Structure):
                 ("stop_logit", C.c_float), ("stop_every", C.c_int32), ("team", C.c_int32),
                 ("warps_per_block", C.c_int32), ("timing_events", C.c_void_p * 2),
                 ("visited_smem_log2", C.c_int32), ("prefetch", C.c_int32), ("lean", C.c_int32),
-                ("rotation", C.c_int32), ("kernel", C.c_int32)]
+                ("rotation", C.c_int32), ("kernel", C.c_int32), ("uniform_k", C.c_int32)]
 
 
 class Info(C.Structure):

@@ -76,7 +76,7 @@ class Index:
                max_ef: int = 0, stop_mlp: torch.Tensor | None = None, stop_logit: float = 0.0,
                stop_every: int = 1, warps_per_block: int = 0, timing_events=None, visited_smem_log2: int = 0,
                prefetch: int = 0, lean: int = 0, rotation: int = 0, team: int = 0,
-               kernel: int = 0) -> B.SearchParams:
+               kernel: int = 0, uniform_k: int = 0) -> B.SearchParams:
         p = B.SearchParams()
         p.eps0 = float(eps0)
         p.multi_estimate = 1 if multi_estimate else 0
@@ -95,6 +95,7 @@ class Index:
         p.rotation = int(rotation)
         p.team = int(team)
         p.kernel = int(kernel)
+        p.uniform_k = int(uniform_k)
         if timing_events is not None:  # torch.cuda.Event pair, already recorded once
             p.timing_events[0] = timing_events[0].cuda_event
             p.timing_events[1] = timing_events[1].cuda_event
@@ -105,8 +106,9 @@ class Index:
         """Search a batch (Algorithm 1 per query).
 
         queries: (nq, d) float32 CUDA tensor.  k, ef: ints or (nq,) tensors.
-        Returns (ids int32, dists float32): shape (nq, k) when k is one int,
-        else flat ragged arrays (query i at offset sum_{j<i} k[j]).  Padding
+        Returns (ids int32, dists float32): shape (nq, k) when k is one int
+        (or (nq, uniform_k) with that keyword), else flat ragged arrays
+        (query i at offset sum_{j<i} k[j]).  Padding
         is id -1 with distance +inf.  With stats=True also returns an
         (nq, 2) int32 tensor of (hops, status bits)."""
         queries = self.fit_queries(queries)
@@ -116,8 +118,9 @@ class Index:
         nq, dev = queries.shape[0], queries.device
         kt, et = _i32(k, nq, dev), _i32(ef, nq, dev)
         uniform = not isinstance(k, torch.Tensor) and np.ndim(k) == 0
+        uk = int(kw.get("uniform_k", 0))  # rows of uk slots whatever k[] holds
         if out is None:  # (with `out` given nothing here waits on the device)
-            total = int(k) * nq if uniform else int(kt.clamp(0, B.MAX_K).sum().item())
+            total = uk * nq if uk else int(k) * nq if uniform else int(kt.clamp(0, B.MAX_K).sum().item())
             ids = torch.empty(total, dtype=torch.int32, device=dev)
             dists = torch.empty(total, dtype=torch.float32, device=dev)
         else:
@@ -126,6 +129,8 @@ class Index:
         p = self.params(**kw)
         if uniform and p.max_k == 0:
             p.max_k = int(k)
+        if uniform and "uniform_k" not in kw and p.max_k == int(k):
+            p.uniform_k = int(k)  # one k for the batch: outputs at i * k, no planning kernel
         if not isinstance(ef, torch.Tensor) and np.ndim(ef) == 0 and p.max_ef == 0:
             p.max_ef = int(ef)
         ws_ptr, ws_bytes = (workspace.data_ptr(), workspace.numel() * workspace.element_size()) \
@@ -134,8 +139,8 @@ class Index:
                                    dists.data_ptr(), C.byref(p), ws_ptr, ws_bytes,
                                    st.data_ptr() if st is not None else None, _stream_ptr(stream))
         B.check(rc, "sqg_search_ex")
-        if uniform:
-            ids, dists = ids.view(nq, int(k)), dists.view(nq, int(k))
+        if uniform or uk:
+            ids, dists = ids.view(nq, uk or int(k)), dists.view(nq, uk or int(k))
         return (ids, dists, st) if stats else (ids, dists)
 
     def search_plain(self, queries: torch.Tensor, k: torch.Tensor, ef: torch.Tensor, out_ids: torch.Tensor,
@@ -312,7 +317,7 @@ class HostPipeline:
         with torch.cuda.stream(sl.stream):
             sl.qd.copy_(qh, non_blocking=True)
             self.ix.search(sl.qd, sl.kt, sl.et, out=(sl.ids, sl.dists), workspace=sl.ws, stream=sl.stream,
-                           max_k=self.k, max_ef=self.ef, **self.kw)
+                           max_k=self.k, max_ef=self.ef, uniform_k=self.k, **self.kw)
             sl.ih.copy_(sl.ids.view(self.nq, self.k), non_blocking=True)
             sl.dh.copy_(sl.dists.view(self.nq, self.k), non_blocking=True)
             sl.event.record(sl.stream)

@@ -114,6 +114,8 @@ class GraphSearch:
         self.dists = torch.empty(total, dtype=torch.float32, device=dev)
         self.ws = torch.empty(ix.workspace_size(nq, max_k, max_ef, **kw), dtype=torch.uint8, device=dev)
         self.kw = dict(max_k=max_k, max_ef=max_ef, **kw)
+        if np.ndim(k) == 0 and "uniform_k" not in kw and max_k == int(k):
+            self.kw["uniform_k"] = int(k)  # one k: outputs at i * k, no planning kernel
         s = torch.cuda.Stream(device=dev)
         s.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(s):  # warm-up outside the capture

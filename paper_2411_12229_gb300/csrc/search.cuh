@@ -53,6 +53,7 @@ struct SearchArgs {
     uint32_t *status_word;   // OR of all status bits
     unsigned int *queue_head;
     int max_k, max_ef, hop_cap;
+    int uniform_k;        // > 0: every k[i] equals it, outputs at i * uniform_k (offsets unused)
     uint32_t hash_bits;   // full visited table: 2^hash_bits >= 2 * hop cap + 1
     uint32_t shash_bits;  // shared-memory table (<= hash_bits)
     uint32_t *ghash;      // per-warp full tables in global memory when shash_bits < hash_bits
@@ -527,10 +528,10 @@ __global__ void __launch_bounds__(128, (LEAN ? 8 : (CH <= 2 ? 5 : 3))) search_ke
         if (qi >= a.nq) break;
 
         const int k = a.k[qi], ef = a.ef[qi];
-        const long long off = a.offsets[qi];
+        const long long off = a.uniform_k ? (long long)qi * a.uniform_k : a.offsets[qi];
         uint32_t status = 0;
-        if (!(k >= 1 && k <= a.max_k && ef >= k && ef <= a.max_ef)) {
-            const int kk = k < 0 ? 0 : (k > SQG_MAX_K ? SQG_MAX_K : k);
+        if (!(k >= 1 && k <= a.max_k && ef >= k && ef <= a.max_ef && (!a.uniform_k || k == a.uniform_k))) {
+            const int kk = a.uniform_k ? a.uniform_k : (k < 0 ? 0 : (k > SQG_MAX_K ? SQG_MAX_K : k));
             for (int t = tl; t < kk; t += T) {
                 a.out_ids[off + t] = SQG_NO_ID;
                 a.out_dists[off + t] = __int_as_float(0x7f800000);

@@ -12,7 +12,10 @@
 //     unsigned compare and a duplicate (key, id) is one xor;
 //   * the beam (at most 64 entries) sits in shared memory, sorted, and
 //     lane l also keeps entries l and l + 32 in registers for the select
-//     and the visited marks;
+//     and the visited marks; all 64 slots are always written, the empty
+//     entry (greater than every entry, visited bit set) from the beam's
+//     length on, so the binary search, the select and the marks need no
+//     bound on the length;
 //   * the admitted candidates' beam positions come from a branch-free
 //     binary search; the merged beam is gathered into the other of two
 //     beam buffers, each output slot finding its source from a 64-bit mask
@@ -143,10 +146,10 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
         qi = __shfl_sync(kFull, qi, 0);
         if (qi >= a.nq) break;
         const int k = a.k[qi], ef = a.ef[qi];
-        const long long off = a.offsets[qi];
+        const long long off = a.uniform_k ? (long long)qi * a.uniform_k : a.offsets[qi];
         uint32_t status = 0;
-        if (!(k >= 1 && k <= a.max_k && ef >= k && ef <= a.max_ef)) {
-            const int kk = k < 0 ? 0 : (k > SQG_MAX_K ? SQG_MAX_K : k);
+        if (!(k >= 1 && k <= a.max_k && ef >= k && ef <= a.max_ef && (!a.uniform_k || k == a.uniform_k))) {
+            const int kk = a.uniform_k ? a.uniform_k : (k < 0 ? 0 : (k > SQG_MAX_K ? SQG_MAX_K : k));
             for (int t = lane; t < kk; t += 32) {
                 a.out_ids[off + t] = SQG_NO_ID;
                 a.out_dists[off + t] = __int_as_float(0x7f800000);
@@ -188,6 +191,9 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
         int m = 1;
         uint64_t bA = lane == 0 ? pack_entry(0u, a.entry) | 1ull : kNone;  // beam[lane]
         uint64_t bB = kNone;                                                 // beam[lane + 32]
+        // both beam buffers hold all 64 slots, kNone from m on: no bound on m below
+        beam_a[lane] = bA;
+        beam_a[lane + 32] = kNone;
         uint64_t res = kNone;                                                // result[lane], lane < k
         uint64_t rworst = kNone;  // result[k - 1]: the entry a new result must beat
         uint64_t bworst = kNone;  // beam[ef - 1] once the beam holds ef entries (the early cut)
@@ -195,7 +201,6 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
         __syncwarp();
         hash_insert_warp(H, hbits, p, lane);
         if (lane == 0) {
-            beam_a[0] = bA;
             fence_proxy_async();
             bulk_fetch(buf, a.blocks + (size_t)p * a.block_bytes, a.block_bytes, &bar[0]);
         }
@@ -262,8 +267,8 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                 nxt = ((uint64_t)chi << 32) | clo;
             }
             {
-                const uint32_t ua = __ballot_sync(kFull, lane < m && !(bA & 1ull));
-                const uint32_t ub = __ballot_sync(kFull, lane + 32 < m && !(bB & 1ull));
+                const uint32_t ua = __ballot_sync(kFull, !(bA & 1ull));  // kNone reads as visited
+                const uint32_t ub = __ballot_sync(kFull, !(bB & 1ull));
                 if (ua | ub) {
                     const int sl = ua ? __ffs(ua) - 1 : 32 + __ffs(ub) - 1;
                     const uint64_t o = shfl64(sl < 32 ? bA : bB, sl & 31);
@@ -291,9 +296,9 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
 #pragma unroll
                 for (int step = 32; step >= 1; step >>= 1) {
                     const int t = pos + step;
-                    if (t <= m && B[t - 1] < cand) pos = t;
+                    if (B[t - 1] < cand) pos = t;  // kNone from m on: pos <= m
                 }
-                if (adm && pos < m && ((B[pos] ^ cand) >> 1) == 0) adm = false;
+                if (adm && ((B[pos] ^ cand) >> 1) == 0) adm = false;
                 am = __ballot_sync(kFull, adm);
             }
             if (am) {
@@ -319,21 +324,15 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                 {
                     const int o = lane;
                     const int c = __popc(lo & ((1u << lane) - 1u));
-                    uint64_t v = kNone;
-                    if (o < m2) {
-                        v = ((lo >> lane) & 1u) ? stage[c] : B[o - c];
-                        Bn[o] = v;
-                    }
+                    const uint64_t v = o < m2 ? (((lo >> lane) & 1u) ? stage[c] : B[o - c]) : kNone;
+                    Bn[o] = v;
                     bA = v;
                 }
                 {
                     const int o = lane + 32;
                     const int c = __popc(lo) + __popc(hi & ((1u << lane) - 1u));
-                    uint64_t v = kNone;
-                    if (o < m2) {
-                        v = ((hi >> lane) & 1u) ? stage[c] : B[o - c];
-                        Bn[o] = v;
-                    }
+                    const uint64_t v = o < m2 ? (((hi >> lane) & 1u) ? stage[c] : B[o - c]) : kNone;
+                    Bn[o] = v;
                     bB = v;
                 }
                 beam_b = beam_a;
@@ -347,11 +346,11 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
             // ---- line 3: the next vertex is visited; every copy of it in the
             // beam is marked (reading R5: the copies keep their slots)
             p = pn;
-            if (lane < m && entry_id(bA) == p && !(bA & 1ull)) {
+            if (entry_id(bA) == p && !(bA & 1ull)) {
                 bA |= 1ull;
                 beam_a[lane] = bA;
             }
-            if (lane + 32 < m && entry_id(bB) == p && !(bB & 1ull)) {
+            if (entry_id(bB) == p && !(bB & 1ull)) {
                 bB |= 1ull;
                 beam_a[lane + 32] = bB;
             }

@@ -525,7 +525,7 @@ int check_params(const sqg_search_params &p) {
         !std::isfinite(p.eps0) ||
         (p.visited_smem_log2 != 0 && (p.visited_smem_log2 < 5 || p.visited_smem_log2 > 12)) ||
         p.prefetch < 0 || p.prefetch > 2 || p.lean < 0 || p.lean > 2 || p.rotation < 0 || p.rotation > 2 ||
-        p.kernel < 0 || p.kernel > 2 ||
+        p.kernel < 0 || p.kernel > 2 || p.uniform_k < 0 || p.uniform_k > SQG_MAX_K ||
         (p.stop_mlp && p.stop_every < 1))
         return SQG_ERR_INVALID_ARG;
     return SQG_OK;
@@ -742,6 +742,10 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     DeviceGuard g(ix->device);
     cudaError_t e;
     int max_k = p.max_k, max_ef = p.max_ef;
+    if (p.uniform_k > 0) {
+        if (max_k == 0) max_k = p.uniform_k;
+        if (max_k != p.uniform_k) return SQG_ERR_INVALID_ARG;
+    }
     if (max_k == 0 || max_ef == 0) {  // read the batch's bounds (one stream sync)
         void *tmp = nullptr;
         if (cudaMallocAsync(&tmp, 8 * (size_t)nq + 256, stream) != cudaSuccess) return SQG_ERR_OOM;
@@ -815,9 +819,11 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     a.gt_k = gt_k;
     a.path = path;
     a.path_cap = path_cap;
+    a.uniform_k = p.uniform_k;
 
-    plan_kernel<<<1, kPlanThreads, 0, stream>>>(k, ef, nq, const_cast<long long *>(a.offsets),
-                                                reinterpret_cast<int *>(ws + pl.ws_maxes));
+    if (p.uniform_k == 0)  // ragged outputs: the offsets are the prefix sum of k[]
+        plan_kernel<<<1, kPlanThreads, 0, stream>>>(k, ef, nq, const_cast<long long *>(a.offsets),
+                                                    reinterpret_cast<int *>(ws + pl.ws_maxes));
     if (use_tc_rotation(ix, p)) {  // tensor cores, then the exact quantization
         a.qplanes = reinterpret_cast<uint32_t *>(ws + pl.ws_planes);
         a.qscal = reinterpret_cast<float4 *>(ws + pl.ws_scal);

@@ -222,6 +222,40 @@ def test_mixed_k_ef_ragged_batch(gpu_tiny, oracle_mod):
         assert st[i, 0] == oh
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_uniform_k_outputs_without_planning(gpu_tiny, oracle_mod, kernel):
+    """uniform_k: outputs at i * k with no prefix sum.  Identical to the
+    ragged launch of the same k[]; a query whose k differs is padding with
+    SQG_STATUS_BAD_PARAM and the rest are untouched; max_k other than
+    uniform_k is rejected."""
+    from paper_2411_12229_gb300 import _binding as B
+    ix, p, x, q = gpu_tiny
+    O = oracle_mod.Index(p)
+    nq, k, ef = q.shape[0], 10, 40
+    qd = torch.from_numpy(q).cuda()
+    kt = torch.full((nq,), k, dtype=torch.int32)
+    et = torch.full((nq,), ef, dtype=torch.int32)
+    r_ids, r_d, r_st = ix.search(qd, kt, et, stats=True, kernel=kernel, max_k=k, max_ef=ef)
+    u_ids, u_d, u_st = ix.search(qd, kt, et, stats=True, kernel=kernel, max_k=k, max_ef=ef, uniform_k=k)
+    assert torch.equal(r_ids, u_ids.flatten()) and torch.equal(r_d, u_d.flatten()) and torch.equal(r_st, u_st)
+    s_ids, s_d = ix.search(qd, k, ef, kernel=kernel)  # scalar k takes this path by itself
+    assert torch.equal(s_ids, u_ids) and torch.equal(s_d, u_d)
+    kt[3], kt[7] = 5, 11
+    m_ids, m_d, m_st = ix.search(qd, kt, et, stats=True, kernel=kernel, max_k=k, max_ef=ef, uniform_k=k)
+    m_ids, m_d, m_st = _np(m_ids).view(np.uint32).reshape(nq, k), _np(m_d).reshape(nq, k), _np(m_st)
+    for i in range(nq):
+        if i in (3, 7):
+            assert m_st[i, 1] == B.STATUS_BAD_PARAM and np.all(m_ids[i] == 0xFFFFFFFF) and np.all(np.isinf(m_d[i]))
+        else:
+            oi, od, oh, _ = O.search(q[i], k, ef)
+            np.testing.assert_array_equal(m_ids[i], oi)
+            np.testing.assert_array_equal(m_d[i], od)
+            assert m_st[i, 0] == oh
+    assert ix.status() & B.STATUS_BAD_PARAM
+    with pytest.raises(RuntimeError):
+        ix.search(qd, kt, et, max_k=12, max_ef=ef, uniform_k=k)
+
+
 def test_plain_sqg_search_entry_point(gpu_tiny, oracle_mod):
     """sqg_search (device k[], ef[], bounds read on the device)."""
     ix, p, x, q = gpu_tiny
