@@ -8,11 +8,12 @@ beam size ef of the sweep whose recall@10 on the first batch reaches 0.95.
 The job draws a pool of `--batches` distinct batches (one seeded query
 stream) and step s searches batch s mod batches, so no two steps in flight
 share a query.  Inputs are resident in HBM before the timed region.  Each
-step is one CUDA graph (plan, rotation, search); the job replays K steps
-back to back alternating over two streams (the index is larger than L2, so
-no flush between them), so one step's tail overlaps the next step's start.
+step is one CUDA graph (rotation and search; plus the planning kernel
+when k differs per query); the job replays K steps back to back
+alternating over three streams (the index is larger than L2, so no flush
+between them), so one step's tail overlaps the next steps' start.
 `step_isolated_ms` is one step alone, L2 flushed before it.  The sweep's
-`qps_at_recall` is timed the same way (distinct batches, two streams).
+`qps_at_recall` is timed the same way (distinct batches, three streams).
 `e2e` repeats the job through the public host-to-host API (pinned H2D of
 each step's queries, D2H of ids and distances inside the timed region).
 
@@ -293,7 +294,7 @@ def aggregate_replicas(local_ms, nq: int, world: int, dist, device):
 def learned_stop_comparison(args, w, ix, pool_d, gt_ids, sweep, ef_sel, device, nq, nb):
     """The learned stop (not in the paper) against the plain fixed-ef search
     at equal recall, both timed like the headline (captured batched
-    searches over distinct batches on two streams).
+    searches over distinct batches on three streams).
 
     The network is trained on the GPU from traces of separate training
     queries with the label the stop is built for: the result already holds
@@ -353,13 +354,13 @@ def learned_stop_comparison(args, w, ix, pool_d, gt_ids, sweep, ef_sel, device, 
                        "final": "the result holds what the search at the cap ends with"},
             "train_queries": int(ntrain), "variants": models,
             "perfect_stop_bound": bound, "evaluation_overhead_by_period": overhead,
-            "timing": f"graph-captured searches of {nbe} distinct batches of {nq}, 2 streams (as the headline)",
+            "timing": f"graph-captured searches of {nbe} distinct batches of {nq}, {JOB_STREAMS} streams (as the headline)",
             "points": rows, "at_recall": at, "qps_ratio_vs_plain": at["0.95"]["qps_ratio"]}
 
 
 def stop_point(ix, pool_d, gt_ids, nq, nbe, ef, kw):
     """Recall over nbe batches, mean expansions and job QPS of one search
-    configuration (graph per batch, two streams)."""
+    configuration (graph per batch, three streams)."""
     from paper_2411_12229_gb300 import eval as E
     from paper_2411_12229_gb300.autotune import GraphSearch
     gs, hops = [], []
@@ -378,7 +379,21 @@ def stop_point(ix, pool_d, gt_ids, nq, nbe, ef, kw):
     return {"recall": round(rec, 4), "qps": round(nq / (ms / 1e3)), "hops": round(float(np.mean(hops)), 2)}
 
 
-def time_job(graphs, steps: int, nstreams: int = 2) -> float:
+L2_BYTES = 129_000_000  # GB300 L2, 129 MB
+
+
+def l2_note(ix, flushed: str) -> str:
+    """How the job's steps stand to the L2: the index larger than it (no
+    flush needed between steps) or resident in it (the small workload)."""
+    size = ix.n * ix.block_bytes
+    where = "larger than L2" if size > L2_BYTES else "fits in L2 (L2-resident by design)"
+    return f"index ({size / 1e9:.2f} GB) {where}, no flush between job steps; {flushed}"
+
+
+JOB_STREAMS = 3  # 1 / 2 / 3 / 4 streams: 0.310 / 0.223 / 0.214 / 0.214 ms per 1M x 128 step
+
+
+def time_job(graphs, steps: int, nstreams: int = JOB_STREAMS) -> float:
     """Device ms per step of `steps` steps back to back: step s replays
     graphs[s % len(graphs)] (each graph owns its query batch and buffers)
     on stream s % nstreams, bracketed by events on the launching stream."""
@@ -500,11 +515,10 @@ def bench_mixed(args, w, ix, pool_d, pool, gt_ids, rank, world, dist, local, nb)
                        "ef": "U[k, 8k]", "queries_per_step": nq, "knobs": knobs},
             "recall_per_k": rec,
             "k10_fixed_ef_sweep": k10_sweep,
-            "timing": {"l2": f"index ({ix.n * ix.block_bytes / 1e9:.2f} GB) larger than L2, no flush between job "
-                             "steps; isolated steps flushed (512 MiB write)",
+            "timing": {"l2": l2_note(ix, "isolated steps flushed (512 MiB write)"),
                        "batches": f"{nb} distinct batches of {nq} queries, own k and ef draws; step s searches "
                                   f"batch s mod {nb}",
-                       "launch": "one CUDA graph per batch, steps alternating over 2 streams",
+                       "launch": f"one CUDA graph per batch, steps alternating over {JOB_STREAMS} streams",
                        "step_isolated_ms": round(iso_ms, 4)},
             "roofline": {"bound": "hbm", "achieved": round(alg / (ms / 1e3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4), "peak_source": src,
@@ -846,7 +860,7 @@ def main():
 
     # ---- sweep (untimed for the metric): recall on the first batch (where
     # the operating point is chosen) and on the whole pool, hops, and QPS
-    # timed like the job (distinct batches, two streams)
+    # timed like the job (distinct batches, three streams)
     sweep = []
     nb_sweep = min(nb, 4)
     for ef in ([args.ef] if args.ef else w.ef):
@@ -881,9 +895,9 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ef_sel = int(t.item())
 
-    # ---- timed steps: step s replays the graph of batch s mod nb (plan,
-    # rotation, search); two streams, so one step's tail overlaps the next
-    # step's start, and no two steps in flight share a query
+    # ---- timed steps: step s replays the graph of batch s mod nb (rotation,
+    # search); three streams, so one step's tail overlaps the next steps'
+    # start, and no two steps in flight share a query
     graphs = graphs_for(ix, pool_d, nq, k, ef_sel, nb)
     for _ in range(max(3, args.warmup)):
         for g in graphs[:2]:
@@ -923,12 +937,12 @@ def main():
     hops = torch.cat(sts)[:, 0].double().cpu().numpy()
     # ---- end to end through host buffers: every step copies its batch in
     # from pinned host memory and its (ids, dists) back, through the public
-    # pipelined API (two streams: one step's copies overlap another's search);
+    # pipelined API (three streams: one step's copies overlap another's search);
     # host wall clock over all steps, device idle at both ends
     qh = [torch.from_numpy(pool[b * nq:(b + 1) * nq]).pin_memory() for b in range(nb)]
     e2e_ms, rec_e2e = [], None
     if not args.skip_e2e:
-        pipe = ix.host_pipeline(nq, k, ef_sel, depth=2)
+        pipe = ix.host_pipeline(nq, k, ef_sel, depth=JOB_STREAMS)
         for s in range(max(3, args.warmup)):
             pipe.submit(qh[s % nb])
         pipe.drain()
@@ -983,16 +997,15 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": headline_config(w, args, k, ef_sel, nq, world),
         "recall@10": {"first_batch": round(pick_rec(sweep, ef_sel), 4), "job": round(rec_job, 4)},
-        "timing": {"l2": f"index ({ix.n * ix.block_bytes / 1e9:.2f} GB) larger than L2, no flush between job "
-                         "steps; isolated steps and kernel launches flushed (512 MiB write)",
+        "timing": {"l2": l2_note(ix, "isolated steps and kernel launches flushed (512 MiB write)"),
                    "batches": f"{nb} distinct batches of {nq} queries; step s searches batch s mod {nb}",
-                   "launch": "one CUDA graph per batch, steps alternating over 2 streams",
+                   "launch": f"one CUDA graph per batch, steps alternating over {JOB_STREAMS} streams",
                    "step_isolated_ms": round(iso_ms, 4),
                    "step_isolated_qps": round(nq / (iso_ms / 1e3), 1)},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(nq * ix.d * 4),
                 "d2h_bytes_per_step": int(nq * k * 8),
                 "recall@10": round(rec_e2e, 4) if rec_e2e is not None else None,
-                "api": "Index.host_pipeline (2 streams) over the same distinct batches, host wall clock"},
+                "api": f"Index.host_pipeline ({JOB_STREAMS} streams) over the same distinct batches, host wall clock"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "gpu_launches": launches_per_step(w.d, args.metric) * args.steps,

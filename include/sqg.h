@@ -106,8 +106,9 @@ typedef struct {
                                 64 registers (more resident warps, a few spills; the
                                 default), 2 = the 96-register build (and never the
                                 compact kernel).  Compact kernel: 0 = the build for 8
-                                resident blocks of 4 warps per SM (64 registers), 1 = for
-                                10 (48 registers, a few spilled bytes) */
+                                resident blocks of 4 warps per SM (64 registers) up to
+                                ef 64 and for 7 (72) up to ef 128; 1 = one block more
+                                (56 / 64 registers) */
     int32_t rotation;        /* q' = P^-1 q: 1 = the canonical fp32 order (see
                                 sqg_prepare_queries) on the CUDA cores; 2 = tcgen05 tensor
                                 cores (3xTF32) followed by an exact pass that recomputes in
@@ -118,7 +119,7 @@ typedef struct {
                                 whose queries always take the fast transform */
     int32_t kernel;          /* 0 (default) = the compact search kernel wherever it applies
                                 (one warp per query, d <= 256, degree 32, every k[i] <= 32
-                                and ef[i] <= 64 by max_k / max_ef, multiple estimates, no
+                                and ef[i] <= 128 by max_k / max_ef, multiple estimates, no
                                 learned stop, no trace, prefetch 1), else the general one;
                                 1 = always the general kernel; 2 = the compact kernel or
                                 SQG_ERR_UNSUPPORTED.  Both return identical results. */

@@ -1005,10 +1005,11 @@ cudaError_t launch_search_team(int ch, int nb, int team, dim3 grid, dim3 block, 
 cudaError_t search_occupancy_team(int ch, int nb, int team, int block, size_t smem, int *blocks_per_sm);
 cudaError_t search_occupancy_nb2(int ch, int block, size_t smem, int *blocks_per_sm);
 // the compact kernel (search_compact.cu): d <= 256 (ch 1, 2), out-degree 32,
-// k <= 32, ef <= 64, whole warps, multiple estimates, no stop network or trace
-// (lean 1: the build for 10 resident blocks of 4 warps per SM, else 8)
-cudaError_t launch_search_compact(int ch, int lean, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+// k <= 32, ef <= 64 (bnb 2) or 128 (bnb 4) beam entries, whole warps,
+// multiple estimates, no stop network or trace (lean 1: the build for one
+// more resident block of 4 warps per SM: 9 / 8, else 8 / 7)
+cudaError_t launch_search_compact(int ch, int bnb, int lean, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                                   const SearchArgs &a);
-cudaError_t search_occupancy_compact(int ch, int lean, int block, size_t smem, int *blocks_per_sm);
+cudaError_t search_occupancy_compact(int ch, int bnb, int lean, int block, size_t smem, int *blocks_per_sm);
 
 }  // namespace sqg

@@ -1,5 +1,5 @@
 // search_compact.cu -- the compact search kernel: one warp per query for
-// d <= 256, out-degree 32, k <= 32 and ef <= 64, with multiple estimates.
+// d <= 256, out-degree 32, k <= 32 and ef <= 128, with multiple estimates.
 //
 // It runs the same Algorithm 1 (Querying, Sec. 3.1.3) with multiple
 // estimated distances and implicit re-ranking (Sec. 3.1.2) as
@@ -10,16 +10,16 @@
 //   * a beam entry is one 64-bit word, (order-preserving key bits << 32) |
 //     (id << 1) | visited, so the (key, id) order of reading R4 is one
 //     unsigned compare and a duplicate (key, id) is one xor;
-//   * the beam (at most 64 entries) sits in shared memory, sorted, and
-//     lane l also keeps entries l and l + 32 in registers for the select
-//     and the visited marks; all 64 slots are always written, the empty
-//     entry (greater than every entry, visited bit set) from the beam's
-//     length on, so the binary search, the select and the marks need no
-//     bound on the length;
+//   * the beam (at most 32 NB entries: NB = 2 for ef <= 64, 4 for ef <=
+//     128) sits in shared memory, sorted, and lane l also keeps entries
+//     l + 32 s (s < NB) in registers for the select and the visited marks;
+//     all 32 NB slots are always written, the empty entry (greater than
+//     every entry, visited bit set) from the beam's length on, so the
+//     binary search, the select and the marks need no bound on the length;
 //   * the admitted candidates' beam positions come from a branch-free
 //     binary search; the merged beam is gathered into the other of two
-//     beam buffers, each output slot finding its source from a 64-bit mask
-//     of the candidates' final positions (no shifting loop);
+//     beam buffers, each output slot finding its source from a 32 NB-bit
+//     mask of the candidates' final positions (no shifting loop);
 //   * the k <= 32 results live in registers, lane i holding the i-th.
 //
 // The next vertex -- the smaller of the best admitted candidate and the
@@ -115,9 +115,21 @@ __device__ __forceinline__ float key32(const float *fac, const QuerySide &qs, ui
 
 }  // namespace
 
-// MINB: resident blocks of 4 warps per SM the build is made for -- 8 (up to
-// 64 registers) or 9 (56 registers).
-template <int CH, int MINB>
+// Entry s of a lane's NB beam registers, s warp-uniform (an unrolled
+// select: no local-memory array).
+template <int NB>
+__device__ __forceinline__ uint64_t pick(const uint64_t (&b)[NB], int s) {
+    uint64_t v = b[0];
+#pragma unroll
+    for (int t = 1; t < NB; ++t)
+        if (s == t) v = b[t];
+    return v;
+}
+
+// NB: beam slots per lane (2: ef <= 64, 4: ef <= 128).  MINB: resident
+// blocks of 4 warps per SM the build is made for (NB 2: 8 for up to 64
+// registers or 9 for 56; NB 4: 7 for up to 72 or 8 for 64).
+template <int CH, int NB, int MINB>
 __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -125,8 +137,8 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
     unsigned char *ws = smem + (size_t)warp * a.warp_bytes;
     unsigned char *const buf = ws + a.o_buf0;
     uint64_t *const bar = reinterpret_cast<uint64_t *>(ws + a.o_bar);
-    uint64_t *beam_a = reinterpret_cast<uint64_t *>(ws + a.o_beam);  // two buffers of 64 entries
-    uint64_t *beam_b = beam_a + 64;
+    uint64_t *beam_a = reinterpret_cast<uint64_t *>(ws + a.o_beam);  // two buffers of 32 NB entries
+    uint64_t *beam_b = beam_a + 32 * NB;
     uint64_t *const stage = reinterpret_cast<uint64_t *>(ws + a.o_spos);  // this step's candidates by rank
     uint32_t *const planes = reinterpret_cast<uint32_t *>(ws + a.o_planes);
     const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -189,12 +201,13 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
         // ---- Algorithm 1, line 1: the beam holds the entry, which is expanded
         // first (its key, its exact distance, is set at that expansion)
         int m = 1;
-        uint64_t bA = lane == 0 ? pack_entry(0u, a.entry) | 1ull : kNone;  // beam[lane]
-        uint64_t bB = kNone;                                                 // beam[lane + 32]
-        // both beam buffers hold all 64 slots, kNone from m on: no bound on m below
-        beam_a[lane] = bA;
-        beam_a[lane + 32] = kNone;
-        uint64_t res = kNone;                                                // result[lane], lane < k
+        uint64_t b[NB];  // b[s] = beam[lane + 32 s]
+#pragma unroll
+        for (int s = 0; s < NB; ++s) {
+            b[s] = s == 0 && lane == 0 ? pack_entry(0u, a.entry) | 1ull : kNone;
+            beam_a[lane + 32 * s] = b[s];  // all 32 NB slots, kNone from m on: no bound on m below
+        }
+        uint64_t res = kNone;  // result[lane], lane < k
         uint64_t rworst = kNone;  // result[k - 1]: the entry a new result must beat
         uint64_t bworst = kNone;  // beam[ef - 1] once the beam holds ef entries (the early cut)
         uint32_t p = a.entry;
@@ -225,11 +238,11 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
             const float dist_c = exact_reduce<32>(dacc, tm);
             if (hops == 1) {  // reading R8: the entry's key is its exact distance
                 if (lane == 0) {
-                    bA = pack_entry(key_bits(dist_c), p) | 1ull;
-                    beam_a[0] = bA;
+                    b[0] = pack_entry(key_bits(dist_c), p) | 1ull;
+                    beam_a[0] = b[0];
                 }
                 __syncwarp();
-                if (ef == 1) bworst = shfl64(bA, 0);
+                if (ef == 1) bworst = shfl64(b[0], 0);
             }
             {  // result top-k in registers: (dist bits << 32) | id, dist >= 0
                 const uint64_t r = ((uint64_t)__float_as_uint(dist_c) << 32) | p;
@@ -267,11 +280,19 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                 nxt = ((uint64_t)chi << 32) | clo;
             }
             {
-                const uint32_t ua = __ballot_sync(kFull, !(bA & 1ull));  // kNone reads as visited
-                const uint32_t ub = __ballot_sync(kFull, !(bB & 1ull));
-                if (ua | ub) {
-                    const int sl = ua ? __ffs(ua) - 1 : 32 + __ffs(ub) - 1;
-                    const uint64_t o = shfl64(sl < 32 ? bA : bB, sl & 31);
+                uint32_t u[NB];
+#pragma unroll
+                for (int s = 0; s < NB; ++s) u[s] = __ballot_sync(kFull, !(b[s] & 1ull));  // kNone: visited
+                int su = NB;  // the first slot row with an unvisited entry
+                uint32_t uu = 0;
+#pragma unroll
+                for (int s = NB - 1; s >= 0; --s)
+                    if (u[s]) {
+                        su = s;
+                        uu = u[s];
+                    }
+                if (su < NB) {
+                    const uint64_t o = shfl64(pick<NB>(b, su), __ffs(uu) - 1);
                     nxt = o < nxt ? o : nxt;
                 }
             }
@@ -294,7 +315,7 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                 // beam position (lower bound) by a branch-free binary search;
                 // an identical (key, id) already in the beam is dropped
 #pragma unroll
-                for (int step = 32; step >= 1; step >>= 1) {
+                for (int step = 16 * NB; step >= 1; step >>= 1) {
                     const int t = pos + step;
                     if (B[t - 1] < cand) pos = t;  // kNone from m on: pos <= m
                 }
@@ -314,46 +335,42 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                 __syncwarp();
                 const int fp = pos + rank;  // final position in the merged beam
                 if (adm) stage[rank] = cand;
-                const uint32_t lo = __reduce_or_sync(kFull, adm && fp < 32 ? 1u << fp : 0u);
-                const uint32_t hi = __reduce_or_sync(kFull, adm && fp >= 32 && fp < 64 ? 1u << (fp - 32) : 0u);
+                uint32_t mk[NB];  // bit l of mk[s]: a candidate lands in slot 32 s + l
+#pragma unroll
+                for (int s = 0; s < NB; ++s)
+                    mk[s] = __reduce_or_sync(kFull, adm && (fp >> 5) == s ? 1u << (fp & 31) : 0u);
                 const int m2 = min(ef, m + nadm);
                 uint64_t *Bn = beam_b;
                 __syncwarp();
                 // output slot o: a candidate if bit o of the mask is set (the one
                 // of rank = candidates placed before o), else old entry o - that count
-                {
-                    const int o = lane;
-                    const int c = __popc(lo & ((1u << lane) - 1u));
-                    const uint64_t v = o < m2 ? (((lo >> lane) & 1u) ? stage[c] : B[o - c]) : kNone;
+                int cbase = 0;
+#pragma unroll
+                for (int s = 0; s < NB; ++s) {
+                    const int o = lane + 32 * s;
+                    const int c = cbase + __popc(mk[s] & ((1u << lane) - 1u));
+                    const uint64_t v = o < m2 ? (((mk[s] >> lane) & 1u) ? stage[c] : B[o - c]) : kNone;
                     Bn[o] = v;
-                    bA = v;
-                }
-                {
-                    const int o = lane + 32;
-                    const int c = __popc(lo) + __popc(hi & ((1u << lane) - 1u));
-                    const uint64_t v = o < m2 ? (((hi >> lane) & 1u) ? stage[c] : B[o - c]) : kNone;
-                    Bn[o] = v;
-                    bB = v;
+                    b[s] = v;
+                    cbase += __popc(mk[s]);
                 }
                 beam_b = beam_a;
                 beam_a = Bn;
                 m = m2;
                 // (a visited mark set below does not matter to the early cut: no
                 // candidate shares an id with a visited entry)
-                bworst = m == ef ? shfl64((ef - 1) < 32 ? bA : bB, (ef - 1) & 31) : kNone;
+                bworst = m == ef ? shfl64(pick<NB>(b, (ef - 1) >> 5), (ef - 1) & 31) : kNone;
             }
 
             // ---- line 3: the next vertex is visited; every copy of it in the
             // beam is marked (reading R5: the copies keep their slots)
             p = pn;
-            if (entry_id(bA) == p && !(bA & 1ull)) {
-                bA |= 1ull;
-                beam_a[lane] = bA;
-            }
-            if (entry_id(bB) == p && !(bB & 1ull)) {
-                bB |= 1ull;
-                beam_a[lane + 32] = bB;
-            }
+#pragma unroll
+            for (int s = 0; s < NB; ++s)
+                if (entry_id(b[s]) == p && !(b[s] & 1ull)) {
+                    b[s] |= 1ull;
+                    beam_a[lane + 32 * s] = b[s];
+                }
             hash_insert_warp(H, hbits, p, lane);  // its closing __syncwarp also orders the marks above
             ++hops;
             if (Hg && H == Hs && (uint32_t)hops >= (1u << hbits) / 2) {
@@ -377,42 +394,48 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
     }
 }
 
-template <int CH, int MINB>
+template <int CH, int NB, int MINB>
 static cudaError_t compact_launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const SearchArgs &a) {
-    auto fn = search_compact_kernel<CH, MINB>;
+    auto fn = search_compact_kernel<CH, NB, MINB>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int CH, int MINB>
+template <int CH, int NB, int MINB>
 static cudaError_t compact_occ_one(int block, size_t smem, int *nb) {
-    auto fn = search_compact_kernel<CH, MINB>;
+    auto fn = search_compact_kernel<CH, NB, MINB>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, fn, block, smem);
 }
 
-#define SQG_COMPACT_SWITCH(CALL)                      \
-    switch (ch * 10 + (lean == 1 ? 1 : 0)) {          \
-        case 10: return CALL(1, 8);                   \
-        case 11: return CALL(1, 9);                   \
-        case 20: return CALL(2, 8);                   \
-        case 21: return CALL(2, 9);                   \
-        default: return cudaErrorInvalidValue;        \
+// (d chunks CH, beam slots per lane NB, lean build) -> the instantiation
+#define SQG_COMPACT_SWITCH(CALL)                                  \
+    switch (ch * 100 + bnb * 10 + (lean == 1 ? 1 : 0)) {          \
+        case 120: return CALL(1, 2, 8);                           \
+        case 121: return CALL(1, 2, 9);                           \
+        case 220: return CALL(2, 2, 8);                           \
+        case 221: return CALL(2, 2, 9);                           \
+        case 140: return CALL(1, 4, 7);                           \
+        case 141: return CALL(1, 4, 8);                           \
+        case 240: return CALL(2, 4, 7);                           \
+        case 241: return CALL(2, 4, 8);                           \
+        default: return cudaErrorInvalidValue;                    \
     }
 
-// lean 1: the build for 9 resident blocks (56 registers); else 8 (64)
-cudaError_t launch_search_compact(int ch, int lean, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+// bnb: beam slots per lane (2 or 4); lean 1: the build for one more
+// resident block per SM (fewer registers)
+cudaError_t launch_search_compact(int ch, int bnb, int lean, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                                   const SearchArgs &a) {
-#define CALL(C, M) compact_launch_one<C, M>(grid, block, smem, s, a)
+#define CALL(C, N, M) compact_launch_one<C, N, M>(grid, block, smem, s, a)
     SQG_COMPACT_SWITCH(CALL)
 #undef CALL
 }
 
-cudaError_t search_occupancy_compact(int ch, int lean, int block, size_t smem, int *blocks_per_sm) {
-#define CALL(C, M) compact_occ_one<C, M>(block, smem, blocks_per_sm)
+cudaError_t search_occupancy_compact(int ch, int bnb, int lean, int block, size_t smem, int *blocks_per_sm) {
+#define CALL(C, N, M) compact_occ_one<C, N, M>(block, smem, blocks_per_sm)
     SQG_COMPACT_SWITCH(CALL)
 #undef CALL
 }

@@ -2,7 +2,7 @@
 gathered merge, results in registers) against the oracle.
 
 It serves every search it applies to (one warp per query, d <= 256,
-degree 32, k <= 32, ef <= 64, multiple estimates, no learned stop, no
+degree 32, k <= 32, ef <= 128, multiple estimates, no learned stop, no
 trace); here it is forced (kernel = 2) and held to the same bar as the
 general kernel: ids, distances, hop counts and status bits identical to
 the oracle, on the plain and the ragged batch, with the error-bound key,
@@ -50,46 +50,51 @@ def check(ix, O, q, k, ef, *, oracle_kw=None, **kw):
 
 @pytest.mark.parametrize("lean", [0, 1])
 @pytest.mark.parametrize("k,ef", [(1, 1), (1, 8), (10, 10), (10, 16), (10, 33), (10, 40), (10, 64), (32, 32),
-                                  (32, 64), (5, 63)])
+                                  (32, 64), (5, 63), (10, 65), (10, 80), (1, 96), (10, 112), (32, 128), (7, 127)])
 def test_compact_parity(gpu_tiny, oracle_mod, k, ef, lean):
     """Both register builds of the compact kernel (lean 0: 8 resident
-    blocks per SM, 1: 10)."""
+    blocks per SM with 2 beam slots per lane, 7 with 4; lean 1: one more),
+    for beams of up to 64 (2 slots per lane) and 128 entries (4)."""
     ix, p, x, q = gpu_tiny
     check(ix, oracle_mod.Index(p), q, k, ef, lean=lean)
 
 
+@pytest.mark.parametrize("ef", [48, 100])
 @pytest.mark.parametrize("eps0", [0.5, 1.9])
-def test_compact_error_bound_key(gpu_tiny, oracle_mod, eps0):
+def test_compact_error_bound_key(gpu_tiny, oracle_mod, eps0, ef):
     ix, p, x, q = gpu_tiny
-    check(ix, oracle_mod.Index(p), q, 10, 48, eps0=eps0)
+    check(ix, oracle_mod.Index(p), q, 10, ef, eps0=eps0)
 
 
+@pytest.mark.parametrize("ef", [64, 128])
 @pytest.mark.parametrize("cap", [1, 2, 7, 30])
-def test_compact_hop_cap(gpu_tiny, oracle_mod, cap):
+def test_compact_hop_cap(gpu_tiny, oracle_mod, cap, ef):
     ix, p, x, q = gpu_tiny
-    _, _, st = check(ix, oracle_mod.Index(p), q, 5, 64, hop_cap=cap)
+    _, _, st = check(ix, oracle_mod.Index(p), q, 5, ef, hop_cap=cap)
     assert np.all(st[:, 0] <= cap) and np.all(st[:, 1] == 1)
 
 
+@pytest.mark.parametrize("ef", [64, 128])
 @pytest.mark.parametrize("smem_log2", [5, 6])
-def test_compact_visited_set_migration(gpu_tiny, oracle_mod, smem_log2):
+def test_compact_visited_set_migration(gpu_tiny, oracle_mod, smem_log2, ef):
     ix, p, x, q = gpu_tiny
-    _, _, st = check(ix, oracle_mod.Index(p), q, 10, 64, visited_smem_log2=smem_log2)
+    _, _, st = check(ix, oracle_mod.Index(p), q, 10, ef, visited_smem_log2=smem_log2)
     assert st[:, 0].min() > (1 << smem_log2) // 2
 
 
-def test_compact_ragged_batch(gpu_tiny, oracle_mod):
-    """Per-query k in {1, 10, 32} and ef in [k, 64] in one launch."""
+@pytest.mark.parametrize("max_ef", [64, 128])
+def test_compact_ragged_batch(gpu_tiny, oracle_mod, max_ef):
+    """Per-query k in {1, 10, 32} and ef in [k, max_ef] in one launch."""
     ix, p, x, q = gpu_tiny
     O = oracle_mod.Index(p)
-    rng = np.random.default_rng(17)
+    rng = np.random.default_rng(17 + max_ef)
     nq = q.shape[0]
     k = rng.choice([1, 10, 32], size=nq).astype(np.int32)
-    ef = np.array([rng.integers(kk, 65) for kk in k], dtype=np.int32)
+    ef = np.array([rng.integers(kk, max_ef + 1) for kk in k], dtype=np.int32)
     qd = torch.from_numpy(q).cuda()
     kt, et = torch.from_numpy(k), torch.from_numpy(ef)
-    ids, dists, st = ix.search(qd, kt, et, stats=True, kernel=2, max_k=32, max_ef=64)
-    g = ix.search(qd, kt, et, stats=True, kernel=1, max_k=32, max_ef=64)
+    ids, dists, st = ix.search(qd, kt, et, stats=True, kernel=2, max_k=32, max_ef=max_ef)
+    g = ix.search(qd, kt, et, stats=True, kernel=1, max_k=32, max_ef=max_ef)
     assert torch.equal(ids, g[0]) and torch.equal(dists, g[1]) and torch.equal(st, g[2])
     ids, dists, st = _np(ids).view(np.uint32), _np(dists), _np(st)
     off = np.concatenate([[0], np.cumsum(k)])
@@ -165,10 +170,11 @@ def gpu_ties_compact(tmp_path_factory, lib_built):
 def test_compact_ties_and_duplicates(gpu_ties_compact, oracle_mod):
     ix, p, x, q = gpu_ties_compact
     O = oracle_mod.Index(p)
-    for ef in (16, 40, 64):
+    for ef in (16, 40, 64, 100, 128):
         _, dists, _ = check(ix, O, q, 10, ef)
     assert np.all(dists[:8, 0] == 0.0)
     check(ix, O, q, 10, 64, eps0=1.9)
+    check(ix, O, q, 10, 128, eps0=1.9)
 
 
 def test_compact_irregular_and_cosine_indexes(oracle_mod, lib_built, tmp_path):
@@ -192,7 +198,7 @@ def test_compact_applies_only_where_it_is_defined(gpu_tiny, tiny_index_r64):
     from paper_2411_12229_gb300.api import Index
     ix, p, x, q = gpu_tiny
     qd = torch.from_numpy(q).cuda()
-    for kw in (dict(k=33, ef=64), dict(k=10, ef=65), dict(k=10, ef=40, multi_estimate=False),
+    for kw in (dict(k=33, ef=64), dict(k=10, ef=129), dict(k=10, ef=40, multi_estimate=False),
                dict(k=10, ef=40, team=16), dict(k=10, ef=40, prefetch=2)):
         k, ef = kw.pop("k"), kw.pop("ef")
         with pytest.raises(SqgError):

@@ -25,10 +25,11 @@ def full_index(lib_built):
     return Index(idx, 0), idx, synth.queries(w)
 
 
-@pytest.mark.parametrize("ef,kernel", [(40, 0), (40, 1), (48, 0), (128, 0)])
+@pytest.mark.parametrize("ef,kernel", [(40, 0), (40, 1), (48, 0), (80, 0), (128, 0), (128, 1)])
 def test_full_size_sampled_parity(full_index, oracle_mod, ef, kernel):
-    """ef 40 is the benchmark's operating point (recall@10 0.95); kernel 0
-    takes the compact kernel there, 1 the general one."""
+    """ef 40 is the benchmark's operating point (recall@10 0.95), 80 the
+    one for 0.99; kernel 0 takes the compact kernel (2 beam slots per lane
+    up to ef 64, 4 up to 128), 1 the general one."""
     ix, path, q = full_index
     ids, dists, st = ix.search(torch.from_numpy(q).cuda(), 10, ef, stats=True, kernel=kernel)
     ids, dists, st = ids.cpu().numpy().view(np.uint32), dists.cpu().numpy(), st.cpu().numpy()
