@@ -10,8 +10,9 @@ stream) and step s searches batch s mod batches, so no two steps in flight
 share a query.  Inputs are resident in HBM before the timed region.  Each
 step is one CUDA graph (rotation and search; plus the planning kernel
 when k differs per query); the job replays K steps back to back
-alternating over three streams (the index is larger than L2, so no flush
-between them), so one step's tail overlaps the next steps' start.
+alternating over three streams (more for batches of a few hundred
+queries; the index is larger than L2, so no flush between them), so one
+step's tail overlaps the next steps' start.
 `step_isolated_ms` is one step alone, L2 flushed before it.  The sweep's
 `qps_at_recall` is timed the same way (distinct batches, three streams).
 `e2e` repeats the job through the public host-to-host API (pinned H2D of
@@ -354,7 +355,7 @@ def learned_stop_comparison(args, w, ix, pool_d, gt_ids, sweep, ef_sel, device, 
                        "final": "the result holds what the search at the cap ends with"},
             "train_queries": int(ntrain), "variants": models,
             "perfect_stop_bound": bound, "evaluation_overhead_by_period": overhead,
-            "timing": f"graph-captured searches of {nbe} distinct batches of {nq}, {JOB_STREAMS} streams (as the headline)",
+            "timing": f"graph-captured searches of {nbe} distinct batches of {nq}, {job_streams(nq)} streams (as the headline)",
             "points": rows, "at_recall": at, "qps_ratio_vs_plain": at["0.95"]["qps_ratio"]}
 
 
@@ -390,14 +391,20 @@ def l2_note(ix, flushed: str) -> str:
     return f"index ({size / 1e9:.2f} GB) {where}, no flush between job steps; {flushed}"
 
 
-JOB_STREAMS = 3  # 1 / 2 / 3 / 4 streams: 0.310 / 0.223 / 0.214 / 0.214 ms per 1M x 128 step
+def job_streams(nq: int) -> int:
+    """Streams the job's steps alternate over: 3 for batches of thousands of
+    queries (1 / 2 / 3 / 4 streams: 0.310 / 0.223 / 0.214 / 0.214 ms per
+    1M x 128 step of 10,000), more for small batches, whose single launch
+    occupies a fraction of the GPU's resident warps (16 for 200 queries)."""
+    return min(16, max(3, 8000 // max(nq, 1)))
 
 
-def time_job(graphs, steps: int, nstreams: int = JOB_STREAMS) -> float:
+def time_job(graphs, steps: int, nstreams: int | None = None) -> float:
     """Device ms per step of `steps` steps back to back: step s replays
     graphs[s % len(graphs)] (each graph owns its query batch and buffers)
     on stream s % nstreams, bracketed by events on the launching stream."""
     import torch
+    nstreams = nstreams or job_streams(graphs[0].q.shape[0])
     cur = torch.cuda.current_stream()
     streams = [torch.cuda.Stream() for _ in range(min(nstreams, len(graphs)))]
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -518,7 +525,7 @@ def bench_mixed(args, w, ix, pool_d, pool, gt_ids, rank, world, dist, local, nb)
             "timing": {"l2": l2_note(ix, "isolated steps flushed (512 MiB write)"),
                        "batches": f"{nb} distinct batches of {nq} queries, own k and ef draws; step s searches "
                                   f"batch s mod {nb}",
-                       "launch": f"one CUDA graph per batch, steps alternating over {JOB_STREAMS} streams",
+                       "launch": f"one CUDA graph per batch, steps alternating over {job_streams(nq)} streams",
                        "step_isolated_ms": round(iso_ms, 4)},
             "roofline": {"bound": "hbm", "achieved": round(alg / (ms / 1e3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4), "peak_source": src,
@@ -942,7 +949,7 @@ def main():
     qh = [torch.from_numpy(pool[b * nq:(b + 1) * nq]).pin_memory() for b in range(nb)]
     e2e_ms, rec_e2e = [], None
     if not args.skip_e2e:
-        pipe = ix.host_pipeline(nq, k, ef_sel, depth=JOB_STREAMS)
+        pipe = ix.host_pipeline(nq, k, ef_sel, depth=job_streams(nq))
         for s in range(max(3, args.warmup)):
             pipe.submit(qh[s % nb])
         pipe.drain()
@@ -999,13 +1006,13 @@ def main():
         "recall@10": {"first_batch": round(pick_rec(sweep, ef_sel), 4), "job": round(rec_job, 4)},
         "timing": {"l2": l2_note(ix, "isolated steps and kernel launches flushed (512 MiB write)"),
                    "batches": f"{nb} distinct batches of {nq} queries; step s searches batch s mod {nb}",
-                   "launch": f"one CUDA graph per batch, steps alternating over {JOB_STREAMS} streams",
+                   "launch": f"one CUDA graph per batch, steps alternating over {job_streams(nq)} streams",
                    "step_isolated_ms": round(iso_ms, 4),
                    "step_isolated_qps": round(nq / (iso_ms / 1e3), 1)},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(nq * ix.d * 4),
                 "d2h_bytes_per_step": int(nq * k * 8),
                 "recall@10": round(rec_e2e, 4) if rec_e2e is not None else None,
-                "api": f"Index.host_pipeline ({JOB_STREAMS} streams) over the same distinct batches, host wall clock"},
+                "api": f"Index.host_pipeline ({job_streams(nq)} streams) over the same distinct batches, host wall clock"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "gpu_launches": launches_per_step(w.d, args.metric) * args.steps,
