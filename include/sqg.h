@@ -118,7 +118,7 @@ typedef struct {
                                 else 1.  Ignored for a fast-JLT index (format version 2),
                                 whose queries always take the fast transform */
     int32_t kernel;          /* 0 (default) = the compact search kernel wherever it applies
-                                (one warp per query, d <= 256, degree 32, every k[i] <= 32
+                                (one warp per query, d <= 1024, degree 32 or 64, every k[i] <= 32
                                 and ef[i] <= 128 by max_k / max_ef, multiple estimates, no
                                 learned stop, no trace, prefetch 1), else the general one;
                                 1 = always the general kernel; 2 = the compact kernel or

@@ -1,441 +1,41 @@
-// search_compact.cu -- the compact search kernel: one warp per query for
-// d <= 256, out-degree 32, k <= 32 and ef <= 128, with multiple estimates.
-//
-// It runs the same Algorithm 1 (Querying, Sec. 3.1.3) with multiple
-// estimated distances and implicit re-ranking (Sec. 3.1.2) as
-// search_kernel, takes every decision in the same precision and order, and
-// returns the same ids, distances, hop counts and status bits; what differs
-// is the bookkeeping, cut to a few warp instructions per step:
-//
-//   * a beam entry is one 64-bit word, (order-preserving key bits << 32) |
-//     (id << 1) | visited, so the (key, id) order of reading R4 is one
-//     unsigned compare and a duplicate (key, id) is one xor;
-//   * the beam (at most 32 NB entries: NB = 2 for ef <= 64, 4 for ef <=
-//     128) sits in shared memory, sorted, and lane l also keeps entries
-//     l + 32 s (s < NB) in registers for the select and the visited marks;
-//     all 32 NB slots are always written, the empty entry (greater than
-//     every entry, visited bit set) from the beam's length on, so the
-//     binary search, the select and the marks need no bound on the length;
-//   * the admitted candidates' beam positions come from a branch-free
-//     binary search; the merged beam is gathered into the other of two
-//     beam buffers, each output slot finding its source from a 32 NB-bit
-//     mask of the candidates' final positions (no shifting loop);
-//   * the k <= 32 results live in registers, lane i holding the i-th.
-//
-// The next vertex -- the smaller of the best admitted candidate and the
-// first unvisited beam entry -- is known as soon as the estimates are, so
-// its block copy (1-D bulk copy into shared memory, Sec. 3.1.4's
-// prefetch) is issued before the merge, which then runs while the copy is
-// in flight, together with the marks of the vertex's copies in the beam
-// and its visited-set insert (one warp-wide probe of 32 slots).
-#include "search.cuh"
+// search_compact.cu -- the compact search kernel (search_compact.cuh) for
+// d <= 256 (CH = 1, 2), and the dispatch to the instantiations for larger d
+// (search_compact_wide.cu).
+#include "search_compact.cuh"
 
 namespace sqg {
 
-namespace {
-
-constexpr uint64_t kNone = ~0ull;  // an empty beam or result slot (greater than every entry)
-
-// Order-preserving map of a float key (never NaN) to uint32: a < b as floats
-// iff map(a) < map(b) as unsigned integers; -0 and +0 map to one value, as
-// they compare equal as floats.
-__device__ __forceinline__ uint32_t key_bits(float f) {
-    const uint32_t b = __float_as_uint(__fadd_rn(f, 0.0f));  // -0 + 0 = +0
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ uint64_t pack_entry(uint32_t kb, uint32_t id) {
-    return ((uint64_t)kb << 32) | ((uint64_t)id << 1);
-}
-__device__ __forceinline__ uint32_t entry_id(uint64_t e) { return (uint32_t)(e >> 1) & kIdMask; }
-__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
-    const uint32_t lo = __shfl_sync(kFull, (uint32_t)v, src), hi = __shfl_sync(kFull, (uint32_t)(v >> 32), src);
-    return ((uint64_t)hi << 32) | lo;
-}
-__device__ __forceinline__ uint64_t shfl64_up(uint64_t v, int d) {
-    const uint32_t lo = __shfl_up_sync(kFull, (uint32_t)v, d), hi = __shfl_up_sync(kFull, (uint32_t)(v >> 32), d);
-    return ((uint64_t)hi << 32) | lo;
-}
-
-// Insert an id that is not in the table (an unvisited vertex) with the
-// whole warp: lane l reads probe slot s + l, and the first empty slot of the
-// window is the one a slot-by-slot linear probe would take.
-__device__ __forceinline__ void hash_insert_warp(uint32_t *H, uint32_t bits, uint32_t id, int lane) {
-    const uint32_t mask = (1u << bits) - 1u;
-    uint32_t s = hslot(id, bits);
-    for (;;) {
-        const uint32_t slot = (s + lane) & mask;
-        const uint32_t emp = __ballot_sync(kFull, H[slot] == kEmpty);
-        if (emp) {
-            if (lane == __ffs(emp) - 1) H[slot] = id;
-            __syncwarp();
-            return;
-        }
-        s += 32;
-    }
-}
-
-// S = sum_i b_i qbar_i of neighbour j (Sec. 3.1.1): AND + popc of its code
-// words against the 4 bit-planes, out-degree 32 (word w of neighbour j at
-// w * 32 + j); nw <= 4 * CH words.
-template <int CH>
-__device__ __forceinline__ int estimate_S32(const unsigned char *codes_b, const uint32_t *planes, uint32_t nw,
-                                            int j) {
-    const uint32_t *codes = reinterpret_cast<const uint32_t *>(codes_b) + j;
-    const uint4 *pl = reinterpret_cast<const uint4 *>(planes);
-    int s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-#pragma unroll
-    for (uint32_t w = 0; w < 4 * CH; ++w) {
-        if (w < nw) {
-            const uint32_t c = codes[w * 32];
-            const uint4 p = pl[w];
-            s0 += __popc(c & p.x);
-            s1 += __popc(c & p.y);
-            s2 += __popc(c & p.z);
-            s3 += __popc(c & p.w);
-        }
-    }
-    return s0 + 2 * s1 + 4 * s2 + 8 * s3;
-}
-
-// The key of neighbour j from its S (the estimator of Sec. 3.1.1 and the
-// bound-shifted key of reading R7), out-degree 32: the same operations in
-// the same order as estimate_from_S.
-__device__ __forceinline__ float key32(const float *fac, const QuerySide &qs, uint32_t d, int j, int S,
-                                       float dist_c, float sqrt_dc, float eps0) {
-    const float f_add = fac[j], f_rescale = fac[32 + j];
-    const int pc = (int)reinterpret_cast<const uint32_t *>(fac)[96 + j];
-    const float A = (float)(2 * S - qs.sq);
-    const float B = __fmul_rn(qs.vl, (float)(2 * pc - (int)d));
-    const float ip = __fmul_rn(__fmaf_rn(qs.delta, A, B), qs.inv_sqrt_d);
-    const float est = __fmaf_rn(f_rescale, ip, __fadd_rn(f_add, dist_c));
-    if (eps0 == 0.0f) return est;
-    const float bound = __fmul_rn(fac[64 + j], sqrt_dc);
-    return __fsub_rn(est, __fmul_rn(eps0, bound));
-}
-
-}  // namespace
-
-// Entry s of a lane's NB beam registers, s warp-uniform (an unrolled
-// select: no local-memory array).
-template <int NB>
-__device__ __forceinline__ uint64_t pick(const uint64_t (&b)[NB], int s) {
-    uint64_t v = b[0];
-#pragma unroll
-    for (int t = 1; t < NB; ++t)
-        if (s == t) v = b[t];
-    return v;
-}
-
-// NB: beam slots per lane (2: ef <= 64, 4: ef <= 128).  MINB: resident
-// blocks of 4 warps per SM the build is made for (NB 2: 8 for up to 64
-// registers or 9 for 56; NB 4: 7 for up to 72 or 8 for 64).
-template <int CH, int NB, int MINB>
-__global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t d = a.d, nch = d / 4;
-    unsigned char *ws = smem + (size_t)warp * a.warp_bytes;
-    unsigned char *const buf = ws + a.o_buf0;
-    uint64_t *const bar = reinterpret_cast<uint64_t *>(ws + a.o_bar);
-    uint64_t *beam_a = reinterpret_cast<uint64_t *>(ws + a.o_beam);  // two buffers of 32 NB entries
-    uint64_t *beam_b = beam_a + 32 * NB;
-    uint64_t *const stage = reinterpret_cast<uint64_t *>(ws + a.o_spos);  // this step's candidates by rank
-    uint32_t *const planes = reinterpret_cast<uint32_t *>(ws + a.o_planes);
-    const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
-    uint32_t *const Hs = reinterpret_cast<uint32_t *>(ws + a.o_hash);
-    uint32_t *const Hg = a.ghash ? a.ghash + ((size_t)gwarp << a.hash_bits) : nullptr;
-    const Team<32> tm(lane);
-
-    if (lane == 0) mbar_init(&bar[0], 1);
-    fence_mbar_init();
-    __syncwarp();
-    uint32_t phase = 0;
-    bool healthy = true;
-
-    while (healthy) {
-        int qi = 0;
-        if (lane == 0) qi = (int)atomicAdd(a.queue_head, 1u);
-        qi = __shfl_sync(kFull, qi, 0);
-        if (qi >= a.nq) break;
-        const int k = a.k[qi], ef = a.ef[qi];
-        const long long off = a.uniform_k ? (long long)qi * a.uniform_k : a.offsets[qi];
-        uint32_t status = 0;
-        if (!(k >= 1 && k <= a.max_k && ef >= k && ef <= a.max_ef && (!a.uniform_k || k == a.uniform_k))) {
-            const int kk = a.uniform_k ? a.uniform_k : (k < 0 ? 0 : (k > SQG_MAX_K ? SQG_MAX_K : k));
-            for (int t = lane; t < kk; t += 32) {
-                a.out_ids[off + t] = SQG_NO_ID;
-                a.out_dists[off + t] = __int_as_float(0x7f800000);
-            }
-            if (lane == 0) {
-                if (a.stats) a.stats[qi] = sqg_query_stats{0u, SQG_STATUS_BAD_PARAM};
-                atomicOr(a.status_word, SQG_STATUS_BAD_PARAM);
-            }
-            continue;
-        }
-        const int hop_cap = a.hop_cap > 0 ? a.hop_cap : 4 * ef + 64;
-
-        // ---- query setup: raw query in registers, quantized rotated query planes
-        float4 qv[CH];
-        const float4 *q4 = reinterpret_cast<const float4 *>(a.queries + (size_t)qi * d);
-#pragma unroll
-        for (int t = 0; t < CH; ++t) {
-            const uint32_t c = lane + 32 * t;
-            qv[t] = c < nch ? q4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        QuerySide qs;
-        if (a.qplanes) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(a.qplanes + (size_t)qi * 4 * (d / 32));
-            if (lane < (int)(d / 32)) reinterpret_cast<uint4 *>(planes)[lane] = src[lane];
-            const float4 sc = a.qscal[qi];
-            qs.vl = sc.x;
-            qs.delta = sc.y;
-            qs.sq = (int)sc.z;
-            qs.inv_sqrt_d = sc.w;
-        } else {
-            qs = quantize_team<32>(a.qrot + (size_t)qi * d, d, planes, tm);
-        }
-        uint32_t *H = Hs;
-        uint32_t hbits = a.shash_bits;
-        for (uint32_t i = lane; i < (1u << hbits); i += 32) H[i] = kEmpty;
-
-        // ---- Algorithm 1, line 1: the beam holds the entry, which is expanded
-        // first (its key, its exact distance, is set at that expansion)
-        int m = 1;
-        uint64_t b[NB];  // b[s] = beam[lane + 32 s]
-#pragma unroll
-        for (int s = 0; s < NB; ++s) {
-            b[s] = s == 0 && lane == 0 ? pack_entry(0u, a.entry) | 1ull : kNone;
-            beam_a[lane + 32 * s] = b[s];  // all 32 NB slots, kNone from m on: no bound on m below
-        }
-        uint64_t res = kNone;  // result[lane], lane < k
-        uint64_t rworst = kNone;  // result[k - 1]: the entry a new result must beat
-        uint64_t bworst = kNone;  // beam[ef - 1] once the beam holds ef entries (the early cut)
-        uint32_t p = a.entry;
-        __syncwarp();
-        hash_insert_warp(H, hbits, p, lane);
-        if (lane == 0) {
-            fence_proxy_async();
-            bulk_fetch(buf, a.blocks + (size_t)p * a.block_bytes, a.block_bytes, &bar[0]);
-        }
-        int hops = 1;
-
-        for (;;) {
-            if (!mbar_wait_bounded(&bar[0], phase & 1u)) {
-                status |= SQG_STATUS_TIMEOUT;
-                healthy = false;
-                break;
-            }
-            phase ^= 1u;
-            const unsigned char *blk = buf;
-
-            // ---- line 4: exact distance (implicit re-ranking); the neighbours'
-            // integer sums S while the distance's butterfly is in flight
-            float dacc[1];
-            exact_partial<CH, 32>(reinterpret_cast<const float4(&)[1][CH]>(qv),
-                                  reinterpret_cast<const float *>(blk), nch, tm, dacc);
-            const uint32_t cid = reinterpret_cast<const uint32_t *>(blk + a.off_ids)[lane];
-            const int S = estimate_S32<CH>(blk + a.off_codes, planes, d / 32, lane);
-            const float dist_c = exact_reduce<32>(dacc, tm);
-            if (hops == 1) {  // reading R8: the entry's key is its exact distance
-                if (lane == 0) {
-                    b[0] = pack_entry(key_bits(dist_c), p) | 1ull;
-                    beam_a[0] = b[0];
-                }
-                __syncwarp();
-                if (ef == 1) bworst = shfl64(b[0], 0);
-            }
-            {  // result top-k in registers: (dist bits << 32) | id, dist >= 0
-                const uint64_t r = ((uint64_t)__float_as_uint(dist_c) << 32) | p;
-                if (r < rworst) {
-                    const int pos = __popc(__ballot_sync(kFull, lane < k && res < r));
-                    const uint64_t up = shfl64_up(res, 1);
-                    if (lane == pos) res = r;
-                    else if (lane > pos && lane < k) res = up;
-                    rworst = shfl64(res, k - 1);
-                }
-            }
-
-            // ---- line 5: the estimate and key of every neighbour from the same block
-            const float sqrt_dc = a.eps0 == 0.0f ? 0.0f : __fsqrt_rn(dist_c);
-            const float key = key32(reinterpret_cast<const float *>(blk + a.off_factors), qs, d, lane, S, dist_c,
-                                    sqrt_dc, a.eps0);
-            const uint64_t cand = pack_entry(key_bits(key), cid);
-            // ---- line 6: unvisited neighbours enter the beam; an entry the cut to
-            // ef would drop at once is skipped early
-            bool adm = cid != kEmpty && cand < bworst;
-            if (adm) adm = !hash_contains(H, hbits, cid);
-            uint32_t am = __ballot_sync(kFull, adm);
-
-            // ---- lines 2-3 of the next step, taken now (Sec. 3.1.4: the next
-            // block is fetched while this step's merge runs): the next vertex
-            // is the smaller of the best admitted candidate and the first
-            // unvisited beam entry.  A candidate equal in (key, id) to a beam
-            // entry (dropped below as a duplicate) names that entry's vertex,
-            // which is unvisited, so it may stand in for it here.
-            uint64_t nxt = kNone;
-            if (am) {
-                const uint32_t chi = __reduce_min_sync(kFull, adm ? (uint32_t)(cand >> 32) : 0xFFFFFFFFu);
-                const uint32_t clo =
-                    __reduce_min_sync(kFull, adm && (uint32_t)(cand >> 32) == chi ? (uint32_t)cand : 0xFFFFFFFFu);
-                nxt = ((uint64_t)chi << 32) | clo;
-            }
-            {
-                uint32_t u[NB];
-#pragma unroll
-                for (int s = 0; s < NB; ++s) u[s] = __ballot_sync(kFull, !(b[s] & 1ull));  // kNone: visited
-                int su = NB;  // the first slot row with an unvisited entry
-                uint32_t uu = 0;
-#pragma unroll
-                for (int s = NB - 1; s >= 0; --s)
-                    if (u[s]) {
-                        su = s;
-                        uu = u[s];
-                    }
-                if (su < NB) {
-                    const uint64_t o = shfl64(pick<NB>(b, su), __ffs(uu) - 1);
-                    nxt = o < nxt ? o : nxt;
-                }
-            }
-            if (nxt == kNone) break;  // no unvisited entry: the search ends (line 2)
-            if (hops >= hop_cap) {    // reading R6
-                status |= SQG_STATUS_CAPACITY;
-                break;
-            }
-            const uint32_t pn = entry_id(nxt);
-            __syncwarp();  // every lane's reads of the current block are done
-            if (lane == 0) {
-                fence_proxy_async();
-                bulk_fetch(buf, a.blocks + (size_t)pn * a.block_bytes, a.block_bytes, &bar[0]);
-            }
-
-            // ---- line 6: merge the admitted candidates, cut the beam to ef
-            const uint64_t *B = beam_a;
-            int pos = 0;
-            if (am) {
-                // beam position (lower bound) by a branch-free binary search;
-                // an identical (key, id) already in the beam is dropped
-#pragma unroll
-                for (int step = 16 * NB; step >= 1; step >>= 1) {
-                    const int t = pos + step;
-                    if (B[t - 1] < cand) pos = t;  // kNone from m on: pos <= m
-                }
-                if (adm && ((B[pos] ^ cand) >> 1) == 0) adm = false;
-                am = __ballot_sync(kFull, adm);
-            }
-            if (am) {
-                const int nadm = __popc(am);
-                // rank among the admitted candidates (their ids are distinct):
-                // the candidates are compacted into the stage, and every lane
-                // counts the smaller ones with broadcast reads
-                if (adm) stage[__popc(am & ((1u << lane) - 1u))] = cand;
-                __syncwarp();
-                int rank = 0;
-#pragma unroll 4
-                for (int j = 0; j < nadm; ++j) rank += stage[j] < cand ? 1 : 0;
-                __syncwarp();
-                const int fp = pos + rank;  // final position in the merged beam
-                if (adm) stage[rank] = cand;
-                uint32_t mk[NB];  // bit l of mk[s]: a candidate lands in slot 32 s + l
-#pragma unroll
-                for (int s = 0; s < NB; ++s)
-                    mk[s] = __reduce_or_sync(kFull, adm && (fp >> 5) == s ? 1u << (fp & 31) : 0u);
-                const int m2 = min(ef, m + nadm);
-                uint64_t *Bn = beam_b;
-                __syncwarp();
-                // output slot o: a candidate if bit o of the mask is set (the one
-                // of rank = candidates placed before o), else old entry o - that count
-                int cbase = 0;
-#pragma unroll
-                for (int s = 0; s < NB; ++s) {
-                    const int o = lane + 32 * s;
-                    const int c = cbase + __popc(mk[s] & ((1u << lane) - 1u));
-                    const uint64_t v = o < m2 ? (((mk[s] >> lane) & 1u) ? stage[c] : B[o - c]) : kNone;
-                    Bn[o] = v;
-                    b[s] = v;
-                    cbase += __popc(mk[s]);
-                }
-                beam_b = beam_a;
-                beam_a = Bn;
-                m = m2;
-                // (a visited mark set below does not matter to the early cut: no
-                // candidate shares an id with a visited entry)
-                bworst = m == ef ? shfl64(pick<NB>(b, (ef - 1) >> 5), (ef - 1) & 31) : kNone;
-            }
-
-            // ---- line 3: the next vertex is visited; every copy of it in the
-            // beam is marked (reading R5: the copies keep their slots)
-            p = pn;
-#pragma unroll
-            for (int s = 0; s < NB; ++s)
-                if (entry_id(b[s]) == p && !(b[s] & 1ull)) {
-                    b[s] |= 1ull;
-                    beam_a[lane + 32 * s] = b[s];
-                }
-            hash_insert_warp(H, hbits, p, lane);  // its closing __syncwarp also orders the marks above
-            ++hops;
-            if (Hg && H == Hs && (uint32_t)hops >= (1u << hbits) / 2) {
-                hash_migrate<32>(Hs, hbits, Hg, a.hash_bits, tm);
-                H = Hg;
-                hbits = a.hash_bits;
-            }
-        }
-        // ---- line 8: the k nearest expanded vertices by exact distance
-        const bool ok = !(status & SQG_STATUS_TIMEOUT);
-        if (lane < k) {
-            const bool have = ok && res != kNone;
-            a.out_ids[off + lane] = have ? (uint32_t)res : SQG_NO_ID;
-            a.out_dists[off + lane] = have ? __uint_as_float((uint32_t)(res >> 32)) : __int_as_float(0x7f800000);
-        }
-        if (lane == 0) {
-            if (a.stats) a.stats[qi] = sqg_query_stats{(uint32_t)hops, status};
-            if (status) atomicOr(a.status_word, status);
-        }
-        __syncwarp();
-    }
-}
-
-template <int CH, int NB, int MINB>
-static cudaError_t compact_launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const SearchArgs &a) {
-    auto fn = search_compact_kernel<CH, NB, MINB>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    fn<<<grid, block, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <int CH, int NB, int MINB>
-static cudaError_t compact_occ_one(int block, size_t smem, int *nb) {
-    auto fn = search_compact_kernel<CH, NB, MINB>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, fn, block, smem);
-}
-
-// (d chunks CH, beam slots per lane NB, lean build) -> the instantiation
-#define SQG_COMPACT_SWITCH(CALL)                                  \
-    switch (ch * 100 + bnb * 10 + (lean == 1 ? 1 : 0)) {          \
-        case 120: return CALL(1, 2, 8);                           \
-        case 121: return CALL(1, 2, 9);                           \
-        case 220: return CALL(2, 2, 8);                           \
-        case 221: return CALL(2, 2, 9);                           \
-        case 140: return CALL(1, 4, 7);                           \
-        case 141: return CALL(1, 4, 8);                           \
-        case 240: return CALL(2, 4, 7);                           \
-        case 241: return CALL(2, 4, 8);                           \
-        default: return cudaErrorInvalidValue;                    \
+// (d chunks CH, neighbours per lane NR, beam slots per lane NB, lean build)
+// -> the instantiation; lean 1 is the build for one more resident block
+// per SM (out-degree 32 only)
+#define SQG_COMPACT_SWITCH(CALL)                                            \
+    switch (ch * 1000 + nr * 100 + bnb * 10 + (lean == 1 && nr == 1 ? 1 : 0)) { \
+        case 1120: return CALL(1, 1, 2, 8);                                 \
+        case 1121: return CALL(1, 1, 2, 9);                                 \
+        case 2120: return CALL(2, 1, 2, 8);                                 \
+        case 2121: return CALL(2, 1, 2, 9);                                 \
+        case 1140: return CALL(1, 1, 4, 7);                                 \
+        case 1141: return CALL(1, 1, 4, 8);                                 \
+        case 2140: return CALL(2, 1, 4, 7);                                 \
+        case 2141: return CALL(2, 1, 4, 8);                                 \
+        case 1220: return CALL(1, 2, 2, 6);                                 \
+        case 2220: return CALL(2, 2, 2, 6);                                 \
+        case 1240: return CALL(1, 2, 4, 6);                                 \
+        case 2240: return CALL(2, 2, 4, 6);                                 \
+        default: return cudaErrorInvalidValue;                              \
     }
 
-// bnb: beam slots per lane (2 or 4); lean 1: the build for one more
-// resident block per SM (fewer registers)
-cudaError_t launch_search_compact(int ch, int bnb, int lean, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                                  const SearchArgs &a) {
-#define CALL(C, N, M) compact_launch_one<C, N, M>(grid, block, smem, s, a)
+cudaError_t launch_search_compact(int ch, int nr, int bnb, int lean, dim3 grid, dim3 block, size_t smem,
+                                  cudaStream_t s, const SearchArgs &a) {
+    if (ch > 2) return launch_search_compact_wide(ch, nr, bnb, grid, block, smem, s, a);
+#define CALL(C, R, N, M) compact_launch_one<C, R, N, M>(grid, block, smem, s, a)
     SQG_COMPACT_SWITCH(CALL)
 #undef CALL
 }
 
-cudaError_t search_occupancy_compact(int ch, int bnb, int lean, int block, size_t smem, int *blocks_per_sm) {
-#define CALL(C, N, M) compact_occ_one<C, N, M>(block, smem, blocks_per_sm)
+cudaError_t search_occupancy_compact(int ch, int nr, int bnb, int lean, int block, size_t smem, int *blocks_per_sm) {
+    if (ch > 2) return search_occupancy_compact_wide(ch, nr, bnb, block, smem, blocks_per_sm);
+#define CALL(C, R, N, M) compact_occ_one<C, R, N, M>(block, smem, blocks_per_sm)
     SQG_COMPACT_SWITCH(CALL)
 #undef CALL
 }

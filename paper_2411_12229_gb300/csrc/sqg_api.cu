@@ -372,7 +372,7 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     if (pl.ch < 0 || (pl.nb != 1 && pl.nb != 2)) return SQG_ERR_UNSUPPORTED;
     pl.team = p.team == 0 ? 32 : p.team;
     const int V = 32 / pl.team;  // queries per warp
-    pl.compact = p.kernel != 1 && pl.team == 32 && pl.nb == 1 && pl.ch <= 2 && max_k <= 32 && max_ef <= 128 &&
+    pl.compact = p.kernel != 1 && pl.team == 32 && pl.ch <= 8 && max_k <= 32 && max_ef <= 128 &&
                  p.multi_estimate && !p.stop_mlp && !traced && p.prefetch != 2 && p.lean != 2;
     if (p.kernel == 2 && !pl.compact) return SQG_ERR_UNSUPPORTED;
     pl.cbnb = max_ef <= 64 ? 2 : 4;
@@ -405,10 +405,10 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     a.o_planes = (uint32_t)o; o = align_up(o + 16 * (d / 32), 16);
     if (pl.compact) {
         // two beam buffers of 32 cbnb packed entries, the step's candidates
-        // by rank (32 packed entries); the results live in registers
+        // by rank (R packed entries); the results live in registers
         a.o_beam = (uint32_t)o; o += 2 * 32 * (size_t)pl.cbnb * 8;
         a.o_res = (uint32_t)o;
-        a.o_spos = (uint32_t)o; o += 32 * 8;
+        a.o_spos = (uint32_t)o; o += (size_t)R * 8;
     } else {
         a.o_beam = (uint32_t)o; o = align_up(o + 8 * (size_t)max_ef, 16);
         a.o_res = (uint32_t)o; o = align_up(o + 8 * (size_t)max_k, 16);
@@ -430,7 +430,7 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
         const size_t sm = cta + (size_t)w * V * warp_bytes;
         *blocks = 0;
         if (sm > ix->smem_optin) return cudaSuccess;
-        return pl.compact     ? search_occupancy_compact(pl.ch, pl.cbnb, p.lean, w * 32, sm, blocks)
+        return pl.compact     ? search_occupancy_compact(pl.ch, pl.nb, pl.cbnb, p.lean, w * 32, sm, blocks)
              : pl.team < 32 ? search_occupancy_team(pl.ch, pl.nb, pl.team, w * 32, sm, blocks)
              : pl.nb == 1   ? search_occupancy_nb1(pl.ch, w * 32, sm, blocks)
                             : search_occupancy_nb2(pl.ch, w * 32, sm, blocks);
@@ -847,8 +847,8 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     if (e == cudaSuccess && p.timing_events[0])
         e = cudaEventRecord(reinterpret_cast<cudaEvent_t>(p.timing_events[0]), stream);
     if (e == cudaSuccess) {
-        e = pl.compact ? launch_search_compact(pl.ch, pl.cbnb, p.lean, dim3(pl.grid), dim3(pl.warps * 32), pl.smem,
-                                               stream, a)
+        e = pl.compact ? launch_search_compact(pl.ch, pl.nb, pl.cbnb, p.lean, dim3(pl.grid), dim3(pl.warps * 32),
+                                               pl.smem, stream, a)
             : pl.team < 32 ? launch_search_team(pl.ch, pl.nb, pl.team, dim3(pl.grid), dim3(pl.warps * 32), pl.smem,
                                                 stream, a)
             : pl.nb == 1 ? launch_search_nb1(pl.ch, dim3(pl.grid), dim3(pl.warps * 32), pl.smem, stream, a)

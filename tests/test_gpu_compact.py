@@ -1,8 +1,8 @@
-"""The compact search kernel (search_compact.cu: packed 64-bit beam entries,
+"""The compact search kernel (search_compact.cuh: packed 64-bit beam entries,
 gathered merge, results in registers) against the oracle.
 
-It serves every search it applies to (one warp per query, d <= 256,
-degree 32, k <= 32, ef <= 128, multiple estimates, no learned stop, no
+It serves every search it applies to (one warp per query, d <= 1024,
+degree 32 or 64, k <= 32, ef <= 128, multiple estimates, no learned stop, no
 trace); here it is forced (kernel = 2) and held to the same bar as the
 general kernel: ids, distances, hop counts and status bits identical to
 the oracle, on the plain and the ragged batch, with the error-bound key,
@@ -191,11 +191,61 @@ def test_compact_irregular_and_cosine_indexes(oracle_mod, lib_built, tmp_path):
         check(ix, oracle_mod.Index(p), q, 10, 40)
 
 
-def test_compact_applies_only_where_it_is_defined(gpu_tiny, tiny_index_r64):
+@pytest.fixture(scope="module")
+def gpu_tiny64_compact(tiny_index_r64):
+    from paper_2411_12229_gb300.api import Index
+    p, x, q = tiny_index_r64
+    return Index(p, 0), p, x, q
+
+
+@pytest.mark.parametrize("k,ef", [(1, 1), (10, 10), (10, 40), (10, 64), (10, 65), (32, 100), (10, 128)])
+def test_compact_out_degree_64(gpu_tiny64_compact, oracle_mod, k, ef):
+    """Out-degree 64: lane l estimates neighbours l and l + 32 and the
+    step's candidates are staged 64 wide."""
+    ix, p, x, q = gpu_tiny64_compact
+    check(ix, oracle_mod.Index(p), q, k, ef)
+
+
+def test_compact_out_degree_64_variants(gpu_tiny64_compact, oracle_mod):
+    """Error-bound key, a binding hop cap, visited-set moves, a ragged
+    batch, with two neighbours per lane."""
+    ix, p, x, q = gpu_tiny64_compact
+    O = oracle_mod.Index(p)
+    check(ix, O, q, 10, 100, eps0=1.9)
+    _, _, st = check(ix, O, q, 5, 64, hop_cap=7)
+    assert np.all(st[:, 0] <= 7)
+    _, _, st = check(ix, O, q, 10, 128, visited_smem_log2=5)
+    assert st[:, 0].min() > 16
+    rng = np.random.default_rng(29)
+    nq = q.shape[0]
+    k = rng.choice([1, 10, 32], size=nq).astype(np.int32)
+    ef = np.array([rng.integers(kk, 129) for kk in k], dtype=np.int32)
+    qd = torch.from_numpy(q).cuda()
+    kt, et = torch.from_numpy(k), torch.from_numpy(ef)
+    c = ix.search(qd, kt, et, stats=True, kernel=2, max_k=32, max_ef=128)
+    g = ix.search(qd, kt, et, stats=True, kernel=1, max_k=32, max_ef=128)
+    assert all(torch.equal(u, v) for u, v in zip(c, g))
+    ids, off = _np(c[0]).view(np.uint32), np.concatenate([[0], np.cumsum(k)])
+    for i in range(nq):
+        np.testing.assert_array_equal(ids[off[i]:off[i + 1]], O.search(q[i], int(k[i]), int(ef[i]))[0])
+
+
+@pytest.fixture(scope="module")
+def gpu_d1152(tmp_path_factory, lib_built):
+    """d = 1152, past the compact kernel's d <= 1024."""
+    from paper_2411_12229_gb300 import index_builder as ib
+    from paper_2411_12229_gb300.api import Index
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((400, 1152)).astype(np.float32)
+    p = tmp_path_factory.mktemp("d1152") / "d1152.sqg"
+    ib.build_index(p, x, 32)
+    return Index(p, 0), rng.standard_normal((16, 1152)).astype(np.float32)
+
+
+def test_compact_applies_only_where_it_is_defined(gpu_tiny, gpu_d1152):
     """kernel = 2 outside the compact kernel's range is refused; kernel = 0
     falls back to the general kernel there."""
     from paper_2411_12229_gb300._binding import SqgError
-    from paper_2411_12229_gb300.api import Index
     ix, p, x, q = gpu_tiny
     qd = torch.from_numpy(q).cuda()
     for kw in (dict(k=33, ef=64), dict(k=10, ef=129), dict(k=10, ef=40, multi_estimate=False),
@@ -204,6 +254,7 @@ def test_compact_applies_only_where_it_is_defined(gpu_tiny, tiny_index_r64):
         with pytest.raises(SqgError):
             ix.search(qd, k, ef, kernel=2, **kw)
         ix.search(qd, k, ef, kernel=0, **kw)
-    ix64 = Index(tiny_index_r64[0], 0)
+    ixw, qw = gpu_d1152
     with pytest.raises(SqgError):
-        ix64.search(torch.from_numpy(tiny_index_r64[2]).cuda(), 10, 40, kernel=2)
+        ixw.search(torch.from_numpy(qw).cuda(), 10, 40, kernel=2)
+    ixw.search(torch.from_numpy(qw).cuda(), 10, 40, kernel=0)

@@ -177,10 +177,13 @@ def test_search_parity_r32(gpu_tiny, oracle_mod, ef, kernel):
     _check_search(ix, oracle_mod.Index(p), q, 10, ef, kernel=kernel)
 
 
-@pytest.mark.parametrize("ef", [16, 64, 200])
-def test_search_parity_r64(gpu_tiny64, oracle_mod, ef):
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("ef", [16, 64, 100, 200])
+def test_search_parity_r64(gpu_tiny64, oracle_mod, ef, kernel):
+    """Out-degree 64 (two neighbours per lane); kernel 0 takes the compact
+    kernel up to ef 128, 1 the general kernel."""
     ix, p, x, q = gpu_tiny64
-    _check_search(ix, oracle_mod.Index(p), q, 10, ef)
+    _check_search(ix, oracle_mod.Index(p), q, 10, ef, kernel=kernel)
 
 
 def test_search_variants(gpu_tiny, oracle_mod):
@@ -400,6 +403,11 @@ def test_other_shapes_parity(shaped_index, oracle_mod):
         np.testing.assert_array_equal(key[i], r["key"])
     for ef in (10, 40, 100):
         _check_search(ix, O, q, 10, ef)
+    if ix.d <= 1024:  # the compact kernel's range: its output is the general kernel's
+        for ef in (40, 128):
+            c = ix.search(qd, 10, ef, stats=True, kernel=2)
+            g = ix.search(qd, 10, ef, stats=True, kernel=1)
+            assert all(torch.equal(u, v) for u, v in zip(c, g))
 
 
 @pytest.mark.parametrize("ef", [16, 64])
