@@ -120,7 +120,8 @@ typedef struct {
     int32_t kernel;          /* 0 (default) = the compact search kernel wherever it applies
                                 (one warp per query, d <= 1024, degree 32 or 64, every k[i] <= 32
                                 and ef[i] <= 128 by max_k / max_ef, multiple estimates, no
-                                learned stop, no trace, prefetch 1), else the general one;
+                                trace, prefetch 1; with or without the learned stop), else
+                                the general one;
                                 1 = always the general kernel; 2 = the compact kernel or
                                 SQG_ERR_UNSUPPORTED.  Both return identical results. */
     int32_t uniform_k;       /* 0 (default): k[] may differ per query, outputs ragged at the

@@ -1006,7 +1006,7 @@ cudaError_t search_occupancy_team(int ch, int nb, int team, int block, size_t sm
 cudaError_t search_occupancy_nb2(int ch, int block, size_t smem, int *blocks_per_sm);
 // the compact kernel (search_compact.cuh): d <= 1024 (ch 1, 2, 4, 8),
 // out-degree 32 (nr 1) or 64 (nr 2), k <= 32, ef <= 64 (bnb 2) or 128 (bnb
-// 4) beam entries, whole warps, multiple estimates, no stop network or trace
+// 4) beam entries, whole warps, multiple estimates, no trace
 // (lean 1, d <= 256 and out-degree 32: the build for one more resident block
 // of 4 warps per SM: 9 / 8, else 8 / 7)
 cudaError_t launch_search_compact(int ch, int nr, int bnb, int lean, dim3 grid, dim3 block, size_t smem,
@@ -1016,5 +1016,9 @@ cudaError_t search_occupancy_compact(int ch, int nr, int bnb, int lean, int bloc
 cudaError_t launch_search_compact_wide(int ch, int nr, int bnb, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                                        const SearchArgs &a);
 cudaError_t search_occupancy_compact_wide(int ch, int nr, int bnb, int block, size_t smem, int *blocks_per_sm);
+// its builds with the learned early stop fused (search_compact_stop.cu)
+cudaError_t launch_search_compact_stop(int ch, int nr, int bnb, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                       const SearchArgs &a);
+cudaError_t search_occupancy_compact_stop(int ch, int nr, int bnb, int block, size_t smem, int *blocks_per_sm);
 
 }  // namespace sqg

@@ -132,6 +132,12 @@ __device__ __forceinline__ float keyR(const float *fac, const QuerySide &qs, uin
     return __fsub_rn(est, __fmul_rn(eps0, bound));
 }
 
+// The key a packed entry holds (the inverse of key_bits; -0 comes back as +0).
+__device__ __forceinline__ float entry_key(uint64_t e) {
+    const uint32_t kb = (uint32_t)(e >> 32);
+    return __uint_as_float((kb & 0x80000000u) ? (kb & 0x7FFFFFFFu) : ~kb);
+}
+
 // Entry s of a lane's NB beam registers, s warp-uniform (an unrolled
 // select: no local-memory array).
 template <int NB>
@@ -149,8 +155,10 @@ __device__ __forceinline__ uint64_t pick(const uint64_t (&b)[NB], int s) {
 // neighbours per lane (out-degree 32 NR).  NB: beam slots per lane (2: ef <=
 // 64, 4: ef <= 128).  MINB: resident blocks of 4 warps per SM the build is
 // made for (d <= 256 with NR 1: NB 2: 8 for up to 64 registers or 9 for 56;
-// NB 4: 7 for up to 72 or 8 for 64).
-template <int CH, int NR, int NB, int MINB>
+// NB 4: 7 for up to 72 or 8 for 64).  STOP: the build with the learned
+// early stop fused (the same features, network and decision points as
+// search_kernel's, so the same hops, results and status bits).
+template <int CH, int NR, int NB, int MINB, bool STOP = false>
 __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchArgs a) {
     using namespace compact;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -240,6 +248,10 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
             bulk_fetch(buf, a.blocks + (size_t)p * a.block_bytes, a.block_bytes, &bar[0]);
         }
         int hops = 1;
+        // learned-stop state (STOP builds): last hop whose vertex entered the
+        // result, moving averages of entering and of the inserted share
+        int last_improve = 0;
+        float ema_improve = 0.0f, ema_insert = 0.0f;
 
         for (;;) {
             if (!mbar_wait_bounded(&bar[0], phase & 1u)) {
@@ -269,9 +281,11 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                 __syncwarp();
                 if (ef == 1) bworst = shfl64(b[0], 0);
             }
+            bool improved = false;
             {  // result top-k in registers: (dist bits << 32) | id, dist >= 0
                 const uint64_t r = ((uint64_t)__float_as_uint(dist_c) << 32) | p;
                 if (r < rworst) {
+                    improved = true;
                     const int pos = __popc(__ballot_sync(kFull, lane < k && res < r));
                     const uint64_t up = shfl64_up(res, 1);
                     if (lane == pos) res = r;
@@ -334,17 +348,21 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                     nxt = o < nxt ? o : nxt;
                 }
             }
-            if (nxt == kNone) break;  // no unvisited entry: the search ends (line 2)
-            if (hops >= hop_cap) {    // reading R6
-                status |= SQG_STATUS_CAPACITY;
-                break;
+            if constexpr (!STOP) {  // (with the stop these two ends follow its decision)
+                if (nxt == kNone) break;  // no unvisited entry: the search ends (line 2)
+                if (hops >= hop_cap) {    // reading R6
+                    status |= SQG_STATUS_CAPACITY;
+                    break;
+                }
             }
+            const bool go = !STOP || (nxt != kNone && hops < hop_cap);  // a next expansion follows
             const uint32_t pn = entry_id(nxt);
             __syncwarp();  // every lane's reads of the current block are done
-            if (lane == 0) {
+            if (go && lane == 0) {
                 fence_proxy_async();
                 bulk_fetch(buf, a.blocks + (size_t)pn * a.block_bytes, a.block_bytes, &bar[0]);
             }
+            int inserted = 0;  // this step's candidates kept by the cut (the stop's features)
 
             // ---- line 6: merge the admitted candidates, cut the beam to ef
             const uint64_t *B = beam_a;
@@ -392,6 +410,7 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                 for (int t = 0; t < NR; ++t) {
                     fp[t] = pos[t] + rank[t];
                     if (adm[t]) stage[rank[t]] = cand[t];
+                    if constexpr (STOP) inserted += __popc(__ballot_sync(kFull, adm[t] && fp[t] < ef));
                 }
                 uint32_t mk[NB];  // bit l of mk[s]: a candidate lands in slot 32 s + l
 #pragma unroll
@@ -422,6 +441,73 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                 // (a visited mark set below does not matter to the early cut: no
                 // candidate shares an id with a visited entry)
                 bworst = m == ef ? shfl64(pick<NB>(b, (ef - 1) >> 5), (ef - 1) & 31) : kNone;
+            }
+
+            // ---- learned early stop (not in the paper): after the merge, on
+            // the merged beam, before the next vertex is marked -- the point
+            // where search_kernel takes it
+            if constexpr (STOP) {
+                if (improved) last_improve = hops;
+                ema_improve = __fadd_rn(__fmul_rn(0.75f, ema_improve), __fmul_rn(0.25f, improved ? 1.0f : 0.0f));
+                const float inv_R = __fdiv_rn(1.0f, (float)(32 * NR));
+                ema_insert = __fadd_rn(__fmul_rn(0.75f, ema_insert), __fmul_rn(0.25f, __fmul_rn((float)inserted, inv_R)));
+                if (a.stop_every > 0 && hops % a.stop_every == 0 && rworst != kNone) {
+                    const float rk = __uint_as_float((uint32_t)(rworst >> 32));
+                    const float rk2 = __fmul_rn(1.25f, rk);
+                    int u = 0, near1 = 0, near2 = 0;  // unvisited; of them with key <= rk, <= 1.25 rk
+#pragma unroll
+                    for (int s = 0; s < NB; ++s) {
+                        const bool un = !(b[s] & 1ull);  // kNone reads as visited
+                        const float kk = un ? entry_key(b[s]) : 0.0f;
+                        u += __popc(__ballot_sync(kFull, un));
+                        near1 += __popc(__ballot_sync(kFull, un && kk <= rk));
+                        near2 += __popc(__ballot_sync(kFull, un && kk <= rk2));
+                    }
+                    const float den = rk > 1e-20f ? rk : 1e-20f;
+                    const float fef = (float)ef;
+                    const float since = (float)(hops - last_improve);
+                    const float inv_ef = __fdiv_rn(1.0f, fef), inv_den = __fdiv_rn(1.0f, den);
+                    const float inv_k = __fdiv_rn(1.0f, (float)k);
+                    const float inv_h1 = __fdiv_rn(1.0f, __fadd_rn((float)hops, 1.0f));
+                    const float r0 = __uint_as_float((uint32_t)(shfl64(res, 0) >> 32));
+                    float f[SQG_MLP_IN];
+                    f[0] = __fmul_rn((float)hops, inv_ef);
+                    f[1] = __fmul_rn(since, inv_ef);
+                    f[2] = __fmul_rn((float)u, inv_ef);
+                    f[3] = __fmul_rn((float)m, inv_ef);
+                    f[4] = __fmul_rn(r0, inv_den);
+                    f[5] = u > 0 ? __fmul_rn(entry_key(nxt), inv_den) : 0.0f;  // nxt: the first unvisited entry
+                    f[6] = __fmul_rn(dist_c, inv_den);
+                    f[7] = __fmul_rn((float)inserted, inv_R);
+                    f[8] = __fmul_rn((float)k, inv_ef);
+                    f[9] = ema_improve;
+                    f[10] = ema_insert;
+                    f[11] = __fmul_rn((float)near1, inv_k);
+                    f[12] = __fmul_rn((float)near2, inv_k);
+                    f[13] = __fmul_rn(since, inv_h1);
+                    f[14] = dist_c <= rk ? 1.0f : 0.0f;
+                    f[15] = __fmul_rn((float)k, 0.01f);
+#pragma unroll
+                    for (int i = 0; i < SQG_MLP_IN; ++i) f[i] = clamp8(f[i]);
+                    __syncwarp();  // the gather's reads of the stage are done: it holds the hidden layer
+                    if (mlp_logit_warp(a.mlp, f, lane, reinterpret_cast<float *>(stage)) > a.stop_logit) {
+                        status |= SQG_STATUS_LEARNED_STOP;
+                        if (go) {  // the copy issued for the next vertex completes unused
+                            if (mbar_wait_bounded(&bar[0], phase & 1u)) {
+                                phase ^= 1u;
+                            } else {
+                                status |= SQG_STATUS_TIMEOUT;
+                                healthy = false;
+                            }
+                        }
+                        break;
+                    }
+                }
+                if (nxt == kNone) break;  // no unvisited entry: the search ends (line 2)
+                if (hops >= hop_cap) {    // reading R6
+                    status |= SQG_STATUS_CAPACITY;
+                    break;
+                }
             }
 
             // ---- line 3: the next vertex is visited; every copy of it in the
@@ -456,18 +542,18 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
     }
 }
 
-template <int CH, int NR, int NB, int MINB>
+template <int CH, int NR, int NB, int MINB, bool STOP = false>
 static cudaError_t compact_launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const SearchArgs &a) {
-    auto fn = search_compact_kernel<CH, NR, NB, MINB>;
+    auto fn = search_compact_kernel<CH, NR, NB, MINB, STOP>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int CH, int NR, int NB, int MINB>
+template <int CH, int NR, int NB, int MINB, bool STOP = false>
 static cudaError_t compact_occ_one(int block, size_t smem, int *nb) {
-    auto fn = search_compact_kernel<CH, NR, NB, MINB>;
+    auto fn = search_compact_kernel<CH, NR, NB, MINB, STOP>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, fn, block, smem);

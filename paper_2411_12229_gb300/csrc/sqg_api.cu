@@ -373,7 +373,7 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     pl.team = p.team == 0 ? 32 : p.team;
     const int V = 32 / pl.team;  // queries per warp
     pl.compact = p.kernel != 1 && pl.team == 32 && pl.ch <= 8 && max_k <= 32 && max_ef <= 128 &&
-                 p.multi_estimate && !p.stop_mlp && !traced && p.prefetch != 2 && p.lean != 2;
+                 p.multi_estimate && !traced && p.prefetch != 2 && p.lean != 2;
     if (p.kernel == 2 && !pl.compact) return SQG_ERR_UNSUPPORTED;
     pl.cbnb = max_ef <= 64 ? 2 : 4;
     if (pl.compact) {
@@ -430,7 +430,8 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
         const size_t sm = cta + (size_t)w * V * warp_bytes;
         *blocks = 0;
         if (sm > ix->smem_optin) return cudaSuccess;
-        return pl.compact     ? search_occupancy_compact(pl.ch, pl.nb, pl.cbnb, p.lean, w * 32, sm, blocks)
+        return pl.compact && p.stop_mlp ? search_occupancy_compact_stop(pl.ch, pl.nb, pl.cbnb, w * 32, sm, blocks)
+             : pl.compact     ? search_occupancy_compact(pl.ch, pl.nb, pl.cbnb, p.lean, w * 32, sm, blocks)
              : pl.team < 32 ? search_occupancy_team(pl.ch, pl.nb, pl.team, w * 32, sm, blocks)
              : pl.nb == 1   ? search_occupancy_nb1(pl.ch, w * 32, sm, blocks)
                             : search_occupancy_nb2(pl.ch, w * 32, sm, blocks);
@@ -713,6 +714,8 @@ extern "C" size_t sqg_workspace_size(const sqg_index *ix, int nq, int max_k, int
     if (make_plan(ix, nq, max_k, max_ef, p, pl) == SQG_OK) need = std::max(need, pl.ws_total);
     p.stop_mlp = reinterpret_cast<const float *>(16);  // any non-null: only the layout is planned
     if (make_plan(ix, nq, max_k, max_ef, p, pl) == SQG_OK) need = std::max(need, pl.ws_total);
+    p.kernel = 0;  // the compact kernel's build with the stop fused
+    if (make_plan(ix, nq, max_k, max_ef, p, pl) == SQG_OK) need = std::max(need, pl.ws_total);
     return need;
 }
 
@@ -847,8 +850,11 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     if (e == cudaSuccess && p.timing_events[0])
         e = cudaEventRecord(reinterpret_cast<cudaEvent_t>(p.timing_events[0]), stream);
     if (e == cudaSuccess) {
-        e = pl.compact ? launch_search_compact(pl.ch, pl.nb, pl.cbnb, p.lean, dim3(pl.grid), dim3(pl.warps * 32),
-                                               pl.smem, stream, a)
+        e = pl.compact && p.stop_mlp
+                ? launch_search_compact_stop(pl.ch, pl.nb, pl.cbnb, dim3(pl.grid), dim3(pl.warps * 32), pl.smem,
+                                             stream, a)
+            : pl.compact ? launch_search_compact(pl.ch, pl.nb, pl.cbnb, p.lean, dim3(pl.grid), dim3(pl.warps * 32),
+                                                 pl.smem, stream, a)
             : pl.team < 32 ? launch_search_team(pl.ch, pl.nb, pl.team, dim3(pl.grid), dim3(pl.warps * 32), pl.smem,
                                                 stream, a)
             : pl.nb == 1 ? launch_search_nb1(pl.ch, dim3(pl.grid), dim3(pl.warps * 32), pl.smem, stream, a)

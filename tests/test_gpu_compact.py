@@ -2,8 +2,8 @@
 gathered merge, results in registers) against the oracle.
 
 It serves every search it applies to (one warp per query, d <= 1024,
-degree 32 or 64, k <= 32, ef <= 128, multiple estimates, no learned stop, no
-trace); here it is forced (kernel = 2) and held to the same bar as the
+degree 32 or 64, k <= 32, ef <= 128, multiple estimates, no trace; the
+learned stop in a build of its own); here it is forced (kernel = 2) and held to the same bar as the
 general kernel: ids, distances, hop counts and status bits identical to
 the oracle, on the plain and the ragged batch, with the error-bound key,
 binding hop caps, exact ties and duplicate vectors, visited-set moves, the

@@ -337,27 +337,54 @@ def test_speculative_prefetch_changes_nothing(gpu_tiny, oracle_mod):
     _check_search(ix, oracle_mod.Index(p), q, 10, 64, prefetch=2, warps_per_block=1)
 
 
-def test_learned_stop_constant_networks(gpu_tiny, oracle_mod):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_learned_stop_constant_networks(gpu_tiny, oracle_mod, kernel):
+    """kernel 1: the stop fused into the general kernel; 2: into the
+    compact kernel's stop build."""
     ix, p, x, q = gpu_tiny
     O = oracle_mod.Index(p)
     mlp = np.zeros(5313, np.float32)
     for b3, want in ((-100.0, 0), (100.0, 2)):
         mlp[-1] = b3
         dm = torch.from_numpy(mlp).cuda()
-        _, _, st = _check_search(ix, O, q, 10, 64, stop_mlp=dm, mlp_np=mlp, stop_logit=0.0, stop_every=4)
+        _, _, st = _check_search(ix, O, q, 10, 64, stop_mlp=dm, mlp_np=mlp, stop_logit=0.0, stop_every=4,
+                                 kernel=kernel)
         assert np.all(st[:, 1] == want)
 
 
-def test_learned_stop_random_network_parity(gpu_tiny, oracle_mod):
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("ef", [64, 100])
+def test_learned_stop_random_network_parity(gpu_tiny, oracle_mod, kernel, ef):
     """A random network: the fused fp32 forward takes the same stop decision
-    at the same hop as the oracle's forward."""
+    at the same hop as the oracle's forward (both kernels; 2 and 4 beam
+    slots per lane in the compact one)."""
     ix, p, x, q = gpu_tiny
     O = oracle_mod.Index(p)
     rng = np.random.default_rng(5)
     mlp = (rng.standard_normal(5313) * 0.3).astype(np.float32)
     dm = torch.from_numpy(mlp).cuda()
     for thr in (-1.0, 0.5, 2.0):
-        _check_search(ix, O, q, 10, 64, stop_mlp=dm, mlp_np=mlp, stop_logit=thr, stop_every=2)
+        _check_search(ix, O, q, 10, ef, stop_mlp=dm, mlp_np=mlp, stop_logit=thr, stop_every=2, kernel=kernel)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_learned_stop_edges(gpu_tiny, gpu_tiny64, oracle_mod, kernel):
+    """The stop with a binding hop cap, the error-bound key, every hop
+    (the last expansion of a search that ends by itself included), small k
+    and out-degree 64 (two neighbours per lane)."""
+    rng = np.random.default_rng(8)
+    mlp = (rng.standard_normal(5313) * 0.3).astype(np.float32)
+    dm = torch.from_numpy(mlp).cuda()
+    kw = dict(stop_mlp=dm, mlp_np=mlp, kernel=kernel)
+    ix, p, x, q = gpu_tiny
+    O = oracle_mod.Index(p)
+    _check_search(ix, O, q, 10, 64, stop_logit=1.0, stop_every=3, hop_cap=20, **kw)
+    _check_search(ix, O, q, 10, 48, stop_logit=1.0, stop_every=2, eps0=1.9, **kw)
+    _, _, st = _check_search(ix, O, q, 1, 8, stop_logit=3.0, stop_every=1, **kw)
+    ix, p, x, q = gpu_tiny64
+    O = oracle_mod.Index(p)
+    for ef in (40, 128):
+        _check_search(ix, O, q, 10, ef, stop_logit=0.5, stop_every=2, **kw)
 
 
 def test_trace_features_bit_exact(gpu_tiny, oracle_mod):
