@@ -25,6 +25,7 @@
 // intrinsics; the file is built with -fmad=false), so that the CPU oracle
 // can take the same decisions bit for bit.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -62,6 +63,7 @@ struct SearchArgs {
     const float *mlp;       // the stop network with W1, W2 transposed to [in][out], or null
     float stop_logit;
     int stop_every;
+    uint64_t stop_magic;  // 2^64 / stop_every + 1 for stop_every >= 2 (hops mod stop_every by a multiply)
     int prefetch;       // 1: next block only; 2: also L2-prefetch the runner-up
     float *trace_feat;  // nq x trace_cap x 16, or null
     int32_t *trace_hit; // nq x trace_cap
@@ -431,8 +433,14 @@ __device__ __forceinline__ float clamp8(float x) { return x < -8.0f ? -8.0f : (x
 // its bias; the first layer's outputs pass to the second through `hbuf`
 // (64 floats of the warp's shared memory); the output adds
 // p_l = fmaf(W3[l+32], h[l+32], W3[l] h[l]) by xor butterfly, then b3.
-__device__ __forceinline__ float mlp_logit_warp(const float *w, const float (&f)[SQG_MLP_IN], int lane,
-                                                float *hbuf) {
+// The features f come from registers (an array) or from shared memory (a
+// pointer to SQG_MLP_IN floats the warp wrote before a __syncwarp); the
+// arithmetic is the same.  From shared memory the loops are not unrolled,
+// so that few registers are in flight (for builds at their register
+// limit); from registers they are, for more loads in flight.
+template <typename FV>
+__device__ __forceinline__ float mlp_logit_warp(const float *w, const FV &f, int lane, float *hbuf) {
+    constexpr bool kLean = std::is_pointer<FV>::value;
     const float4 *W1p = reinterpret_cast<const float4 *>(w);               // [8][32]
     const float2 *b1p = reinterpret_cast<const float2 *>(w + 8 * 32 * 4);  // [32]
     const float4 *W2p = reinterpret_cast<const float4 *>(w + 8 * 32 * 4 + 64);        // [32][32]
@@ -441,13 +449,19 @@ __device__ __forceinline__ float mlp_logit_warp(const float *w, const float (&f)
     const float *b3 = reinterpret_cast<const float *>(W3p + 32);
     const float2 bb1 = __ldg(b1p + lane);
     float ha = bb1.x, hb = bb1.y;
-#pragma unroll
-    for (int i2 = 0; i2 < SQG_MLP_IN / 2; ++i2) {
+    auto layer1 = [&](int i2) {
         const float4 wv = __ldg(W1p + i2 * 32 + lane);
         ha = __fmaf_rn(wv.x, f[2 * i2], ha);
         hb = __fmaf_rn(wv.y, f[2 * i2], hb);
         ha = __fmaf_rn(wv.z, f[2 * i2 + 1], ha);
         hb = __fmaf_rn(wv.w, f[2 * i2 + 1], hb);
+    };
+    if constexpr (kLean) {
+#pragma unroll 1
+        for (int i2 = 0; i2 < SQG_MLP_IN / 2; ++i2) layer1(i2);
+    } else {  // a register array: constant indices only
+#pragma unroll
+        for (int i2 = 0; i2 < SQG_MLP_IN / 2; ++i2) layer1(i2);
     }
     hbuf[lane] = ha > 0.0f ? ha : 0.0f;
     hbuf[lane + 32] = hb > 0.0f ? hb : 0.0f;
@@ -455,8 +469,7 @@ __device__ __forceinline__ float mlp_logit_warp(const float *w, const float (&f)
     const float2 bb2 = __ldg(b2p + lane);
     float ga = bb2.x, gb = bb2.y;
     const float4 *h4 = reinterpret_cast<const float4 *>(hbuf);
-#pragma unroll 4
-    for (int i4 = 0; i4 < 16; ++i4) {
+    auto layer2 = [&](int i4) {
         const float4 h = h4[i4];
         const float4 w0 = __ldg(W2p + (2 * i4) * 32 + lane), w1 = __ldg(W2p + (2 * i4 + 1) * 32 + lane);
         ga = __fmaf_rn(w0.x, h.x, ga);
@@ -467,6 +480,13 @@ __device__ __forceinline__ float mlp_logit_warp(const float *w, const float (&f)
         gb = __fmaf_rn(w1.y, h.z, gb);
         ga = __fmaf_rn(w1.z, h.w, ga);
         gb = __fmaf_rn(w1.w, h.w, gb);
+    };
+    if constexpr (kLean) {
+#pragma unroll 1
+        for (int i4 = 0; i4 < 16; ++i4) layer2(i4);
+    } else {
+#pragma unroll 4
+        for (int i4 = 0; i4 < 16; ++i4) layer2(i4);
     }
     __syncwarp();  // hbuf may be reused after this
     ga = ga > 0.0f ? ga : 0.0f;

@@ -41,6 +41,13 @@ namespace compact {
 
 constexpr uint64_t kNone = ~0ull;  // an empty beam or result slot (greater than every entry)
 
+// The learned stop's state carried from hop to hop (12 bytes of the warp's
+// shared memory after its mbarrier).
+struct StopCarry {
+    int last_improve;
+    float ema_improve, ema_insert;
+};
+
 // Order-preserving map of a float key (never NaN) to uint32: a < b as floats
 // iff map(a) < map(b) as unsigned integers; -0 and +0 map to one value, as
 // they compare equal as floats.
@@ -248,10 +255,13 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
             bulk_fetch(buf, a.blocks + (size_t)p * a.block_bytes, a.block_bytes, &bar[0]);
         }
         int hops = 1;
-        // learned-stop state (STOP builds): last hop whose vertex entered the
-        // result, moving averages of entering and of the inserted share
-        int last_improve = 0;
-        float ema_improve = 0.0f, ema_insert = 0.0f;
+        // learned-stop state (STOP builds): the last hop whose vertex entered
+        // the result and the moving averages of entering and of the inserted
+        // share, kept by lane 0 in shared memory beside the barrier (no
+        // registers held across the loop)
+        StopCarry *const sst = reinterpret_cast<StopCarry *>(ws + a.o_bar + 8);
+        if (STOP && lane == 0)
+            *sst = StopCarry{0, 0.0f, 0.0f};
 
         for (;;) {
             if (!mbar_wait_bounded(&bar[0], phase & 1u)) {
@@ -318,35 +328,17 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
             // unvisited beam entry.  A candidate equal in (key, id) to a beam
             // entry (dropped below as a duplicate) names that entry's vertex,
             // which is unvisited, so it may stand in for it here.
-            uint64_t nxt = kNone;
-            if (anyam) {
-                uint32_t h = 0xFFFFFFFFu;
+            uint64_t nxt;
+            {  // the smallest of the lane's admitted candidates and unvisited
+               // entries, then the warp's smallest (high word, then low word)
+                uint64_t v = kNone;
 #pragma unroll
-                for (int t = 0; t < NR; ++t) h = min(h, adm[t] ? (uint32_t)(cand[t] >> 32) : 0xFFFFFFFFu);
-                const uint32_t chi = __reduce_min_sync(kFull, h);
-                uint32_t l = 0xFFFFFFFFu;
+                for (int t = 0; t < NR; ++t) v = adm[t] && cand[t] < v ? cand[t] : v;
 #pragma unroll
-                for (int t = 0; t < NR; ++t)
-                    l = min(l, adm[t] && (uint32_t)(cand[t] >> 32) == chi ? (uint32_t)cand[t] : 0xFFFFFFFFu);
-                const uint32_t clo = __reduce_min_sync(kFull, l);
+                for (int s = 0; s < NB; ++s) v = !(b[s] & 1ull) && b[s] < v ? b[s] : v;  // kNone: visited
+                const uint32_t chi = __reduce_min_sync(kFull, (uint32_t)(v >> 32));
+                const uint32_t clo = __reduce_min_sync(kFull, (uint32_t)(v >> 32) == chi ? (uint32_t)v : 0xFFFFFFFFu);
                 nxt = ((uint64_t)chi << 32) | clo;
-            }
-            {
-                uint32_t u[NB];
-#pragma unroll
-                for (int s = 0; s < NB; ++s) u[s] = __ballot_sync(kFull, !(b[s] & 1ull));  // kNone: visited
-                int su = NB;  // the first slot row with an unvisited entry
-                uint32_t uu = 0;
-#pragma unroll
-                for (int s = NB - 1; s >= 0; --s)
-                    if (u[s]) {
-                        su = s;
-                        uu = u[s];
-                    }
-                if (su < NB) {
-                    const uint64_t o = shfl64(pick<NB>(b, su), __ffs(uu) - 1);
-                    nxt = o < nxt ? o : nxt;
-                }
             }
             if constexpr (!STOP) {  // (with the stop these two ends follow its decision)
                 if (nxt == kNone) break;  // no unvisited entry: the search ends (line 2)
@@ -398,8 +390,14 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                 int rank[NR];
 #pragma unroll
                 for (int t = 0; t < NR; ++t) rank[t] = 0;
-#pragma unroll 4
-                for (int j = 0; j < nadm; ++j) {
+                int j = 0;
+#pragma unroll 2
+                for (; j + 2 <= nadm; j += 2) {  // two staged candidates per 16-byte read
+                    const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(stage + j);
+#pragma unroll
+                    for (int t = 0; t < NR; ++t) rank[t] += (v.x < cand[t] ? 1 : 0) + (v.y < cand[t] ? 1 : 0);
+                }
+                if (j < nadm) {
                     const uint64_t v = stage[j];
 #pragma unroll
                     for (int t = 0; t < NR; ++t) rank[t] += v < cand[t] ? 1 : 0;
@@ -447,11 +445,19 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
             // the merged beam, before the next vertex is marked -- the point
             // where search_kernel takes it
             if constexpr (STOP) {
-                if (improved) last_improve = hops;
-                ema_improve = __fadd_rn(__fmul_rn(0.75f, ema_improve), __fmul_rn(0.25f, improved ? 1.0f : 0.0f));
-                const float inv_R = __fdiv_rn(1.0f, (float)(32 * NR));
-                ema_insert = __fadd_rn(__fmul_rn(0.75f, ema_insert), __fmul_rn(0.25f, __fmul_rn((float)inserted, inv_R)));
-                if (a.stop_every > 0 && hops % a.stop_every == 0 && rworst != kNone) {
+                constexpr float inv_R = 1.0f / (32 * NR);  // a power of 2: exact, the division's value
+                if (lane == 0) {
+                    if (improved) sst->last_improve = hops;
+                    sst->ema_improve =
+                        __fadd_rn(__fmul_rn(0.75f, sst->ema_improve), __fmul_rn(0.25f, improved ? 1.0f : 0.0f));
+                    sst->ema_insert =
+                        __fadd_rn(__fmul_rn(0.75f, sst->ema_insert), __fmul_rn(0.25f, __fmul_rn((float)inserted, inv_R)));
+                }
+                // hops mod the period by a multiply-high with the host's
+                // 2^64 / period + 1, exact for every hops < 2^32
+                const uint64_t hq = __umul64hi((uint64_t)hops, a.stop_magic);
+                const bool eval_now = a.stop_every == 1 || (uint64_t)hops == hq * (uint64_t)a.stop_every;
+                if (a.stop_every > 0 && eval_now && rworst != kNone) {
                     const float rk = __uint_as_float((uint32_t)(rworst >> 32));
                     const float rk2 = __fmul_rn(1.25f, rk);
                     int u = 0, near1 = 0, near2 = 0;  // unvisited; of them with key <= rk, <= 1.25 rk
@@ -464,33 +470,49 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                         near2 += __popc(__ballot_sync(kFull, un && kk <= rk2));
                     }
                     const float den = rk > 1e-20f ? rk : 1e-20f;
-                    const float fef = (float)ef;
-                    const float since = (float)(hops - last_improve);
-                    const float inv_ef = __fdiv_rn(1.0f, fef), inv_den = __fdiv_rn(1.0f, den);
+                    const float since = (float)(hops - sst->last_improve);  // (lane 0's value is the one written)
+                    const float inv_ef = __fdiv_rn(1.0f, (float)ef), inv_den = __fdiv_rn(1.0f, den);
                     const float inv_k = __fdiv_rn(1.0f, (float)k);
                     const float inv_h1 = __fdiv_rn(1.0f, __fadd_rn((float)hops, 1.0f));
                     const float r0 = __uint_as_float((uint32_t)(shfl64(res, 0) >> 32));
+                    // d <= 256 (builds at their register limit): the features go to
+                    // the beam buffer the next merge writes (idle until then), each
+                    // as soon as it is known, so that few registers hold them;
+                    // larger d: registers.  The stage holds the hidden layer.
+                    constexpr bool kFeatSmem = CH <= 2;
+                    float *const fs = reinterpret_cast<float *>(beam_b);
                     float f[SQG_MLP_IN];
-                    f[0] = __fmul_rn((float)hops, inv_ef);
-                    f[1] = __fmul_rn(since, inv_ef);
-                    f[2] = __fmul_rn((float)u, inv_ef);
-                    f[3] = __fmul_rn((float)m, inv_ef);
-                    f[4] = __fmul_rn(r0, inv_den);
-                    f[5] = u > 0 ? __fmul_rn(entry_key(nxt), inv_den) : 0.0f;  // nxt: the first unvisited entry
-                    f[6] = __fmul_rn(dist_c, inv_den);
-                    f[7] = __fmul_rn((float)inserted, inv_R);
-                    f[8] = __fmul_rn((float)k, inv_ef);
-                    f[9] = ema_improve;
-                    f[10] = ema_insert;
-                    f[11] = __fmul_rn((float)near1, inv_k);
-                    f[12] = __fmul_rn((float)near2, inv_k);
-                    f[13] = __fmul_rn(since, inv_h1);
-                    f[14] = dist_c <= rk ? 1.0f : 0.0f;
-                    f[15] = __fmul_rn((float)k, 0.01f);
-#pragma unroll
-                    for (int i = 0; i < SQG_MLP_IN; ++i) f[i] = clamp8(f[i]);
-                    __syncwarp();  // the gather's reads of the stage are done: it holds the hidden layer
-                    if (mlp_logit_warp(a.mlp, f, lane, reinterpret_cast<float *>(stage)) > a.stop_logit) {
+                    __syncwarp();  // the gather's reads of both buffers and the stage are done
+                    auto put = [&](int i, float v) {
+                        if constexpr (kFeatSmem) {
+                            if (lane == 0) fs[i] = clamp8(v);
+                        } else {
+                            f[i] = clamp8(v);
+                        }
+                    };
+                    put(0, __fmul_rn((float)hops, inv_ef));
+                    put(1, __fmul_rn(since, inv_ef));
+                    put(2, __fmul_rn((float)u, inv_ef));
+                    put(3, __fmul_rn((float)m, inv_ef));
+                    put(4, __fmul_rn(r0, inv_den));
+                    put(5, u > 0 ? __fmul_rn(entry_key(nxt), inv_den) : 0.0f);  // nxt: the first unvisited entry
+                    put(6, __fmul_rn(dist_c, inv_den));
+                    put(7, __fmul_rn((float)inserted, inv_R));
+                    put(8, __fmul_rn((float)k, inv_ef));
+                    put(9, sst->ema_improve);
+                    put(10, sst->ema_insert);
+                    put(11, __fmul_rn((float)near1, inv_k));
+                    put(12, __fmul_rn((float)near2, inv_k));
+                    put(13, __fmul_rn(since, inv_h1));
+                    put(14, dist_c <= rk ? 1.0f : 0.0f);
+                    put(15, __fmul_rn((float)k, 0.01f));
+                    __syncwarp();
+                    float logit;
+                    if constexpr (kFeatSmem)
+                        logit = mlp_logit_warp(a.mlp, static_cast<const float *>(fs), lane, reinterpret_cast<float *>(stage));
+                    else
+                        logit = mlp_logit_warp(a.mlp, f, lane, reinterpret_cast<float *>(stage));
+                    if (logit > a.stop_logit) {
                         status |= SQG_STATUS_LEARNED_STOP;
                         if (go) {  // the copy issued for the next vertex completes unused
                             if (mbar_wait_bounded(&bar[0], phase & 1u)) {
@@ -515,7 +537,7 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
             p = pn;
 #pragma unroll
             for (int s = 0; s < NB; ++s)
-                if (entry_id(b[s]) == p && !(b[s] & 1ull)) {
+                if ((uint32_t)b[s] == p << 1) {  // id p, not yet visited (ids < 2^31)
                     b[s] |= 1ull;
                     beam_a[lane + 32 * s] = b[s];
                 }

@@ -401,7 +401,7 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     // the resident warps at d = 960 / 1536
     a.o_buf0 = (uint32_t)o; o += bb;
     a.o_buf1 = a.o_buf0;
-    a.o_bar = (uint32_t)o; o += 16;
+    a.o_bar = (uint32_t)o; o += 32;  // the mbarrier(s); the compact kernel keeps its stop state after the first
     a.o_planes = (uint32_t)o; o = align_up(o + 16 * (d / 32), 16);
     if (pl.compact) {
         // two beam buffers of 32 cbnb packed entries, the step's candidates
@@ -815,6 +815,7 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     }
     a.stop_logit = p.stop_logit;
     a.stop_every = p.stop_every;
+    a.stop_magic = p.stop_every >= 2 ? ~0ull / (uint64_t)p.stop_every + 1ull : 0ull;
     a.prefetch = p.prefetch == 0 ? 1 : p.prefetch;
     a.trace_feat = trace_feat;
     a.trace_hit = trace_hit;
