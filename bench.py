@@ -1056,8 +1056,8 @@ def main():
 
 def search_kernel_name(ix, k: int, ef: int, args) -> str:
     """The search kernel a default search of this shape runs (the compact
-    kernel's range: d <= 256, degree 32, k <= 32, ef <= 64)."""
-    if ix.d <= 256 and ix.degree == 32 and k <= 32 and ef <= 64:
+    kernel's range: d <= 1024, degree 32 or 64, k <= 32, ef <= 128)."""
+    if ix.d <= 1024 and ix.degree in (32, 64) and k <= 32 and ef <= COMPACT_MAX_EF:
         return "sqg::search_compact_kernel"
     return "sqg::search_kernel"
 
