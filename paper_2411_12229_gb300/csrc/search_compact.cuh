@@ -458,6 +458,9 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                 const uint64_t hq = __umul64hi((uint64_t)hops, a.stop_magic);
                 const bool eval_now = a.stop_every == 1 || (uint64_t)hops == hq * (uint64_t)a.stop_every;
                 if (a.stop_every > 0 && eval_now && rworst != kNone) {
+                    // lane 0's stop state is visible to every lane after this, and
+                    // the gather's reads of both beam buffers and the stage are done
+                    __syncwarp();
                     const float rk = __uint_as_float((uint32_t)(rworst >> 32));
                     const float rk2 = __fmul_rn(1.25f, rk);
                     int u = 0, near1 = 0, near2 = 0;  // unvisited; of them with key <= rk, <= 1.25 rk
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                         near2 += __popc(__ballot_sync(kFull, un && kk <= rk2));
                     }
                     const float den = rk > 1e-20f ? rk : 1e-20f;
-                    const float since = (float)(hops - sst->last_improve);  // (lane 0's value is the one written)
+                    const float since = (float)(hops - sst->last_improve);
                     const float inv_ef = __fdiv_rn(1.0f, (float)ef), inv_den = __fdiv_rn(1.0f, den);
                     const float inv_k = __fdiv_rn(1.0f, (float)k);
                     const float inv_h1 = __fdiv_rn(1.0f, __fadd_rn((float)hops, 1.0f));
@@ -482,7 +485,6 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                     constexpr bool kFeatSmem = CH <= 2;
                     float *const fs = reinterpret_cast<float *>(beam_b);
                     float f[SQG_MLP_IN];
-                    __syncwarp();  // the gather's reads of both buffers and the stage are done
                     auto put = [&](int i, float v) {
                         if constexpr (kFeatSmem) {
                             if (lane == 0) fs[i] = clamp8(v);
