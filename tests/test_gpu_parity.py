@@ -437,6 +437,28 @@ def test_other_shapes_parity(shaped_index, oracle_mod):
             assert all(torch.equal(u, v) for u, v in zip(c, g))
 
 
+def test_other_shapes_learned_stop(shaped_index, oracle_mod):
+    """The fused stop with a random network on the other workloads' shapes:
+    the compact kernel's stop builds for d = 96 and 256 (features through
+    shared memory) and for d = 960 at out-degree 64 (features in
+    registers), beams of 2 and 4 slots per lane, and the general kernel at
+    every shape (d = 1536 included): stop decisions, hops, ids and
+    distances identical to the oracle's."""
+    ix, p, x, q = shaped_index
+    O = oracle_mod.Index(p)
+    rng = np.random.default_rng(17)
+    mlp = (rng.standard_normal(5313) * 0.3).astype(np.float32)
+    dm = torch.from_numpy(mlp).cuda()
+    q = q[:24]
+    stopped = 0
+    for kernel in ((1, 2) if ix.d <= 1024 else (1,)):
+        for ef, every, thr in ((40, 3, -1.0), (100, 2, 1.5)):
+            _, _, st = _check_search(ix, O, q, 10, ef, stop_mlp=dm, mlp_np=mlp, stop_logit=thr, stop_every=every,
+                                     kernel=kernel)
+            stopped += int(np.count_nonzero(st[:, 1] & 2))  # SQG_STATUS_LEARNED_STOP
+    assert stopped > 0  # the network's decision was exercised
+
+
 @pytest.mark.parametrize("ef", [16, 64])
 def test_expansion_order_identical(gpu_tiny, oracle_mod, ef):
     """Algorithm 1 line 3: the sequence of expanded vertices, hop by hop,
