@@ -298,12 +298,15 @@ def learned_stop_comparison(args, w, ix, pool_d, gt_ids, sweep, ef_sel, device, 
     searches over distinct batches on three streams).
 
     The network is trained on the GPU from traces of separate training
-    queries with the label the stop is built for: the result already holds
-    the true top-10.  Each variant (evaluation period, fixed-ef cap at or
-    above the plain operating point) picks its threshold on held-out
-    training queries, then runs the test batches at a few thresholds; the
-    plain frontier is the sweep.  Reported: the stop's QPS at the first
-    point whose recall reaches each target, beside the plain search's."""
+    queries with the label the stop is built for (the result already holds
+    the true top-10) or with "final" (it holds what the search at the cap
+    ends with).  Variants: evaluation every 8 or 16 hops, fixed-ef caps from
+    the plain operating point up to 1.5x, for the target recall and for
+    0.99; each picks its threshold on held-out training queries, then runs
+    the test batches at a few thresholds; the plain frontier is the sweep.
+    Reported per target recall: the stop's best QPS among points reaching
+    it, beside the first plain ef reaching it, and the ratio against the
+    plain frontier interpolated to the stop's own recall."""
     from paper_2411_12229_gb300 import eval as E
     from paper_2411_12229_gb300 import learned_stop as L
     t0 = time.time()
