@@ -107,8 +107,9 @@ typedef struct {
                                 default), 2 = the 96-register build (and never the
                                 compact kernel).  Compact kernel: 0 = the build for 8
                                 resident blocks of 4 warps per SM (64 registers) up to
-                                ef 64 and for 7 (72) up to ef 128; 1 = one block more
-                                (56 / 64 registers) */
+                                ef 64 and for 7 (72) up to ef 128 with k <= 32; 1 = one
+                                block more (56 / 64 registers); ignored past ef 128 or
+                                k 32 */
     int32_t rotation;        /* q' = P^-1 q: 1 = the canonical fp32 order (see
                                 sqg_prepare_queries) on the CUDA cores; 2 = tcgen05 tensor
                                 cores (3xTF32) followed by an exact pass that recomputes in
@@ -119,9 +120,9 @@ typedef struct {
                                 whose queries always take the fast transform */
     int32_t kernel;          /* 0 (default) = the compact search kernel wherever it applies
                                 (one warp per query, d <= 1024, degree 32 or 64, every k[i] <= 32
-                                and ef[i] <= 128 by max_k / max_ef, multiple estimates, no
-                                trace, prefetch 1; with or without the learned stop), else
-                                the general one;
+                                and ef[i] <= 128 by max_k / max_ef -- for d <= 256 k[i] <= 128
+                                and ef[i] <= 256 --, multiple estimates, no trace, prefetch 1;
+                                with or without the learned stop), else the general one;
                                 1 = always the general kernel; 2 = the compact kernel or
                                 SQG_ERR_UNSUPPORTED.  Both return identical results. */
     int32_t uniform_k;       /* 0 (default): k[] may differ per query, outputs ragged at the

@@ -1026,7 +1026,8 @@ cudaError_t search_occupancy_team(int ch, int nb, int team, int block, size_t sm
 cudaError_t search_occupancy_nb2(int ch, int block, size_t smem, int *blocks_per_sm);
 // the compact kernel (search_compact.cuh): d <= 1024 (ch 1, 2, 4, 8),
 // out-degree 32 (nr 1) or 64 (nr 2), k <= 32, ef <= 64 (bnb 2) or 128 (bnb
-// 4) beam entries, whole warps, multiple estimates, no trace
+// 4) beam entries (for d <= 256 also k <= 128 and ef <= 256: the big
+// builds below), whole warps, multiple estimates, no trace
 // (lean 1, d <= 256 and out-degree 32: the build for one more resident block
 // of 4 warps per SM: 9 / 8, else 8 / 7)
 cudaError_t launch_search_compact(int ch, int nr, int bnb, int lean, dim3 grid, dim3 block, size_t smem,
@@ -1040,5 +1041,11 @@ cudaError_t search_occupancy_compact_wide(int ch, int nr, int bnb, int block, si
 cudaError_t launch_search_compact_stop(int ch, int nr, int bnb, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                                        const SearchArgs &a);
 cudaError_t search_occupancy_compact_stop(int ch, int nr, int bnb, int block, size_t smem, int *blocks_per_sm);
+// its builds for d <= 256 with 256-entry beams (bnb 8) or k <= 128 (rk 4),
+// plain or with the stop fused (search_compact_big.cu)
+cudaError_t launch_search_compact_big(int ch, int nr, int bnb, int rk, bool stop, dim3 grid, dim3 block, size_t smem,
+                                      cudaStream_t s, const SearchArgs &a);
+cudaError_t search_occupancy_compact_big(int ch, int nr, int bnb, int rk, bool stop, int block, size_t smem,
+                                         int *blocks_per_sm);
 
 }  // namespace sqg

@@ -160,12 +160,14 @@ __device__ __forceinline__ uint64_t pick(const uint64_t (&b)[NB], int s) {
 
 // CH: float4 chunks of the raw vector per lane (d <= 128 CH).  NR:
 // neighbours per lane (out-degree 32 NR).  NB: beam slots per lane (2: ef <=
-// 64, 4: ef <= 128).  MINB: resident blocks of 4 warps per SM the build is
-// made for (d <= 256 with NR 1: NB 2: 8 for up to 64 registers or 9 for 56;
-// NB 4: 7 for up to 72 or 8 for 64).  STOP: the build with the learned
-// early stop fused (the same features, network and decision points as
-// search_kernel's, so the same hops, results and status bits).
-template <int CH, int NR, int NB, int MINB, bool STOP = false>
+// 64, 4: ef <= 128, 8: ef <= 256).  MINB: resident blocks of 4 warps per SM
+// the build is made for (d <= 256 with NR 1: NB 2: 8 for up to 64 registers
+// or 9 for 56; NB 4: 7 for up to 72 or 8 for 64).  STOP: the build with the
+// learned early stop fused (the same features, network and decision points
+// as search_kernel's, so the same hops, results and status bits).  RK:
+// result slots per lane (1: k <= 32, 4: k <= 128), lane l holding results
+// l + 32 s.
+template <int CH, int NR, int NB, int MINB, bool STOP = false, int RK = 1>
 __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchArgs a) {
     using namespace compact;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -244,7 +246,9 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
             b[s] = s == 0 && lane == 0 ? pack_entry(0u, a.entry) | 1ull : kNone;
             beam_a[lane + 32 * s] = b[s];  // all 32 NB slots, kNone from m on: no bound on m below
         }
-        uint64_t res = kNone;  // result[lane], lane < k
+        uint64_t res[RK];  // res[s] = result[lane + 32 s], for lane + 32 s < k
+#pragma unroll
+        for (int s = 0; s < RK; ++s) res[s] = kNone;
         uint64_t rworst = kNone;  // result[k - 1]: the entry a new result must beat
         uint64_t bworst = kNone;  // beam[ef - 1] once the beam holds ef entries (the early cut)
         uint32_t p = a.entry;
@@ -296,11 +300,25 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                 const uint64_t r = ((uint64_t)__float_as_uint(dist_c) << 32) | p;
                 if (r < rworst) {
                     improved = true;
-                    const int pos = __popc(__ballot_sync(kFull, lane < k && res < r));
-                    const uint64_t up = shfl64_up(res, 1);
-                    if (lane == pos) res = r;
-                    else if (lane > pos && lane < k) res = up;
-                    rworst = shfl64(res, k - 1);
+                    int pos = 0;
+#pragma unroll
+                    for (int s = 0; s < RK; ++s) pos += __popc(__ballot_sync(kFull, lane + 32 * s < k && res[s] < r));
+                    // entries pos .. k - 2 move up one slot: slot j takes old j - 1
+                    // (lane 0 of row s from lane 31 of row s - 1)
+                    uint64_t up[RK];
+#pragma unroll
+                    for (int s = 0; s < RK; ++s) {
+                        const uint64_t u = shfl64_up(res[s], 1);
+                        const uint64_t c = s > 0 ? shfl64(res[s > 0 ? s - 1 : 0], 31) : kNone;
+                        up[s] = lane == 0 ? c : u;
+                    }
+#pragma unroll
+                    for (int s = 0; s < RK; ++s) {
+                        const int j = lane + 32 * s;
+                        if (j == pos) res[s] = r;
+                        else if (j > pos && j < k) res[s] = up[s];
+                    }
+                    rworst = shfl64(pick<RK>(res, (k - 1) >> 5), (k - 1) & 31);
                 }
             }
 
@@ -477,7 +495,7 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
                     const float inv_ef = __fdiv_rn(1.0f, (float)ef), inv_den = __fdiv_rn(1.0f, den);
                     const float inv_k = __fdiv_rn(1.0f, (float)k);
                     const float inv_h1 = __fdiv_rn(1.0f, __fadd_rn((float)hops, 1.0f));
-                    const float r0 = __uint_as_float((uint32_t)(shfl64(res, 0) >> 32));
+                    const float r0 = __uint_as_float((uint32_t)(shfl64(res[0], 0) >> 32));
                     // d <= 256 (builds at their register limit): the features go to
                     // the beam buffer the next merge writes (idle until then), each
                     // as soon as it is known, so that few registers hold them;
@@ -553,10 +571,14 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
         }
         // ---- line 8: the k nearest expanded vertices by exact distance
         const bool ok = !(status & SQG_STATUS_TIMEOUT);
-        if (lane < k) {
-            const bool have = ok && res != kNone;
-            a.out_ids[off + lane] = have ? (uint32_t)res : SQG_NO_ID;
-            a.out_dists[off + lane] = have ? __uint_as_float((uint32_t)(res >> 32)) : __int_as_float(0x7f800000);
+#pragma unroll
+        for (int s = 0; s < RK; ++s) {
+            const int j = lane + 32 * s;
+            if (j < k) {
+                const bool have = ok && res[s] != kNone;
+                a.out_ids[off + j] = have ? (uint32_t)res[s] : SQG_NO_ID;
+                a.out_dists[off + j] = have ? __uint_as_float((uint32_t)(res[s] >> 32)) : __int_as_float(0x7f800000);
+            }
         }
         if (lane == 0) {
             if (a.stats) a.stats[qi] = sqg_query_stats{(uint32_t)hops, status};
@@ -566,18 +588,18 @@ __global__ void __launch_bounds__(128, MINB) search_compact_kernel(const SearchA
     }
 }
 
-template <int CH, int NR, int NB, int MINB, bool STOP = false>
+template <int CH, int NR, int NB, int MINB, bool STOP = false, int RK = 1>
 static cudaError_t compact_launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const SearchArgs &a) {
-    auto fn = search_compact_kernel<CH, NR, NB, MINB, STOP>;
+    auto fn = search_compact_kernel<CH, NR, NB, MINB, STOP, RK>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int CH, int NR, int NB, int MINB, bool STOP = false>
+template <int CH, int NR, int NB, int MINB, bool STOP = false, int RK = 1>
 static cudaError_t compact_occ_one(int block, size_t smem, int *nb) {
-    auto fn = search_compact_kernel<CH, NR, NB, MINB, STOP>;
+    auto fn = search_compact_kernel<CH, NR, NB, MINB, STOP, RK>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, fn, block, smem);

@@ -355,7 +355,8 @@ int pick_ch(uint32_t d) {
 struct LaunchPlan {
     int ch, nb, team, warps, grid;
     bool compact;  // the compact kernel (search_compact.cu)
-    int cbnb;      // its beam slots per lane: 2 (ef <= 64) or 4 (ef <= 128)
+    int cbnb;      // its beam slots per lane: 2 (ef <= 64), 4 (ef <= 128) or 8 (ef <= 256, d <= 256)
+    int crk;       // its result slots per lane: 1 (k <= 32) or 4 (k <= 128, d <= 256)
     size_t smem;
     SearchArgs a;  // layout fields filled in
     bool ghash;
@@ -372,10 +373,15 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
     if (pl.ch < 0 || (pl.nb != 1 && pl.nb != 2)) return SQG_ERR_UNSUPPORTED;
     pl.team = p.team == 0 ? 32 : p.team;
     const int V = 32 / pl.team;  // queries per warp
-    pl.compact = p.kernel != 1 && pl.team == 32 && pl.ch <= 8 && max_k <= 32 && max_ef <= 128 &&
-                 p.multi_estimate && !traced && p.prefetch != 2 && p.lean != 2;
+    // the compact kernel's range: k <= 32 and ef <= 128, for d <= 256 k <= 128
+    // and ef <= 256
+    const bool small_d = pl.ch <= 2;
+    pl.compact = p.kernel != 1 && pl.team == 32 && pl.ch <= 8 && max_k <= (small_d ? 128 : 32) &&
+                 max_ef <= (small_d ? 256 : 128) && p.multi_estimate && !traced && p.prefetch != 2 && p.lean != 2;
     if (p.kernel == 2 && !pl.compact) return SQG_ERR_UNSUPPORTED;
-    pl.cbnb = max_ef <= 64 ? 2 : 4;
+    pl.cbnb = max_ef <= 64 ? 2 : max_ef <= 128 ? 4 : 8;
+    pl.crk = max_k <= 32 ? 1 : 4;
+    const bool big = pl.compact && (pl.cbnb == 8 || pl.crk == 4);  // search_compact_big.cu
     if (pl.compact) {
     } else if (pl.team < 32) {
         // smaller teams: d <= 256, the 96-register build, no fused stop network
@@ -430,7 +436,9 @@ int make_plan(const sqg_index *ix, int nq, int max_k, int max_ef, const sqg_sear
         const size_t sm = cta + (size_t)w * V * warp_bytes;
         *blocks = 0;
         if (sm > ix->smem_optin) return cudaSuccess;
-        return pl.compact && p.stop_mlp ? search_occupancy_compact_stop(pl.ch, pl.nb, pl.cbnb, w * 32, sm, blocks)
+        return big ? search_occupancy_compact_big(pl.ch, pl.nb, pl.cbnb, pl.crk, p.stop_mlp != nullptr, w * 32, sm,
+                                                  blocks)
+             : pl.compact && p.stop_mlp ? search_occupancy_compact_stop(pl.ch, pl.nb, pl.cbnb, w * 32, sm, blocks)
              : pl.compact     ? search_occupancy_compact(pl.ch, pl.nb, pl.cbnb, p.lean, w * 32, sm, blocks)
              : pl.team < 32 ? search_occupancy_team(pl.ch, pl.nb, pl.team, w * 32, sm, blocks)
              : pl.nb == 1   ? search_occupancy_nb1(pl.ch, w * 32, sm, blocks)
@@ -851,7 +859,10 @@ static int search_impl(const sqg_index *ix, const float *queries, int nq, const 
     if (e == cudaSuccess && p.timing_events[0])
         e = cudaEventRecord(reinterpret_cast<cudaEvent_t>(p.timing_events[0]), stream);
     if (e == cudaSuccess) {
-        e = pl.compact && p.stop_mlp
+        e = pl.compact && (pl.cbnb == 8 || pl.crk == 4)
+                ? launch_search_compact_big(pl.ch, pl.nb, pl.cbnb, pl.crk, p.stop_mlp != nullptr, dim3(pl.grid),
+                                            dim3(pl.warps * 32), pl.smem, stream, a)
+            : pl.compact && p.stop_mlp
                 ? launch_search_compact_stop(pl.ch, pl.nb, pl.cbnb, dim3(pl.grid), dim3(pl.warps * 32), pl.smem,
                                              stream, a)
             : pl.compact ? launch_search_compact(pl.ch, pl.nb, pl.cbnb, p.lean, dim3(pl.grid), dim3(pl.warps * 32),

@@ -2,8 +2,9 @@
 gathered merge, results in registers) against the oracle.
 
 It serves every search it applies to (one warp per query, d <= 1024,
-degree 32 or 64, k <= 32, ef <= 128, multiple estimates, no trace; the
-learned stop in a build of its own); here it is forced (kernel = 2) and held to the same bar as the
+degree 32 or 64, k <= 32, ef <= 128 -- for d <= 256 k <= 128 and ef <= 256
+--, multiple estimates, no trace; the learned stop in a build of its own);
+here it is forced (kernel = 2) and held to the same bar as the
 general kernel: ids, distances, hop counts and status bits identical to
 the oracle, on the plain and the ragged batch, with the error-bound key,
 binding hop caps, exact ties and duplicate vectors, visited-set moves, the
@@ -57,6 +58,50 @@ def test_compact_parity(gpu_tiny, oracle_mod, k, ef, lean):
     for beams of up to 64 (2 slots per lane) and 128 entries (4)."""
     ix, p, x, q = gpu_tiny
     check(ix, oracle_mod.Index(p), q, k, ef, lean=lean)
+
+
+@pytest.mark.parametrize("k,ef", [(10, 129), (10, 200), (32, 256), (33, 33), (33, 64), (64, 100), (100, 100),
+                                  (100, 160), (128, 128), (128, 256), (1, 256)])
+def test_compact_big_beams_and_results(gpu_tiny, oracle_mod, k, ef):
+    """d <= 256: beams of 129-256 entries (8 slots per lane) and 33-128
+    results (4 result slots per lane, lane l holding results l + 32 s)."""
+    ix, p, x, q = gpu_tiny
+    check(ix, oracle_mod.Index(p), q, k, ef)
+
+
+def test_compact_big_variants(gpu_tiny, gpu_tiny64_compact, oracle_mod):
+    """The big builds with out-degree 64, the error-bound key, a binding
+    hop cap, visited-set moves, a ragged batch of k in {1, 10, 100} and ef
+    up to 256, and the fused stop with a random network."""
+    ix, p, x, q = gpu_tiny
+    O = oracle_mod.Index(p)
+    check(ix, O, q, 100, 200, eps0=1.9)
+    _, _, st = check(ix, O, q, 50, 150, hop_cap=9)
+    assert np.all(st[:, 0] <= 9)
+    check(ix, O, q, 10, 240, visited_smem_log2=5)
+    rng = np.random.default_rng(31)
+    nq = q.shape[0]
+    k = rng.choice([1, 10, 100], size=nq).astype(np.int32)
+    ef = np.array([rng.integers(kk, 257) for kk in k], dtype=np.int32)
+    qd = torch.from_numpy(q).cuda()
+    kt, et = torch.from_numpy(k), torch.from_numpy(ef)
+    c = ix.search(qd, kt, et, stats=True, kernel=2, max_k=128, max_ef=256)
+    g = ix.search(qd, kt, et, stats=True, kernel=1, max_k=128, max_ef=256)
+    assert all(torch.equal(u, v) for u, v in zip(c, g))
+    ids, off = _np(c[0]).view(np.uint32), np.concatenate([[0], np.cumsum(k)])
+    for i in range(nq):
+        np.testing.assert_array_equal(ids[off[i]:off[i + 1]], O.search(q[i], int(k[i]), int(ef[i]))[0])
+    mlp = (rng.standard_normal(5313) * 0.3).astype(np.float32)
+    dm = torch.from_numpy(mlp).cuda()
+    for kk, e, thr in ((100, 160, 0.5), (10, 200, 1.5), (33, 64, -1.0)):
+        check(ix, O, q, kk, e, stop_mlp=dm, stop_logit=thr, stop_every=3,
+              oracle_kw=dict(mlp=mlp, stop_logit=thr, stop_every=3))
+    ix64, p64, x64, q64 = gpu_tiny64_compact
+    O64 = oracle_mod.Index(p64)
+    for kk, e in ((10, 160), (100, 200), (128, 256)):
+        check(ix64, O64, q64, kk, e)
+    check(ix64, O64, q64, 100, 180, stop_mlp=dm, stop_logit=0.5, stop_every=2,
+          oracle_kw=dict(mlp=mlp, stop_logit=0.5, stop_every=2))
 
 
 @pytest.mark.parametrize("ef", [48, 100])
@@ -248,7 +293,7 @@ def test_compact_applies_only_where_it_is_defined(gpu_tiny, gpu_d1152):
     from paper_2411_12229_gb300._binding import SqgError
     ix, p, x, q = gpu_tiny
     qd = torch.from_numpy(q).cuda()
-    for kw in (dict(k=33, ef=64), dict(k=10, ef=129), dict(k=10, ef=40, multi_estimate=False),
+    for kw in (dict(k=129, ef=200), dict(k=10, ef=257), dict(k=10, ef=40, multi_estimate=False),
                dict(k=10, ef=40, team=16), dict(k=10, ef=40, prefetch=2)):
         k, ef = kw.pop("k"), kw.pop("ef")
         with pytest.raises(SqgError):

@@ -431,10 +431,13 @@ def test_other_shapes_parity(shaped_index, oracle_mod):
     for ef in (10, 40, 100):
         _check_search(ix, O, q, 10, ef)
     if ix.d <= 1024:  # the compact kernel's range: its output is the general kernel's
-        for ef in (40, 128):
-            c = ix.search(qd, 10, ef, stats=True, kernel=2)
-            g = ix.search(qd, 10, ef, stats=True, kernel=1)
+        big = ((100, 160), (10, 256)) if ix.d <= 256 else ()  # k <= 128 and ef <= 256 for d <= 256
+        for k, ef in ((10, 40), (10, 128)) + big:
+            c = ix.search(qd, k, ef, stats=True, kernel=2)
+            g = ix.search(qd, k, ef, stats=True, kernel=1)
             assert all(torch.equal(u, v) for u, v in zip(c, g))
+        for k, ef in big:
+            _check_search(ix, O, q[:16], k, ef, kernel=2)
 
 
 def test_other_shapes_learned_stop(shaped_index, oracle_mod):
