@@ -320,9 +320,11 @@ def learned_stop_comparison(args, w, ix, pool_d, gt_ids, sweep, ef_sel, device, 
 
     def caps_for(ef0):
         # fixed-ef caps from the plain operating point up to 1.5x; where that
-        # point runs in the compact kernel, caps stay in its range (ef <= 128)
+        # point runs in the compact kernel, caps stay in its range (ef <= 128,
+        # for d <= 256 ef <= 256)
         cs = {ef0, int(round(1.25 * ef0)), int(round(1.5 * ef0))}
-        return sorted({min(c, COMPACT_MAX_EF) for c in cs} if ef0 <= COMPACT_MAX_EF else cs)
+        cmax = COMPACT_MAX_EF_SMALL_D if ix.d <= 256 else COMPACT_MAX_EF
+        return sorted({min(c, cmax) for c in cs} if ef0 <= cmax else cs)
 
     # two operating points: the target recall (thresholds chosen for it) and
     # recall 0.99, where the plain search's fixed ef costs the most
@@ -408,6 +410,7 @@ def stop_point(ix, pool_d, gt_ids, nq, nbe, ef, kw):
 
 L2_BYTES = 129_000_000  # GB300 L2, 129 MB
 COMPACT_MAX_EF = 128  # the largest beam the compact search kernel takes (sqg_search_params.kernel)
+COMPACT_MAX_EF_SMALL_D = 256  # ... and for d <= 256
 
 
 def l2_note(ix, flushed: str) -> str:
@@ -623,7 +626,8 @@ def bench_serving(args, w, ix, q, gt_ids, device):
     latency, achieved QPS and recall@10, with the learned stop on and, for
     comparison, off.  Each k gets the smallest ef of the sweep (>= k) whose
     recall@10 on the test queries reaches the target; with the stop, k = 10
-    requests may search up to twice that beam."""
+    requests may search up to twice that beam, within the compact kernel's
+    range for d <= 256 (ef 256)."""
     import torch
 
     from paper_2411_12229_gb300 import eval as E
@@ -638,7 +642,8 @@ def bench_serving(args, w, ix, q, gt_ids, device):
             if E.recall(ids.cpu().numpy()[:, :10], gt_ids, 10) >= args.target:
                 break
         ef_for[k] = ef
-    caps = {10: 2 * ef_for[10], 100: ef_for[100]}
+    big_ef = COMPACT_MAX_EF_SMALL_D if ix.d <= 256 else COMPACT_MAX_EF
+    caps = {10: max(ef_for[10], min(2 * ef_for[10], big_ef)), 100: ef_for[100]}
     tq = synth.train_queries(w, args.stop_train or 20000)
     tg, _ = E.ground_truth(synth.base(w), tq, 100, device=device)
     model = L.fit_mixed(ix, tq, tg, [(10, caps[10]), (100, caps[100])], args.target, every=4)
@@ -1067,8 +1072,11 @@ def main():
 
 def search_kernel_name(ix, k: int, ef: int, args) -> str:
     """The search kernel a default search of this shape runs (the compact
-    kernel's range: d <= 1024, degree 32 or 64, k <= 32, ef <= 128)."""
-    if ix.d <= 1024 and ix.degree in (32, 64) and k <= 32 and ef <= COMPACT_MAX_EF:
+    kernel's range: d <= 1024, degree 32 or 64, k <= 32, ef <= 128; for
+    d <= 256 k <= 128, ef <= 256)."""
+    small = ix.d <= 256
+    if (ix.d <= 1024 and ix.degree in (32, 64) and k <= (128 if small else 32)
+            and ef <= (COMPACT_MAX_EF_SMALL_D if small else COMPACT_MAX_EF)):
         return "sqg::search_compact_kernel"
     return "sqg::search_kernel"
 
