@@ -84,9 +84,10 @@ class Server:
 
     def _launch(self, slot, sel, queries, ks, efs):
         n = len(sel)
-        slot["qh"][:n].copy_(torch.from_numpy(queries[sel]))
-        slot["kh"][:n].copy_(torch.from_numpy(ks[sel]))
-        slot["eh"][:n].copy_(torch.from_numpy(efs[sel]))
+        # gathered straight into the pinned staging buffers (no temporaries)
+        np.take(queries, sel, axis=0, out=slot["qh"][:n].numpy())
+        np.take(ks, sel, out=slot["kh"][:n].numpy())
+        np.take(efs, sel, out=slot["eh"][:n].numpy())
         s = slot["stream"]
         with torch.cuda.stream(s):
             qd = slot["qh"][:n].to("cuda", non_blocking=True)
@@ -95,7 +96,7 @@ class Server:
             kw = {}
             if self.stop is not None:
                 kw = dict(stop_mlp=self.stop.params, stop_logit=self.stop.logit, stop_every=self.stop.every)
-            tot = int(ks[sel].sum())
+            tot = int(slot["kh"][:n].numpy().sum())
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
             self.ix.search(qd, kd, ed, out=(slot["ids"][:tot], slot["dists"][:tot]), workspace=slot["ws"],
@@ -122,8 +123,7 @@ class Server:
         done_at = np.zeros(n)
         ks = np.ascontiguousarray(ks, dtype=np.int32)
         efs = np.ascontiguousarray(efs, dtype=np.int32)
-        ids_out = np.full((n, self.max_k), -1, dtype=np.int32)
-        d_out = np.full((n, self.max_k), np.inf, dtype=np.float32)
+        retired = []       # per batch: (requests, their flat ids, dists), split per request after the loop
         nxt = 0            # next request (in arrival order) not yet admitted
         inflight = 0       # bytes held by running batches
         held = {}          # slot index -> bytes
@@ -140,11 +140,7 @@ class Server:
                     tdone = time.perf_counter() - t0
                     ev, sel, tot, _, (e0, e1) = b
                     search_ms += e0.elapsed_time(e1)
-                    kk = ks[sel]
-                    rows = np.repeat(sel, kk)
-                    cols = np.arange(tot) - np.repeat(np.cumsum(kk) - kk, kk)
-                    ids_out[rows, cols] = slot["ih"][:tot].numpy()
-                    d_out[rows, cols] = slot["dh"][:tot].numpy()
+                    retired.append((sel, slot["ih"][:tot].numpy().copy(), slot["dh"][:tot].numpy().copy()))
                     lat[sel] = tdone - arrivals_s[sel]
                     done_at[sel] = tdone
                     finished += len(sel)
@@ -178,6 +174,9 @@ class Server:
                     time.sleep(2e-5)
                 idle_s += time.perf_counter() - ts
         wall = time.perf_counter() - t0
-        out_ids = [ids_out[i, :ks[i]] for i in range(n)]
-        out_d = [d_out[i, :ks[i]] for i in range(n)]
+        out_ids, out_d = [None] * n, [None] * n
+        for sel, bi, bd in retired:  # batch outputs are ragged at the prefix sums of k
+            ends = np.cumsum(ks[sel])
+            for r, a, e in zip(sel, ends - ks[sel], ends):
+                out_ids[r], out_d[r] = bi[a:e], bd[a:e]
         return ServeResult(lat, done_at, out_ids, out_d, batches, peak, wall, search_ms, wall - idle_s)
