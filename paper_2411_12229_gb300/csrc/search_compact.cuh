@@ -1,7 +1,9 @@
 // search_compact.cuh -- the compact search kernel: one warp per query for
-// d <= 1024, out-degree 32 or 64, k <= 32 and ef <= 128, with multiple
-// estimates (instantiated in search_compact.cu for d <= 256 and in
-// search_compact_wide.cu for 256 < d <= 1024).
+// d <= 1024, out-degree 32 or 64, k <= 32 and ef <= 128 (for d <= 256 also
+// k <= 128 and ef <= 256), with multiple estimates (instantiated in
+// search_compact.cu for d <= 256, search_compact_wide.cu for 256 < d <=
+// 1024, search_compact_stop.cu with the learned stop and
+// search_compact_big.cu for d <= 256 past k 32 or ef 128).
 //
 // It runs the same Algorithm 1 (Querying, Sec. 3.1.3) with multiple
 // estimated distances and implicit re-ranking (Sec. 3.1.2) as
@@ -13,7 +15,7 @@
 //     (id << 1) | visited, so the (key, id) order of reading R4 is one
 //     unsigned compare and a duplicate (key, id) is one xor;
 //   * the beam (at most 32 NB entries: NB = 2 for ef <= 64, 4 for ef <=
-//     128) sits in shared memory, sorted, and lane l also keeps entries
+//     128, 8 for ef <= 256) sits in shared memory, sorted, and lane l also keeps entries
 //     l + 32 s (s < NB) in registers for the select and the visited marks;
 //     all 32 NB slots are always written, the empty entry (greater than
 //     every entry, visited bit set) from the beam's length on, so the
@@ -22,7 +24,8 @@
 //     binary search; the merged beam is gathered into the other of two
 //     beam buffers, each output slot finding its source from a 32 NB-bit
 //     mask of the candidates' final positions (no shifting loop);
-//   * the k <= 32 results live in registers, lane i holding the i-th;
+//   * the k <= 32 RK results live in registers, lane l holding results
+//     l + 32 s (s < RK);
 //   * with out-degree 64 (NR = 2) lane l estimates neighbours l and l + 32
 //     and the step's candidates are staged 64 wide.
 //
