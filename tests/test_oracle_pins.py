@@ -344,15 +344,17 @@ def small_graph(tmp_path_factory, lib_built, oracle_mod):
     return oracle_mod.Index(p), x, synth.queries(w)
 
 
-def test_full_beam_returns_exact_knn(small_graph, oracle_mod):
+@pytest.mark.parametrize("k", [10, 100, 128])
+def test_full_beam_returns_exact_knn(small_graph, oracle_mod, k):
     """With a beam that never truncates (ef >= n*(R+1) entries), Algorithm 1
     expands every vertex reachable from the entry, so with implicit
-    re-ranking it returns the exact k nearest neighbours."""
+    re-ranking it returns the exact k nearest neighbours (k up to 128: the
+    result list past one slot per lane of a warp)."""
     O, x, qs = small_graph
     ef = O.n * (O.R + 1)
     for i in range(5):
-        ids, dists, hops, st = O.search(qs[i], 10, ef, hop_cap=10 * ef)
-        gt, gd = oracle_mod.bruteforce(x, qs[i], 10)
+        ids, dists, hops, st = O.search(qs[i], k, ef, hop_cap=10 * ef)
+        gt, gd = oracle_mod.bruteforce(x, qs[i], k)
         assert hops == O.n and st == 0
         np.testing.assert_array_equal(ids, gt)
         np.testing.assert_allclose(dists, gd, rtol=1e-5)
