@@ -32,6 +32,22 @@ def request_bytes(k: int, ef: int, d: int) -> int:
     return 8 * ef + 8 * k + hb + 4 * d + 16 + 8 * k
 
 
+def split_batches(retired, ks: np.ndarray, n: int):
+    """Per-request (ids, dists) from retired batches.  Each batch is
+    (sel, flat_ids, flat_dists): the requests it served, in launch order,
+    and its ragged output, request sel[i]'s k results starting at the sum
+    of the k of sel[:i] (the search's output layout).  Returns two lists of
+    n arrays (views into the batches' arrays), None for a request no batch
+    served."""
+    out_ids, out_d = [None] * n, [None] * n
+    for sel, bi, bd in retired:
+        kk = ks[sel]
+        ends = np.cumsum(kk)
+        for r, a, e in zip(sel, ends - kk, ends):
+            out_ids[r], out_d[r] = bi[a:e], bd[a:e]
+    return out_ids, out_d
+
+
 @dataclasses.dataclass
 class ServeResult:
     latency_s: np.ndarray   # per request
@@ -174,9 +190,5 @@ class Server:
                     time.sleep(2e-5)
                 idle_s += time.perf_counter() - ts
         wall = time.perf_counter() - t0
-        out_ids, out_d = [None] * n, [None] * n
-        for sel, bi, bd in retired:  # batch outputs are ragged at the prefix sums of k
-            ends = np.cumsum(ks[sel])
-            for r, a, e in zip(sel, ends - ks[sel], ends):
-                out_ids[r], out_d[r] = bi[a:e], bd[a:e]
+        out_ids, out_d = split_batches(retired, ks, n)
         return ServeResult(lat, done_at, out_ids, out_d, batches, peak, wall, search_ms, wall - idle_s)

@@ -388,3 +388,24 @@ def test_build_graph_ex_on_the_host_equals_the_plain_call(lib_built):
     np.testing.assert_array_equal(s1[:4], s2[:4])
     assert s2[4] == n
     assert B.lib().sqg_build_graph_ex(ptr(x), n, d, ptr(cand), L, R, 0, 3, 2, ptr(a2), ptr(s2), 2, -1) == -1
+
+
+def test_serving_splits_ragged_batches_per_request():
+    """The serving loop's result assembly: each retired batch's flat output
+    (request sel[i]'s k results at the prefix sum of k over sel[:i]) goes
+    back to its requests in any order of batches and requests."""
+    from paper_2411_12229_gb300.serve import split_batches
+    rng = np.random.default_rng(3)
+    n = 40
+    ks = rng.choice([1, 10, 100], size=n).astype(np.int32)
+    want_i = [rng.integers(0, 1000, size=int(k)).astype(np.int32) for k in ks]
+    want_d = [rng.random(int(k)).astype(np.float32) for k in ks]
+    perm = rng.permutation(n)
+    retired = []
+    for part in np.array_split(perm, 5)[::-1]:  # batches retired out of order
+        retired.append((part, np.concatenate([want_i[r] for r in part]), np.concatenate([want_d[r] for r in part])))
+    got_i, got_d = split_batches(retired, ks, n + 1)
+    for r in range(n):
+        np.testing.assert_array_equal(got_i[r], want_i[r])
+        np.testing.assert_array_equal(got_d[r], want_d[r])
+    assert got_i[n] is None and got_d[n] is None
