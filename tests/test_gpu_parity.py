@@ -6,8 +6,6 @@ precision and order), which is stricter than the 1e-5 relative tolerance
 the float values would need on their own.
 """
 
-import os
-
 import numpy as np
 import pytest
 
